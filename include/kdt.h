@@ -1,0 +1,174 @@
+/*
+ * kdt.h — C ABI of the GB300 kinetic Delaunay library (libkdt.so).
+ *
+ * The library maintains the Delaunay triangulation of a set of moving points in the
+ * plane on one GPU.  It follows the problem statement of the paper "A parallel
+ * algorithm for Delaunay triangulation of moving points on the plane":
+ *   - input: a point set with x and y coordinates (Section I) whose triangulation
+ *     satisfies the Delaunay constraints (Fig. 4, "input");
+ *   - at each time step some points move (Section III, movepoint_i) and the
+ *     triangulation is repaired by deleting each moved point and inserting it at its
+ *     new position (Section IV, Fig. 4 lines "Update / Delete / Insert");
+ *   - output: the Delaunay triangulation after every time step (Fig. 4, "return
+ *     dataset(t)").
+ * The triangulation is the unique one defined by the empty-circumcircle property
+ * (Section I); ties between cocircular points are broken by Simulation of Simplicity
+ * (a smaller point id gets a larger lifting perturbation), so results are
+ * bit-reproducible.
+ *
+ * Conventions for every function:
+ *   - Return 0 on success or a negative KDT_ERR_* code; kdt_error_string() names it.
+ *   - Pointers marked "host or device" may point to host memory (pageable or pinned)
+ *     or to device memory of the handle's GPU; the library detects which and copies
+ *     as needed.  The caller keeps ownership of every buffer it passes; the library
+ *     copies inputs in before returning and never keeps a caller pointer.
+ *   - The library owns all device state of a handle (allocated in kdt_create /
+ *     kdt_build, freed in kdt_destroy).  Handles are independent; no global state.
+ *   - Coordinates are int32 in [0, 2^domain_bits) with domain_bits <= 28.
+ *   - All work is issued on the handle's CUDA stream; every call below is complete
+ *     (stream-synchronous) when it returns unless stated otherwise.
+ *   - On an error detected before a step starts modifying the state, the state is
+ *     unchanged.  On an error found while a step runs (duplicate target, degenerate
+ *     configuration), the step is rolled back: positions are restored and the
+ *     triangulation is rebuilt, so the state is again unchanged.
+ */
+#ifndef KDT_H
+#define KDT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------------ */
+#define KDT_OK 0
+#define KDT_ERR_ARG (-1)             /* bad argument (NULL, n < 0, id out of range, ...) */
+#define KDT_ERR_RANGE (-2)           /* a coordinate outside [0, 2^domain_bits)           */
+#define KDT_ERR_DUPLICATE (-3)       /* coincident points, or one id moved twice in a step */
+#define KDT_ERR_DEGENERATE (-4)      /* n < 3 or all points collinear                      */
+#define KDT_ERR_CAPACITY (-5)        /* an output buffer is too small (*n_tri still set)   */
+#define KDT_ERR_RETRY_EXHAUSTED (-6) /* conflict retries exhausted and fallback disabled   */
+#define KDT_ERR_CUDA (-7)            /* a CUDA runtime call failed                         */
+#define KDT_ERR_INTERNAL (-8)        /* an internal consistency check failed               */
+#define KDT_ERR_STATE (-9)           /* call out of order (e.g. kdt_step before kdt_build) */
+
+/* ---- types -------------------------------------------------------------------- */
+typedef struct kdt kdt; /* opaque handle, owned by the library */
+
+/* One moved point: the point's id and its new absolute position (Section III,
+ * movepoint_i; Lemma 1 moves are axis-aligned, but any target is accepted). */
+typedef struct {
+    int32_t id, x, y;
+} kdt_move;
+
+/* Configuration (kdt_default_config fills the defaults).  The paper's only
+ * parameters are the block layout (Section III, Data structure) and N of the
+ * d-calculation; the rest are implementation choices. */
+typedef struct {
+    int32_t grid;          /* G: G x G equal-area partitions over [0,2^domain_bits)^2; 0 = auto
+                              (about 256 points per partition)                              */
+    int32_t domain_bits;   /* B <= 28: coordinates lie in [0, 2^B)                           */
+    int32_t retry_cap;     /* claim retries per operation before giving up (default 4096)   */
+    int32_t fallback;      /* 1: on retry exhaustion / large steps do a full GPU rebuild
+                              (default); 0: return KDT_ERR_RETRY_EXHAUSTED instead          */
+    float rebuild_ratio;   /* m / n above which a step is done as a full rebuild (0.25)     */
+    int32_t filter;        /* 1: FP32 filter in front of the exact incircle (default)       */
+    int32_t verify;        /* 1: run the full GPU verifier after every step (tests)         */
+    int32_t timing;        /* 1: time the kinetic kernel with CUDA events (kdt_stats)       */
+    int32_t warps_per_block; /* kinetic kernel launch shape (default 4)                      */
+    int32_t build_warps;   /* warps inserting concurrently during a build (0 = auto)         */
+    int32_t reserved[6];
+} kdt_config;
+
+/* Counters since creation (or kdt_reset_stats). */
+typedef struct {
+    int64_t steps, moves, rebuilds, fallbacks, kernel_launches;
+    int64_t flips, retries, walk_steps, exact_incircle, sos_ties, deferred;
+    int64_t violations, fixup_flips, deleted_degree_sum, stack_drops, edge_splits;
+    int64_t ghost_splits, deletes, inserts, flip_tests;
+    double kinetic_kernel_ms; /* sum of event-timed kinetic kernel durations (timing = 1) */
+    int64_t kinetic_kernel_timed; /* launches included in kinetic_kernel_ms               */
+    int64_t reserved[8];
+} kdt_stats;
+
+/* ---- lifecycle ------------------------------------------------------------------ */
+
+/* Fill *cfg with the defaults. */
+int kdt_default_config(kdt_config *cfg);
+
+/* Create a handle on CUDA device `device`, issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  cfg may be NULL (defaults).
+ * *out receives the handle.  Errors: KDT_ERR_ARG, KDT_ERR_CUDA. */
+int kdt_create(kdt **out, const kdt_config *cfg, int device, void *cuda_stream);
+
+/* Release every resource of the handle.  NULL is accepted. */
+int kdt_destroy(kdt *h);
+
+/* ---- the method ------------------------------------------------------------------ */
+
+/* Build the Delaunay triangulation of n distinct points xy[2*i], xy[2*i+1]
+ * (host or device) from scratch on the GPU (Fig. 4, "input: a dataset ... that
+ * satisfies Delaunay constraints"; Section III partition into blocks).  Replaces any
+ * previous state.  Errors: KDT_ERR_ARG (NULL, n > 2^28), KDT_ERR_RANGE,
+ * KDT_ERR_DUPLICATE, KDT_ERR_DEGENERATE (n < 3 or all collinear), KDT_ERR_CUDA. */
+int kdt_build(kdt *h, const int32_t *xy, int64_t n);
+
+/* One time step (Fig. 4 loop body): the m moves (host or device; distinct ids) are
+ * applied simultaneously and the triangulation of the new positions is restored:
+ * per partition, each moved point is deleted from the triangulation and inserted at
+ * its new position (Section IV).  The result does not depend on the order of the
+ * moves.  m = 0 is a no-op.  Errors (state unchanged): KDT_ERR_ARG (id out of range),
+ * KDT_ERR_RANGE, KDT_ERR_DUPLICATE (repeated id, or a target coinciding with
+ * another final position), KDT_ERR_DEGENERATE (all final positions collinear),
+ * KDT_ERR_RETRY_EXHAUSTED (only with fallback = 0), KDT_ERR_STATE, KDT_ERR_CUDA. */
+int kdt_step(kdt *h, const kdt_move *moves, int64_t m);
+
+/* Rebuild the triangulation of the current positions from scratch on the GPU (the
+ * full-rebuild comparator; the same code is the fallback of kdt_step). */
+int kdt_rebuild(kdt *h);
+
+/* Export the triangulation (Fig. 4, "return dataset(t)") as the canonical list:
+ * every finite triangle counter-clockwise, rotated so its smallest id comes first,
+ * rows sorted lexicographically; 3 int32 per row into out (host or device, capacity
+ * `cap` rows).  *n_tri receives the row count (2n - 2 - h, h = hull points) even when
+ * the buffer is too small (KDT_ERR_CAPACITY).  out may be NULL with cap = 0 to query. */
+int kdt_export_triangles(kdt *h, int32_t *out, int64_t cap, int64_t *n_tri);
+
+/* Copy the current positions (2 int32 per point) into xy (host or device). */
+int kdt_export_points(kdt *h, int32_t *xy, int64_t cap_points);
+
+/* Full GPU verifier: every triangle alive and counter-clockwise, adjacency
+ * reciprocal, every edge locally Delaunay (SoS), 2n - 2 triangles with ghosts, every
+ * point's incident-triangle pointer valid.  *bad receives the number of failures. */
+int kdt_verify(kdt *h, int64_t *bad);
+
+/* Number of points of the current state (0 before kdt_build). */
+int64_t kdt_num_points(const kdt *h);
+
+/* Counters. */
+int kdt_get_stats(const kdt *h, kdt_stats *out);
+int kdt_reset_stats(kdt *h);
+
+/* Human-readable name of an error code. */
+const char *kdt_error_string(int code);
+
+/* ABI version (incremented on any incompatible change). */
+int kdt_version(void);
+
+/* ---- diagnostics ---------------------------------------------------------------- */
+
+/* Evaluate the device predicates on m quadruples of point indices (Section I,
+ * empty-circumcircle test).  xy: device, 2 int32 per point; quads: device, 4 int32
+ * (a, b, c, d) per row; out: device, 4 int32 per row receiving
+ *   orient2d(a,b,c), exact incircle sign, FP32-filter verdict (0 = uncertain),
+ *   SoS incircle sign (filter as selected by use_filter).
+ * Runs on `cuda_stream` and synchronizes it.  Used by the parity tests. */
+int kdt_eval_predicates(const int32_t *xy, const int32_t *quads, int64_t m, int32_t *out,
+                        int use_filter, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KDT_H */

@@ -1,0 +1,935 @@
+// Device-side triangle store and the warp-cooperative operations of the kinetic
+// update: star deletion (paper, Section IV "Insertion and Deletion", the simple
+// deletion it prefers), walk + split + Lawson flips for insertion (Section IV,
+// insertion; the result equals Bowyer-Watson's), and the claim protocol that lets
+// partitions ("blocks", Fig. 4) work in parallel on one shared triangulation.
+//
+// Store (structure of arrays, 32 B per triangle, ghosts included, 2n-2 slots):
+//   tv[t] = int4(v0, v1, v2, flags)   vertices counter-clockwise; KDT_GHOST = infinity;
+//                                      flags bit 0 = alive
+//   tn[t] = int4(n0, n1, n2, owner)   n_i = (neighbour << 2) | edge index in the
+//                                      neighbour, across the edge opposite v_i;
+//                                      owner = claim token (0 = free)
+//   xy[p] = int2 position, pt_tri[p] = an incident live triangle (-1 while p is
+//   deleted inside a step).
+//
+// Execution model.  One warp runs one operation.  Control flow is warp-uniform:
+// every lane computes the same sequential logic on the same values, global reads
+// are done by one or several lanes and broadcast with shuffles, global writes are
+// issued by lane 0, and lane-parallel sections (claims, loads, ear tests) combine
+// through ballots.  Claims are taken with atomicCAS on the owner word, never waited
+// for while holding others (release all, back off, retry), so no deadlock exists;
+// every retry loop is capped and reports KDT_DEV_RETRY on exhaustion.
+#pragma once
+#include "kdt_predicates.cuh"
+
+namespace kd {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int KMAX = 64;               // largest vertex degree a deletion handles
+constexpr int MAXC = 2 * KMAX + 16;    // claims one warp may hold
+constexpr int STACK = 96;              // Lawson flip stack per warp
+constexpr int WALK_CAP = 1 << 12;      // steps before a walk restarts
+constexpr int WALK_RESTARTS = 64;      // restarts before point location gives up
+constexpr int ALIVE = 1;
+
+// device status codes (first error wins); mapped to the C-ABI codes on the host
+enum DevStatus : int {
+    DEV_OK = 0,
+    DEV_RETRY = 1,        // claim retries exhausted
+    DEV_DEGREE = 2,       // vertex degree above KMAX
+    DEV_DUPLICATE = 3,    // a point would coincide with another
+    DEV_DEGENERATE = 4,   // a deletion would leave all points collinear
+    DEV_INTERNAL = 5,     // inconsistent store (never expected)
+    DEV_WALK = 6,         // point location failed (never expected)
+    DEV_ARG = 7,          // a move failed validation (id / range / repeated id)
+    DEV_RANGE = 8,
+    DEV_CAPACITY = 9,     // a work list overflowed
+};
+
+enum Counter : int {
+    C_FLIPS = 0, C_RETRIES, C_WALK_STEPS, C_EXACT, C_TIES, C_DEFERRED, C_VIOL, C_FIX_FLIPS,
+    C_DEG_DEL, C_STACK_DROP, C_SPLIT_EDGE, C_SPLIT_GHOST, C_DELETES, C_INSERTS, C_FLIP_TESTS,
+    C_NUM
+};
+
+struct Dev {
+    int2 *xy;
+    int *pt_tri;
+    int4 *tv;
+    int4 *tn;
+    int n;
+    int cap;
+    int *status;
+    int *dirty;          // slots written in this step (for certification)
+    int *dirty_count;
+    int dirty_cap;
+    int *pt_stamp;       // step stamp of points moved in this step
+    int stamp;
+    unsigned long long *counters;
+    int use_filter;
+    int retry_cap;
+};
+
+struct WarpShared {
+    int cl[MAXC];          // claimed slots
+    int S[KMAX];           // star slots
+    int I[KMAX];           // index of the centre in each star triangle
+    int L[KMAX];           // link vertices (ccw)
+    int ON[KMAX];          // outer refs across link edges
+    int2 LX[KMAX];         // link coordinates
+    int2 stack[STACK];     // flip stack: (slot, edge)
+    int tmp[64];
+};
+
+struct Warp {
+    WarpShared *sh;
+    int lane;
+    int token;
+    int ncl;
+    unsigned rng;
+    unsigned cnt[C_NUM];
+};
+
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ int4 bcast4(int4 v, int src)
+{
+    v.x = __shfl_sync(FULL, v.x, src);
+    v.y = __shfl_sync(FULL, v.y, src);
+    v.z = __shfl_sync(FULL, v.z, src);
+    v.w = __shfl_sync(FULL, v.w, src);
+    return v;
+}
+
+__device__ __forceinline__ int2 bcast2(int2 v, int src)
+{
+    v.x = __shfl_sync(FULL, v.x, src);
+    v.y = __shfl_sync(FULL, v.y, src);
+    return v;
+}
+
+__device__ __forceinline__ int comp(const int4 &v, int i) { return i == 0 ? v.x : (i == 1 ? v.y : v.z); }
+
+__device__ __forceinline__ unsigned xorshift(unsigned &s)
+{
+    s ^= s << 13;
+    s ^= s >> 17;
+    s ^= s << 5;
+    return s;
+}
+
+__device__ __forceinline__ void set_status(const Dev &d, int code)
+{
+    atomicCAS(d.status, 0, code);
+}
+
+__device__ __forceinline__ int read_status(const Dev &d) { return __shfl_sync(FULL, __ldcg(d.status), 0); }
+
+// Load tv[t] and tn[t] together (lanes 0 and 1) and broadcast.
+// A slot outside the store (an unclaimed read can see the transient -1 neighbour of
+// a triangle another warp is writing) reads as a dead triangle.
+__device__ __forceinline__ void load_tri(const Warp &w, const Dev &d, int t, int4 &v, int4 &nb)
+{
+    int4 x = make_int4(0, 0, 0, 0);
+    bool in = t >= 0 && t < d.cap;
+    if (in && w.lane == 0) x = __ldcg(d.tv + t);
+    else if (in && w.lane == 1) x = __ldcg(d.tn + t);
+    v = bcast4(x, 0);
+    nb = bcast4(x, 1);
+}
+
+// Coordinates of up to 4 vertices (ghost -> (0,0), never used) in one round trip.
+__device__ __forceinline__ void load_xy4(const Warp &w, const Dev &d, int a, int b, int c, int e,
+                                         int2 &pa, int2 &pb, int2 &pc, int2 &pe)
+{
+    int id = w.lane == 0 ? a : (w.lane == 1 ? b : (w.lane == 2 ? c : (w.lane == 3 ? e : KDT_GHOST)));
+    int2 x = make_int2(0, 0);
+    if (id >= 0) x = __ldcg(d.xy + id);
+    pa = bcast2(x, 0);
+    pb = bcast2(x, 1);
+    pc = bcast2(x, 2);
+    pe = bcast2(x, 3);
+}
+
+__device__ __forceinline__ void backptr(const Dev &d, int ref, int val)
+{
+    reinterpret_cast<int *>(d.tn + (ref >> 2))[ref & 3] = val;
+}
+
+__device__ __forceinline__ void dirty_push(const Dev &d, int t)
+{
+    int pos = atomicAdd(d.dirty_count, 1);
+    if (pos < d.dirty_cap) d.dirty[pos] = t;
+}
+
+__device__ __forceinline__ void backoff(Warp &w, int attempt)
+{
+    unsigned lim = 32u << (attempt < 7 ? attempt : 7);
+    unsigned ns = 16 + (xorshift(w.rng) % lim);  // every lane advances the same state
+    if (w.lane == 0) __nanosleep(ns);
+    __syncwarp();
+    w.cnt[C_RETRIES]++;
+}
+
+__device__ __forceinline__ void flush_counters(const Warp &w, const Dev &d)
+{
+    if (w.lane == 0 && d.counters) {
+        for (int i = 0; i < C_NUM; ++i)
+            if (w.cnt[i]) atomicAdd(d.counters + i, (unsigned long long)w.cnt[i]);
+    }
+}
+
+// ------------------------------------------------------------------ claims
+
+// Try to claim the slots lane j holds in `mine` (j < m).  Returns true when every
+// slot is now owned by this warp.  Newly taken slots are appended to the claim
+// list either way; the caller releases everything on failure.
+__device__ __forceinline__ bool claim_lanes(Warp &w, const Dev &d, int mine, int m)
+{
+    bool ok = true, added = false;
+    if (w.lane < m && mine >= 0) {
+        int old = atomicCAS(&d.tn[mine].w, 0, w.token);
+        ok = (old == 0) || (old == w.token);
+        added = (old == 0);
+    }
+    unsigned am = __ballot_sync(FULL, added);
+    unsigned om = __ballot_sync(FULL, ok);
+    if (added) {
+        int pos = w.ncl + __popc(am & ((1u << w.lane) - 1));
+        w.sh->cl[pos] = mine;
+    }
+    w.ncl += __popc(am);
+    __threadfence();
+    __syncwarp();
+    return om == FULL;
+}
+
+// Claim a list held in shared memory (any length; the caller keeps ncl + m <= MAXC).
+__device__ __forceinline__ bool claim_list(Warp &w, const Dev &d, const int *list, int m)
+{
+    bool all = true;
+    for (int base = 0; base < m; base += 32) {
+        int j = base + w.lane;
+        int mine = j < m ? list[j] : -1;
+        all = claim_lanes(w, d, mine, m - base < 32 ? m - base : 32) && all;
+        if (!all) break;
+    }
+    return all;
+}
+
+__device__ __forceinline__ void release_all(Warp &w, const Dev &d)
+{
+    __syncwarp();
+    if (w.lane == 0) {
+        __threadfence();  // our writes are visible before any owner word clears
+        for (int i = 0; i < w.ncl; ++i) atomicExch(&d.tn[w.sh->cl[i]].w, 0);
+    }
+    w.ncl = 0;
+    __syncwarp();
+}
+
+// ------------------------------------------------------------------ walk
+
+enum Where : int { W_INSIDE = 0, W_EDGE = 1, W_VERTEX = 2, W_GHOST = 3, W_FAIL = -1 };
+
+// Visibility walk (exact orient2d) from slot `t` towards q.  Returns the slot where
+// it stopped; `where` classifies q there, `e` is the edge for W_EDGE, `vtx` the
+// coinciding vertex for W_VERTEX.  Reads are unclaimed; callers re-check after
+// claiming.  A random start edge breaks ties so walks cannot cycle forever in the
+// non-Delaunay states other warps may leave transiently.
+__device__ int walk(Warp &w, const Dev &d, int t, int2 q, int &where, int &e, int &vtx)
+{
+    where = W_FAIL;
+    for (int steps = 0; steps < WALK_CAP; ++steps) {
+        w.cnt[C_WALK_STEPS]++;
+        if (t < 0 || t >= d.cap) return -1;
+        int4 v, nb;
+        load_tri(w, d, t, v, nb);
+        if (!(v.w & ALIVE)) return -1;
+        int2 p0, p1, p2, pz;
+        load_xy4(w, d, v.x, v.y, v.z, KDT_GHOST, p0, p1, p2, pz);
+        int g = v.x == KDT_GHOST ? 0 : (v.y == KDT_GHOST ? 1 : (v.z == KDT_GHOST ? 2 : -1));
+        if (g >= 0) {
+            int2 pu = g == 0 ? p1 : (g == 1 ? p2 : p0);
+            int2 pv = g == 0 ? p2 : (g == 1 ? p0 : p1);
+            if (orient2d(pu, pv, q) > 0) {
+                where = W_GHOST;
+                return t;
+            }
+            t = comp(nb, g) >> 2;  // across the finite edge
+            continue;
+        }
+        int o0 = orient2d(p1, p2, q), o1 = orient2d(p2, p0, q), o2 = orient2d(p0, p1, q);
+        unsigned r = xorshift(w.rng) % 3;
+        int nxt = -1;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            int i = (int)((r + k) % 3);
+            int oi = i == 0 ? o0 : (i == 1 ? o1 : o2);
+            if (oi < 0 && nxt < 0) nxt = i;
+        }
+        if (nxt >= 0) {
+            t = comp(nb, nxt) >> 2;
+            continue;
+        }
+        int zeros = (o0 == 0) + (o1 == 0) + (o2 == 0);
+        if (zeros == 0) {
+            where = W_INSIDE;
+        } else if (zeros == 1) {
+            where = W_EDGE;
+            e = o0 == 0 ? 0 : (o1 == 0 ? 1 : 2);
+        } else {
+            where = W_VERTEX;
+            // the vertex shared by the two zero edges
+            vtx = o0 != 0 ? v.x : (o1 != 0 ? v.y : v.z);
+        }
+        return t;
+    }
+    return -1;
+}
+
+// ------------------------------------------------------------------ writes
+
+// Write the fan of m triangles (q, W[k], W[k+1]) into slots X[k]; O[k] is the
+// outer reference across edge (W[k], W[k+1]).  Used by the 1->3 and 2->4 splits.
+__device__ void write_fan(Warp &w, const Dev &d, int q, const int *W, const int *O, const int *X, int m)
+{
+    if (w.lane == 0) {
+        for (int k = 0; k < m; ++k) {
+            int kn = (k + 1) % m, kp = (k + m - 1) % m;
+            d.tv[X[k]] = make_int4(q, W[k], W[kn], ALIVE);
+            d.tn[X[k]] = make_int4(O[k], (X[kn] << 2) | 2, (X[kp] << 2) | 1, w.token);
+        }
+        for (int k = 0; k < m; ++k) {
+            backptr(d, O[k], (X[k] << 2) | 0);
+            if (W[k] >= 0) d.pt_tri[W[k]] = X[k];
+            dirty_push(d, X[k]);
+        }
+        d.pt_tri[q] = X[0];
+    }
+    __syncwarp();
+}
+
+// Flip the edge opposite vertex e of slot T (apex p).  U is the neighbour across it
+// (its apex at index f is d).  Before:  T = (p, a, b),  U = (b, a, d).
+// After:  T = (p, a, d),  U = (p, d, b).  All four outer back-pointers are rewritten.
+__device__ void do_flip(Warp &w, const Dev &d, int T, int e, const int4 &tv_, const int4 &tn_, int U,
+                        int f, const int4 &uv, const int4 &un)
+{
+    if (w.lane == 0) {
+        int p = comp(tv_, e), a = comp(tv_, (e + 1) % 3), b = comp(tv_, (e + 2) % 3);
+        int dd = comp(uv, f);
+        int nt_a = comp(tn_, (e + 1) % 3), nt_b = comp(tn_, (e + 2) % 3);
+        int nu_b = comp(un, (f + 1) % 3), nu_a = comp(un, (f + 2) % 3);
+        d.tv[T] = make_int4(p, a, dd, ALIVE);
+        d.tn[T] = make_int4(nu_b, (U << 2) | 2, nt_b, w.token);
+        d.tv[U] = make_int4(p, dd, b, ALIVE);
+        d.tn[U] = make_int4(nu_a, nt_a, (T << 2) | 1, w.token);
+        backptr(d, nu_b, (T << 2) | 0);
+        backptr(d, nt_b, (T << 2) | 2);
+        backptr(d, nu_a, (U << 2) | 0);
+        backptr(d, nt_a, (U << 2) | 1);
+        if (p >= 0) d.pt_tri[p] = T;
+        if (a >= 0) d.pt_tri[a] = T;
+        if (dd >= 0) d.pt_tri[dd] = T;
+        if (b >= 0) d.pt_tri[b] = U;
+        dirty_push(d, T);
+        dirty_push(d, U);
+    }
+    __syncwarp();
+}
+
+// ------------------------------------------------------------------ Lawson flips
+
+// Process the flip stack.  insertion_mode: only entries whose apex is still `p` are
+// valid and a flip pushes the two edges opposite p (Lawson after an insertion);
+// otherwise (general repair) any apex is accepted and the four outer edges are
+// pushed.  Tests are made on unclaimed reads; only an indicated flip is claimed and
+// re-checked.  An edge that cannot be settled here is left to the certification
+// pass that follows every step, so correctness never depends on this stack.
+__device__ int lawson(Warp &w, const Dev &d, int top, int p, bool insertion_mode)
+{
+    WarpShared *sh = w.sh;
+    int attempts = 0;
+    while (top > 0) {
+        if (read_status(d)) return top;
+        int2 ent = sh->stack[top - 1];
+        __syncwarp();
+        --top;
+        int T = ent.x, e = ent.y;
+        int4 v, nb;
+        load_tri(w, d, T, v, nb);
+        if (!(v.w & ALIVE)) continue;
+        int apex = comp(v, e);
+        if (insertion_mode && apex != p) continue;
+        int ref = comp(nb, e);
+        int U = ref >> 2, f = ref & 3;
+        int4 uv, un;
+        load_tri(w, d, U, uv, un);
+        if (!(uv.w & ALIVE)) continue;
+        int a = comp(v, (e + 1) % 3), b = comp(v, (e + 2) % 3), dd = comp(uv, f);
+        if (comp(uv, (f + 1) % 3) != b || comp(uv, (f + 2) % 3) != a) continue;  // stale read
+        int2 pp, pa, pb, pd;
+        load_xy4(w, d, apex, a, b, dd, pp, pa, pb, pd);
+        w.cnt[C_FLIP_TESTS]++;
+        int vv[3] = {v.x, v.y, v.z};
+        int2 pv[3];
+        pv[e] = pp;
+        pv[(e + 1) % 3] = pa;
+        pv[(e + 2) % 3] = pb;
+        if (!conflict(vv[0], vv[1], vv[2], pv[0], pv[1], pv[2], dd, pd, d.use_filter,
+                      &w.cnt[C_EXACT], &w.cnt[C_TIES]))
+            continue;
+        // claim the quad and its four outer neighbours, then re-check
+        int mine = -1;
+        if (w.lane == 0) mine = T;
+        else if (w.lane == 1) mine = U;
+        else if (w.lane == 2) mine = comp(nb, (e + 1) % 3) >> 2;
+        else if (w.lane == 3) mine = comp(nb, (e + 2) % 3) >> 2;
+        else if (w.lane == 4) mine = comp(un, (f + 1) % 3) >> 2;
+        else if (w.lane == 5) mine = comp(un, (f + 2) % 3) >> 2;
+        bool ok = claim_lanes(w, d, mine, 6);
+        if (ok) {
+            int4 v2, nb2, uv2, un2;
+            load_tri(w, d, T, v2, nb2);
+            load_tri(w, d, U, uv2, un2);
+            ok = v2.x == v.x && v2.y == v.y && v2.z == v.z && (v2.w & ALIVE) && nb2.x == nb.x &&
+                 nb2.y == nb.y && nb2.z == nb.z && uv2.x == uv.x && uv2.y == uv.y && uv2.z == uv.z &&
+                 (uv2.w & ALIVE) && un2.x == un.x && un2.y == un.y && un2.z == un.z;
+            if (ok) {
+                do_flip(w, d, T, e, v2, nb2, U, f, uv2, un2);
+                w.cnt[insertion_mode ? C_FLIPS : C_FIX_FLIPS]++;
+                release_all(w, d);
+                // push follow-up edges
+                int add = insertion_mode ? 2 : 4;
+                if (top + add > STACK) {
+                    w.cnt[C_STACK_DROP]++;
+                    continue;
+                }
+                if (w.lane == 0) {
+                    sh->stack[top] = make_int2(T, 0);
+                    sh->stack[top + 1] = make_int2(U, 0);
+                    if (!insertion_mode) {
+                        sh->stack[top + 2] = make_int2(T, 2);
+                        sh->stack[top + 3] = make_int2(U, 1);
+                    }
+                }
+                __syncwarp();
+                top += add;
+                attempts = 0;
+                continue;
+            }
+        }
+        release_all(w, d);
+        // contention or a stale read: retry this edge later
+        if (++attempts > d.retry_cap) {
+            w.cnt[C_STACK_DROP]++;
+            attempts = 0;
+            continue;
+        }
+        backoff(w, attempts);
+        if (w.lane == 0) sh->stack[top] = ent;
+        __syncwarp();
+        ++top;
+    }
+    return 0;
+}
+
+// ------------------------------------------------------------------ insertion
+
+// Insertion outside the hull (Section IV insertion; the ghost part of the Bowyer-
+// Watson cavity).  The hull edges visible from q form one chain x_0 -> ... -> x_k;
+// its ghosts, the finite triangles behind them, the two ghosts at its ends and the
+// two spare slots are claimed together, and the chain is replaced in one fan
+// (q, x_k, x_{k-1}), ..., (q, x_1, x_0), (q, x_0, inf), (q, inf, x_k).  Doing it in
+// one claimed operation keeps the hull convex whenever nothing is claimed, so no
+// other warp can ever mistake a pocket of a half-repaired hull for the outside.
+// Returns 0 when written, 1 to retry (contention or stale reads), or an error.
+__device__ int insert_outside(Warp &w, const Dev &d, int p, int2 q, int V0, int spare0, int spare1, int &m_out)
+{
+    WarpShared *sh = w.sh;
+    const int KCH = 60;
+    // ghost (u, v, inf) at slot t: g = index of inf, u = v[g+1], v = v[g+2]; hull edge v -> u.
+    // backward neighbour (hull edge ending at v): edge index g+1; forward (from u): g+2.
+    int cur = V0, eb_ref = -1;
+    for (int s = 0;; ++s) {
+        if (s > KCH) return DEV_CAPACITY;
+        int4 v, nb;
+        load_tri(w, d, cur, v, nb);
+        int g = v.x == KDT_GHOST ? 0 : (v.y == KDT_GHOST ? 1 : (v.z == KDT_GHOST ? 2 : -1));
+        if (!(v.w & ALIVE) || g < 0) return 1;
+        int br = comp(nb, (g + 1) % 3);
+        int4 bv, bn;
+        load_tri(w, d, br >> 2, bv, bn);
+        int bg = bv.x == KDT_GHOST ? 0 : (bv.y == KDT_GHOST ? 1 : (bv.z == KDT_GHOST ? 2 : -1));
+        if (!(bv.w & ALIVE) || bg < 0) return 1;
+        int2 pu, pv, pz, pz2;
+        load_xy4(w, d, comp(bv, (bg + 1) % 3), comp(bv, (bg + 2) % 3), KDT_GHOST, KDT_GHOST, pu, pv, pz, pz2);
+        if (orient2d(pu, pv, q) <= 0) {
+            eb_ref = br;
+            break;
+        }
+        cur = br >> 2;
+    }
+    // forward from the first visible ghost, recording the chain in ccw order
+    int k = 0, ef_ref = -1;
+    while (true) {
+        if (k >= KCH) return DEV_CAPACITY;
+        int4 v, nb;
+        load_tri(w, d, cur, v, nb);
+        int g = v.x == KDT_GHOST ? 0 : (v.y == KDT_GHOST ? 1 : (v.z == KDT_GHOST ? 2 : -1));
+        if (!(v.w & ALIVE) || g < 0) return 1;
+        if (w.lane == 0) {
+            sh->S[k] = cur;
+            sh->L[k] = comp(v, (g + 2) % 3);      // x_k = v (start of the hull edge)
+            sh->L[k + 1] = comp(v, (g + 1) % 3);  // x_{k+1} = u
+            sh->ON[k] = comp(nb, g);              // finite triangle behind the hull edge
+            sh->I[k] = comp(nb, (g + 2) % 3);     // forward ref
+        }
+        __syncwarp();
+        ++k;
+        int fr = comp(nb, (g + 2) % 3);
+        int4 fv, fn;
+        load_tri(w, d, fr >> 2, fv, fn);
+        int fg = fv.x == KDT_GHOST ? 0 : (fv.y == KDT_GHOST ? 1 : (fv.z == KDT_GHOST ? 2 : -1));
+        if (!(fv.w & ALIVE) || fg < 0) return 1;
+        int2 pu, pv, pz, pz2;
+        load_xy4(w, d, comp(fv, (fg + 1) % 3), comp(fv, (fg + 2) % 3), KDT_GHOST, KDT_GHOST, pu, pv, pz, pz2);
+        if (orient2d(pu, pv, q) <= 0) {
+            ef_ref = fr;
+            break;
+        }
+        cur = fr >> 2;
+        if (cur == sh->S[0]) return 1;  // wrapped around: stale reads
+    }
+    // claim: chain ghosts, finite triangles behind them, end ghosts, spares
+    int *cand = reinterpret_cast<int *>(sh->LX);
+    if (w.lane == 0) {
+        for (int j = 0; j < k; ++j) {
+            cand[2 * j] = sh->S[j];
+            cand[2 * j + 1] = sh->ON[j] >> 2;
+        }
+        cand[2 * k] = eb_ref >> 2;
+        cand[2 * k + 1] = ef_ref >> 2;
+        cand[2 * k + 2] = spare0;
+        cand[2 * k + 3] = spare1;
+    }
+    __syncwarp();
+    bool ok = claim_list(w, d, cand, 2 * k + 4);
+    if (ok) {
+        // re-check the chain under the claims
+        bool good = true;
+        for (int j = w.lane; j < k; j += 32) {
+            int4 v = __ldcg(d.tv + sh->S[j]);
+            int4 nb = __ldcg(d.tn + sh->S[j]);
+            int g = v.x == KDT_GHOST ? 0 : (v.y == KDT_GHOST ? 1 : (v.z == KDT_GHOST ? 2 : -1));
+            good = good && (v.w & ALIVE) && g >= 0 && comp(v, (g + 2) % 3) == sh->L[j] &&
+                   comp(v, (g + 1) % 3) == sh->L[j + 1] && comp(nb, g) == sh->ON[j] &&
+                   comp(nb, (g + 2) % 3) == sh->I[j] &&
+                   (j + 1 == k ? comp(nb, (g + 2) % 3) == ef_ref : (comp(nb, (g + 2) % 3) >> 2) == sh->S[j + 1]) &&
+                   (j == 0 ? comp(nb, (g + 1) % 3) == eb_ref : true);
+            if (good) {
+                int2 pu = __ldcg(d.xy + sh->L[j + 1]), pv = __ldcg(d.xy + sh->L[j]);
+                good = orient2d(pu, pv, q) > 0;
+            }
+        }
+        if (w.lane < 2) {
+            int ref = w.lane == 0 ? eb_ref : ef_ref;
+            int4 v = __ldcg(d.tv + (ref >> 2));
+            int g = v.x == KDT_GHOST ? 0 : (v.y == KDT_GHOST ? 1 : (v.z == KDT_GHOST ? 2 : -1));
+            good = good && (v.w & ALIVE) && g >= 0;
+            if (good) {
+                int2 pu = __ldcg(d.xy + comp(v, (g + 1) % 3)), pv = __ldcg(d.xy + comp(v, (g + 2) % 3));
+                good = orient2d(pu, pv, q) <= 0;
+            }
+        }
+        ok = __all_sync(FULL, good);
+    }
+    if (!ok) {
+        release_all(w, d);
+        return 1;
+    }
+    // fan: W = (x_k, ..., x_0, inf) in tmp, outer refs (F_{k-1}, ..., F_0, E_b, E_f) in I
+    // (the forward refs are no longer needed), slots = the chain's own slots + spares in S
+    int m = k + 2;
+    int *W = sh->tmp, *Ow = sh->I, *Xw = sh->S;
+    if (w.lane == 0) {
+        for (int j = 0; j < k; ++j) W[j] = sh->L[k - j];
+        W[k] = sh->L[0];
+        W[k + 1] = KDT_GHOST;
+        for (int j = 0; j < k; ++j) Ow[j] = sh->ON[k - 1 - j];
+        Ow[k] = eb_ref;
+        Ow[k + 1] = ef_ref;
+        Xw[k] = spare0;
+        Xw[k + 1] = spare1;
+    }
+    __syncwarp();
+    write_fan(w, d, p, W, Ow, Xw, m);
+    w.cnt[C_SPLIT_GHOST]++;
+    w.cnt[C_INSERTS]++;
+    release_all(w, d);
+    m_out = m;
+    return 0;
+}
+
+// Insert point p (its coordinates already in xy[p]) starting the walk at `start`.
+// spare0 / spare1 are two dead slots owned by the caller (a deletion's leftovers or
+// fresh slots during a build).  Returns 0, 1 = deferred (p lands on a vertex that is
+// still moving in this step), or a DevStatus error.
+__device__ int insert_point(Warp &w, const Dev &d, int p, int2 q, int start, int spare0, int spare1,
+                            bool allow_defer)
+{
+    WarpShared *sh = w.sh;
+    int t = start, walk_fail = 0;
+    for (int attempt = 0;; ++attempt) {
+        if (attempt > d.retry_cap) return DEV_RETRY;
+        if (read_status(d)) return -1;
+        int where, e = 0, vtx = -1;
+        int tt = walk(w, d, t, q, where, e, vtx);
+        if (tt < 0) {
+            if (++walk_fail > WALK_RESTARTS) return DEV_WALK;
+            // restart from the hint, then from the triangle of a random present point
+            if (attempt & 1) {
+                t = start;
+            } else {
+                int r = (int)(xorshift(w.rng) % (unsigned)d.n);
+                t = __shfl_sync(FULL, __ldcg(d.pt_tri + r), 0);
+                if (t < 0) t = start;
+            }
+            backoff(w, attempt);
+            continue;
+        }
+        if (where == W_VERTEX) {
+            int st = __shfl_sync(FULL, __ldcg(d.pt_stamp + vtx), 0);
+            if (allow_defer && st == d.stamp) return 1;
+            return DEV_DUPLICATE;
+        }
+        if (where == W_GHOST) {
+            int m = 0;
+            int r = insert_outside(w, d, p, q, tt, spare0, spare1, m);
+            if (r == 1) {
+                t = tt;
+                backoff(w, attempt);
+                continue;
+            }
+            if (r) return r;
+            if (w.lane == 0)
+                for (int j = 0; j < m; ++j) sh->stack[j] = make_int2(sh->S[j], 0);
+            __syncwarp();
+            lawson(w, d, m, p, true);
+            return DEV_OK;
+        }
+        int4 v, nb;
+        load_tri(w, d, tt, v, nb);
+        int U = -1, f = 0;
+        int4 uv = make_int4(0, 0, 0, 0), un = make_int4(0, 0, 0, 0);
+        if (where == W_EDGE) {
+            U = comp(nb, e) >> 2;
+            f = comp(nb, e) & 3;
+            load_tri(w, d, U, uv, un);
+        }
+        // claim: the triangle(s) split, their outer neighbours, the spare slots
+        int mine = -1;
+        switch (w.lane) {
+        case 0: mine = tt; break;
+        case 1: mine = spare0; break;
+        case 2: mine = spare1; break;
+        case 3: mine = where == W_EDGE ? comp(nb, (e + 1) % 3) >> 2 : nb.x >> 2; break;
+        case 4: mine = where == W_EDGE ? comp(nb, (e + 2) % 3) >> 2 : nb.y >> 2; break;
+        case 5: mine = where == W_EDGE ? U : nb.z >> 2; break;
+        case 6: mine = where == W_EDGE ? comp(un, (f + 1) % 3) >> 2 : -1; break;
+        case 7: mine = where == W_EDGE ? comp(un, (f + 2) % 3) >> 2 : -1; break;
+        default: break;
+        }
+        bool ok = claim_lanes(w, d, mine, 8);
+        if (ok) {
+            // re-read under the claims and re-classify
+            int4 v2, nb2;
+            load_tri(w, d, tt, v2, nb2);
+            ok = (v2.w & ALIVE) && v2.x == v.x && v2.y == v.y && v2.z == v.z && nb2.x == nb.x &&
+                 nb2.y == nb.y && nb2.z == nb.z;
+            if (ok && where == W_EDGE) {
+                int4 uv2, un2;
+                load_tri(w, d, U, uv2, un2);
+                ok = (uv2.w & ALIVE) && uv2.x == uv.x && uv2.y == uv.y && uv2.z == uv.z &&
+                     un2.x == un.x && un2.y == un.y && un2.z == un.z;
+            }
+            if (ok) {
+                int2 p0, p1, p2, pz;
+                load_xy4(w, d, v.x, v.y, v.z, KDT_GHOST, p0, p1, p2, pz);
+                int g = v.x == KDT_GHOST ? 0 : (v.y == KDT_GHOST ? 1 : (v.z == KDT_GHOST ? 2 : -1));
+                if (g >= 0) {
+                    int2 pu = g == 0 ? p1 : (g == 1 ? p2 : p0);
+                    int2 pv = g == 0 ? p2 : (g == 1 ? p0 : p1);
+                    ok = where == W_GHOST && orient2d(pu, pv, q) > 0;
+                } else {
+                    int o0 = orient2d(p1, p2, q), o1 = orient2d(p2, p0, q), o2 = orient2d(p0, p1, q);
+                    int zeros = (o0 == 0) + (o1 == 0) + (o2 == 0);
+                    ok = o0 >= 0 && o1 >= 0 && o2 >= 0 &&
+                         ((where == W_INSIDE && zeros == 0) ||
+                          (where == W_EDGE && zeros == 1 && comp(make_int4(o0, o1, o2, 0), e) == 0));
+                }
+            }
+        }
+        if (!ok) {
+            release_all(w, d);
+            t = tt;
+            backoff(w, attempt);
+            continue;
+        }
+        // split
+        int *W = sh->tmp, *O = sh->tmp + 8, *X = sh->tmp + 16;
+        int m;
+        if (w.lane == 0) {
+            if (where == W_EDGE) {
+                int a = comp(v, e), b = comp(v, (e + 1) % 3), c = comp(v, (e + 2) % 3);
+                int dd = comp(uv, f);
+                W[0] = a; W[1] = b; W[2] = dd; W[3] = c;
+                O[0] = comp(nb, (e + 2) % 3);   // (a, b)
+                O[1] = comp(un, (f + 1) % 3);   // (b, d): u = (d, c, b), edge opposite c
+                O[2] = comp(un, (f + 2) % 3);   // (d, c): edge opposite b
+                O[3] = comp(nb, (e + 1) % 3);   // (c, a)
+                X[0] = tt; X[1] = U; X[2] = spare0; X[3] = spare1;
+            } else {
+                W[0] = v.x; W[1] = v.y; W[2] = v.z;
+                O[0] = nb.z; O[1] = nb.x; O[2] = nb.y;
+                X[0] = tt; X[1] = spare0; X[2] = spare1;
+            }
+        }
+        m = where == W_EDGE ? 4 : 3;
+        __syncwarp();
+        write_fan(w, d, p, W, O, X, m);
+        if (where == W_EDGE) w.cnt[C_SPLIT_EDGE]++;
+        if (where == W_GHOST) w.cnt[C_SPLIT_GHOST]++;
+        w.cnt[C_INSERTS]++;
+        release_all(w, d);
+        if (w.lane == 0)
+            for (int k = 0; k < m; ++k) sh->stack[k] = make_int2(X[k], 0);
+        __syncwarp();
+        lawson(w, d, m, p, true);
+        return DEV_OK;
+    }
+}
+
+// ------------------------------------------------------------------ deletion
+
+// Gather the star of p counter-clockwise from pt_tri[p] into S/I/L/ON.  Returns k,
+// or -1 when the reads are inconsistent (another warp is working there), -2 when
+// the degree exceeds KMAX.
+__device__ int gather_star(Warp &w, const Dev &d, int p)
+{
+    WarpShared *sh = w.sh;
+    int t0 = __ldcg(d.pt_tri + p);
+    t0 = __shfl_sync(FULL, t0, 0);
+    if (t0 < 0 || t0 >= d.cap) return -1;
+    int t = t0, k = 0;
+    while (true) {
+        int4 v, nb;
+        load_tri(w, d, t, v, nb);
+        if (!(v.w & ALIVE)) return -1;
+        int I = v.x == p ? 0 : (v.y == p ? 1 : (v.z == p ? 2 : -1));
+        if (I < 0) return -1;
+        if (k >= KMAX) return -2;
+        if (w.lane == 0) {
+            sh->S[k] = t;
+            sh->I[k] = I;
+            sh->L[k] = comp(v, (I + 1) % 3);
+            sh->ON[k] = comp(nb, I);
+        }
+        ++k;
+        int nx = comp(nb, (I + 1) % 3) >> 2;
+        if (nx == t0) break;
+        if (nx < 0 || nx >= d.cap) return -1;
+        t = nx;
+    }
+    __syncwarp();
+    return k;
+}
+
+// Is ear (L[i], L[i+1], L[i+2]) of the current link polygon valid?  Finite ears must
+// be counter-clockwise; no remaining link vertex may conflict with the ear
+// (SoS incircle, or the ghost rule for ears through infinity).
+__device__ bool ear_valid(const int *EL, const int2 *EX, int m, int i, const Dev &d,
+                          unsigned *exact_calls, unsigned *ties)
+{
+    int i1 = (i + 1) % m, i2 = (i + 2) % m;
+    int x = EL[i], y = EL[i1], z = EL[i2];
+    int2 px = EX[i], py = EX[i1], pz = EX[i2];
+    int g = x == KDT_GHOST ? 0 : (y == KDT_GHOST ? 1 : (z == KDT_GHOST ? 2 : -1));
+    if (g < 0 && orient2d(px, py, pz) <= 0) return false;
+    int2 gu = g == 0 ? py : (g == 1 ? pz : px);
+    int2 gv = g == 0 ? pz : (g == 1 ? px : py);
+    for (int j = 0; j < m; ++j) {
+        if (j == i || j == i1 || j == i2) continue;
+        int wv = EL[j];
+        if (wv == KDT_GHOST) continue;
+        bool c = g >= 0 ? ghost_conflict(gu, gv, EX[j])
+                        : incircle_sos(x, y, z, wv, px, py, pz, EX[j], d.use_filter, exact_calls, ties) > 0;
+        if (c) return false;
+    }
+    return true;
+}
+
+// Delete p: claim its star and the ring of outer neighbours, re-triangulate the
+// star-shaped hole by Delaunay ears (the simple deletion the paper prefers, Section
+// IV), release.  On success the two slots the hole no longer needs are returned
+// dead in spare0/spare1 and `hint` is a new triangle next to p's old position.
+__device__ int delete_point(Warp &w, const Dev &d, int p, int &spare0, int &spare1, int &hint)
+{
+    WarpShared *sh = w.sh;
+    for (int attempt = 0;; ++attempt) {
+        if (attempt > d.retry_cap) return DEV_RETRY;
+        if (read_status(d)) return -1;
+        int k = gather_star(w, d, p);
+        if (k == -2 && attempt >= 3) return DEV_DEGREE;
+        if (k < 3) {
+            backoff(w, attempt);
+            continue;
+        }
+        // claim the star and the outer ring (outer refs > star refs in the list)
+        if (w.lane == 0)
+            for (int i = 0; i < k; ++i) sh->tmp[i] = sh->ON[i] >> 2;
+        __syncwarp();
+        bool ok = claim_list(w, d, sh->S, k);
+        if (ok) ok = claim_list(w, d, sh->tmp, k);
+        if (ok) {
+            // validate the gathered star under the claims (one parallel pass)
+            bool good = true;
+            for (int i = w.lane; i < k; i += 32) {
+                int4 v = __ldcg(d.tv + sh->S[i]);
+                int4 nb = __ldcg(d.tn + sh->S[i]);
+                int I = sh->I[i];
+                good = good && (v.w & ALIVE) && comp(v, I) == p && comp(v, (I + 1) % 3) == sh->L[i] &&
+                       comp(nb, I) == sh->ON[i] && (comp(nb, (I + 1) % 3) >> 2) == sh->S[(i + 1) % k];
+            }
+            ok = __all_sync(FULL, good);
+        }
+        if (!ok) {
+            release_all(w, d);
+            backoff(w, attempt);
+            continue;
+        }
+        // link coordinates
+        for (int i = w.lane; i < k; i += 32) {
+            int lv = sh->L[i];
+            sh->LX[i] = lv >= 0 ? __ldcg(d.xy + lv) : make_int2(0, 0);
+        }
+        __syncwarp();
+        // degenerate check: a hull vertex whose finite link is collinear and whose
+        // ring has no finite triangle would leave only collinear points behind
+        int gpos = -1;
+        for (int i = 0; i < k; ++i)
+            if (sh->L[i] == KDT_GHOST) gpos = i;
+        if (gpos >= 0) {
+            int f0 = (gpos + 1) % k, f1 = (gpos + 2) % k;
+            bool col = true;
+            for (int i = 0; i < k; ++i)
+                if (i != gpos && orient2d(sh->LX[f0], sh->LX[f1], sh->LX[i]) != 0) col = false;
+            if (col) {
+                bool finite_ring = false;
+                for (int i = w.lane; i < k; i += 32) {
+                    if (sh->L[i] == KDT_GHOST || sh->L[(i + 1) % k] == KDT_GHOST) continue;
+                    int4 ov = __ldcg(d.tv + (sh->ON[i] >> 2));
+                    if (ov.x != KDT_GHOST && ov.y != KDT_GHOST && ov.z != KDT_GHOST) finite_ring = true;
+                }
+                if (!__any_sync(FULL, finite_ring)) {
+                    release_all(w, d);
+                    return DEV_DEGENERATE;
+                }
+            }
+        }
+        // ear clipping over the link polygon; EL/EO/EX live in L/ON/LX
+        int m = k, newc = 0;
+        while (m > 3) {
+            int chosen = -1;
+            unsigned ex = 0, ti = 0;
+            for (int base = 0; base < m && chosen < 0; base += 32) {
+                int i = base + w.lane;
+                bool v = i < m && ear_valid(sh->L, sh->LX, m, i, d, &ex, &ti);
+                unsigned bm = __ballot_sync(FULL, v);
+                if (bm) chosen = base + __ffs(bm) - 1;
+            }
+            w.cnt[C_EXACT] += __reduce_add_sync(FULL, ex);
+            w.cnt[C_TIES] += __reduce_add_sync(FULL, ti);
+            if (chosen < 0) {
+                // cannot happen for a valid star; leave the store to the fallback
+                release_all(w, d);
+                return DEV_INTERNAL;
+            }
+            int i = chosen, i1 = (i + 1) % m, i2 = (i + 2) % m;
+            int X = sh->S[newc++];
+            if (w.lane == 0) {
+                d.tv[X] = make_int4(sh->L[i], sh->L[i1], sh->L[i2], ALIVE);
+                d.tn[X] = make_int4(sh->ON[i1], -1, sh->ON[i], w.token);
+                backptr(d, sh->ON[i1], (X << 2) | 0);
+                backptr(d, sh->ON[i], (X << 2) | 2);
+                if (sh->L[i] >= 0) d.pt_tri[sh->L[i]] = X;
+                if (sh->L[i1] >= 0) d.pt_tri[sh->L[i1]] = X;
+                if (sh->L[i2] >= 0) d.pt_tri[sh->L[i2]] = X;
+                dirty_push(d, X);
+                sh->ON[i] = (X << 2) | 1;
+            }
+            __syncwarp();
+            // remove element i1 (shift the tail down by one)
+            int lv = 0, onv = 0;
+            int2 xv = make_int2(0, 0);
+            int j = w.lane;
+            bool mv = j >= i1 && j < m - 1;
+            if (mv) {
+                lv = sh->L[j + 1];
+                onv = sh->ON[j + 1];
+                xv = sh->LX[j + 1];
+            }
+            bool mv2 = j + 32 >= i1 && j + 32 < m - 1;
+            int lv2 = 0, onv2 = 0;
+            int2 xv2 = make_int2(0, 0);
+            if (mv2) {
+                lv2 = sh->L[j + 33];
+                onv2 = sh->ON[j + 33];
+                xv2 = sh->LX[j + 33];
+            }
+            __syncwarp();
+            if (mv) {
+                sh->L[j] = lv;
+                sh->ON[j] = onv;
+                sh->LX[j] = xv;
+            }
+            if (mv2) {
+                sh->L[j + 32] = lv2;
+                sh->ON[j + 32] = onv2;
+                sh->LX[j + 32] = xv2;
+            }
+            __syncwarp();
+            --m;
+        }
+        {
+            int X = sh->S[newc++];
+            if (w.lane == 0) {
+                d.tv[X] = make_int4(sh->L[0], sh->L[1], sh->L[2], ALIVE);
+                d.tn[X] = make_int4(sh->ON[1], sh->ON[2], sh->ON[0], w.token);
+                backptr(d, sh->ON[1], (X << 2) | 0);
+                backptr(d, sh->ON[2], (X << 2) | 1);
+                backptr(d, sh->ON[0], (X << 2) | 2);
+                for (int c = 0; c < 3; ++c)
+                    if (sh->L[c] >= 0) d.pt_tri[sh->L[c]] = X;
+                dirty_push(d, X);
+            }
+        }
+        // the two slots left over
+        spare0 = sh->S[k - 2];
+        spare1 = sh->S[k - 1];
+        hint = sh->S[0];
+        if (w.lane == 0) {
+            d.tv[spare0].w = 0;
+            d.tv[spare1].w = 0;
+            d.pt_tri[p] = -1;
+        }
+        w.cnt[C_DEG_DEL] += k;
+        w.cnt[C_DELETES]++;
+        release_all(w, d);
+        return DEV_OK;
+    }
+}
+
+}  // namespace kd

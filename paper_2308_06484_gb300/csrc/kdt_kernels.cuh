@@ -1,0 +1,631 @@
+// Kernels of the kinetic Delaunay library.  Included once, by kdt.cu.
+//
+//   step:    k_intake -> scan -> k_scatter -> k_kinetic -> k_deferred -> k_certify
+//            (-> k_fixup / k_certify until no violation)
+//   build:   k_range / k_bbox -> k_hilbert -> scan -> k_place_order -> k_third -> k_init
+//            -> k_insert_level (one launch per level) -> k_certify_all (-> k_fixup ...)
+//   export:  k_exp_count -> scan -> k_exp_place -> k_exp_sortseg
+#pragma once
+#include "kdt_device.cuh"
+
+namespace kd {
+
+constexpr int WPB = 4;  // warps per block of the warp-per-item kernels
+constexpr int DEV_DUP_ID = 10;  // a move id repeated within one step (found at intake)
+
+// small device block of scalars
+enum Slot : int {
+    S_STATUS = 0, S_DIRTY = 1, S_VIOL = 2, S_TRIS = 3, S_DEFER = 4, S_THIRD = 5,
+    S_MINX = 6, S_MINY = 7, S_MAXX = 8, S_MAXY = 9, S_TOTAL = 10, S_BAD = 11, S_ALIVE = 12,
+    S_WRAPS = 13, S_NUM = 16
+};
+
+__device__ __forceinline__ Warp make_warp(WarpShared *sh, int token, unsigned seed)
+{
+    Warp w;
+    w.sh = sh;
+    w.lane = threadIdx.x & 31;
+    w.token = token;
+    w.ncl = 0;
+    w.rng = seed * 2654435761u + 0x9E3779B9u;
+    if (w.rng == 0) w.rng = 1;
+#pragma unroll
+    for (int i = 0; i < C_NUM; ++i) w.cnt[i] = 0;
+    return w;
+}
+
+// ------------------------------------------------------------------ scan
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+// exclusive scan of one tile; tile totals to tile_sums
+__global__ void k_scan_tile(const int *in, int *out, int n, int *tile_sums)
+{
+    __shared__ int ws[SCAN_THREADS / 32];
+    int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    int v[SCAN_ITEMS];
+    int s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        v[i] = base + i < n ? in[base + i] : 0;
+        s += v[i];
+    }
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int y = lane < SCAN_THREADS / 32 ? ws[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int z = __shfl_up_sync(FULL, y, o);
+            if (lane >= o) y += z;
+        }
+        if (lane < SCAN_THREADS / 32) ws[lane] = y;
+    }
+    __syncthreads();
+    int run = x - s + (wid > 0 ? ws[wid - 1] : 0);
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        if (base + i < n) out[base + i] = run;
+        run += v[i];
+    }
+    if (threadIdx.x == SCAN_THREADS - 1) tile_sums[blockIdx.x] = run;
+}
+
+// exclusive scan of the tile totals in one block; grand total to *total
+__global__ void k_scan_sums(int *tile_sums, int ntiles, int *total)
+{
+    __shared__ int ws[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int base = 0; base < ntiles; base += blockDim.x) {
+        int i = base + threadIdx.x;
+        int s = i < ntiles ? tile_sums[i] : 0;
+        int x = s;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) ws[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int y = lane < (int)(blockDim.x / 32) ? ws[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                int z = __shfl_up_sync(FULL, y, o);
+                if (lane >= o) y += z;
+            }
+            ws[lane] = y;
+        }
+        __syncthreads();
+        int excl = carry + x - s + (wid > 0 ? ws[wid - 1] : 0);
+        if (i < ntiles) tile_sums[i] = excl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + s;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void k_scan_add(int *out, int n, const int *tile_sums)
+{
+    int add = tile_sums[blockIdx.x];
+    int base = blockIdx.x * SCAN_TILE;
+    for (int i = threadIdx.x; i < SCAN_TILE; i += blockDim.x)
+        if (base + i < n) out[base + i] += add;
+}
+
+// ------------------------------------------------------------------ step: intake
+
+// Validate the moves (A2), stamp the moved ids, remember old positions, and count
+// the moves of each partition (Section III blocks; cell of the point's position at
+// the start of the step: the block that owns it).
+__global__ void k_intake(Dev d, const int3 *moves, int m, int grid, int bits, int *cell_cnt,
+                         int2 *old_xy, int *move_cell)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int3 mv = moves[i];
+    if (mv.x < 0 || mv.x >= d.n) {
+        atomicCAS(d.status, 0, DEV_ARG);
+        return;
+    }
+    long long lim = 1ll << bits;
+    if (mv.y < 0 || mv.z < 0 || mv.y >= lim || mv.z >= lim) {
+        atomicCAS(d.status, 0, DEV_RANGE);
+        return;
+    }
+    int prev = atomicExch(d.pt_stamp + mv.x, d.stamp);
+    if (prev == d.stamp) {
+        atomicCAS(d.status, 0, DEV_DUP_ID);
+        return;
+    }
+    int2 o = d.xy[mv.x];
+    old_xy[i] = o;
+    int cx = (int)(((long long)o.x * grid) >> bits);
+    int cy = (int)(((long long)o.y * grid) >> bits);
+    int c = cy * grid + cx;
+    move_cell[i] = c;
+    atomicAdd(cell_cnt + c, 1);
+}
+
+__global__ void k_scatter(int m, const int *move_cell, const int *cell_off, int *cell_fill, int *order,
+                          const int *status)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m || *status) return;
+    int c = move_cell[i];
+    order[cell_off[c] + atomicAdd(cell_fill + c, 1)] = i;
+}
+
+// ------------------------------------------------------------------ step: kinetic
+
+// One warp per partition (Fig. 4 "foreach block i do in parallel"): for each of the
+// block's moved points, Delete (Section IV), Update the coordinate, Insert at the
+// new position (walk, split, Lawson flips).  The new block of a point that crosses a
+// partition border follows from its new position; all blocks share one
+// triangulation in HBM, so the hand-off of Fig. 4 is an ownership change, not a
+// message.  A point whose target is still occupied by a point that has not moved
+// yet is deferred to k_deferred.
+__global__ void __launch_bounds__(WPB * 32) k_kinetic(Dev d, const int3 *moves, const int *order,
+                                                      const int *cell_cnt, const int *cell_off, int ncells,
+                                                      int4 *deferred, int *defer_count, int defer_cap)
+{
+    __shared__ WarpShared shs[WPB];
+    int wib = threadIdx.x >> 5;
+    int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+    int nw = gridDim.x * (blockDim.x >> 5);
+    Warp w = make_warp(&shs[wib], gw + 1, gw + 17 * d.stamp);
+    for (int c = gw; c < ncells; c += nw) {
+        int cnt = cell_cnt[c];
+        if (cnt == 0) continue;
+        int off = cell_off[c];
+        for (int j = 0; j < cnt; ++j) {
+            if (read_status(d)) break;
+            int3 mv = moves[order[off + j]];
+            int p = mv.x;
+            int s0, s1, hint;
+            int rc = delete_point(w, d, p, s0, s1, hint);
+            if (rc) {
+                if (rc > 0) set_status(d, rc);
+                break;
+            }
+            // Update (Fig. 4): the point is out of the triangulation, move it
+            if (w.lane == 0) {
+                d.xy[p] = make_int2(mv.y, mv.z);
+                __threadfence();
+            }
+            __syncwarp();
+            rc = insert_point(w, d, p, make_int2(mv.y, mv.z), hint, s0, s1, true);
+            if (rc == 1) {
+                if (w.lane == 0) {
+                    int pos = atomicAdd(defer_count, 1);
+                    if (pos < defer_cap) deferred[pos] = make_int4(p, s0, s1, hint);
+                    else atomicCAS(d.status, 0, DEV_CAPACITY);
+                }
+                w.cnt[C_DEFERRED]++;
+                __syncwarp();
+            } else if (rc) {
+                if (rc > 0) set_status(d, rc);
+                break;
+            }
+        }
+    }
+    flush_counters(w, d);
+}
+
+// Deferred insertions: their targets were held by points that moved away later in
+// the step; any coincidence now is a genuine duplicate.
+__global__ void __launch_bounds__(WPB * 32) k_deferred(Dev d, const int4 *deferred, const int *defer_count,
+                                                       int defer_cap)
+{
+    __shared__ WarpShared shs[WPB];
+    int wib = threadIdx.x >> 5;
+    int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+    int nw = gridDim.x * (blockDim.x >> 5);
+    Warp w = make_warp(&shs[wib], gw + 1, gw + 7919 * d.stamp);
+    int cnt = min(*defer_count, defer_cap);
+    for (int j = gw; j < cnt; j += nw) {
+        if (read_status(d)) break;
+        int4 e = deferred[j];
+        int2 q = __ldcg(d.xy + e.x);
+        q = bcast2(q, 0);
+        int rc = insert_point(w, d, e.x, q, e.w, e.y, e.z, false);
+        if (rc) {
+            if (rc > 0) set_status(d, rc);
+            break;
+        }
+    }
+    flush_counters(w, d);
+}
+
+// ------------------------------------------------------------------ hull winding
+
+// 0 for directions with angle in [0, pi), 1 for [pi, 2 pi)
+__device__ __forceinline__ int dir_half(long long dx, long long dy) { return (dy < 0 || (dy == 0 && dx < 0)) ? 1 : 0; }
+
+// is direction a strictly before direction b in counter-clockwise angle from +x?
+__device__ __forceinline__ bool dir_less(long long ax, long long ay, long long bx, long long by)
+{
+    int ha = dir_half(ax, ay), hb = dir_half(bx, by);
+    if (ha != hb) return ha < hb;
+    return ax * by - ay * bx > 0;
+}
+
+// Does the hull turn "wrap" past angle 0 at the vertex between this ghost's hull edge
+// and the next one?  Summed over the hull, a valid triangulation wraps exactly once:
+// with every triangle counter-clockwise and every edge locally Delaunay, the ghost
+// cycle winding once makes the surface a degree-1 cover of the plane, i.e. a
+// triangulation, and then Lawson's lemma makes it the Delaunay triangulation.
+__device__ int hull_wrap(const Dev &d, const int4 &v, const int4 &nb)
+{
+    int g = v.x == KDT_GHOST ? 0 : (v.y == KDT_GHOST ? 1 : (v.z == KDT_GHOST ? 2 : -1));
+    if (g < 0) return 0;
+    int u = comp(v, (g + 1) % 3), vv = comp(v, (g + 2) % 3);  // hull edge vv -> u
+    int4 nv = __ldcg(d.tv + (comp(nb, (g + 2) % 3) >> 2));
+    int ng = nv.x == KDT_GHOST ? 0 : (nv.y == KDT_GHOST ? 1 : (nv.z == KDT_GHOST ? 2 : -1));
+    if (ng < 0) return 100;  // not a ghost: inconsistent
+    int y = comp(nv, (ng + 1) % 3);                            // next hull edge u -> y
+    int2 pu = __ldcg(d.xy + u), pv = __ldcg(d.xy + vv), py = __ldcg(d.xy + y);
+    return dir_less((long long)py.x - pu.x, (long long)py.y - pu.y, (long long)pu.x - pv.x,
+                    (long long)pu.y - pv.y)
+               ? 1
+               : 0;
+}
+
+// ------------------------------------------------------------------ certification
+
+// Is edge e of live triangle t locally Delaunay?  Also checks that the adjacency is
+// reciprocal and the triangle counter-clockwise.  Returns 0 (fine), 1 (not locally
+// Delaunay), -1 (store inconsistent).
+__device__ int check_edge(const Dev &d, int t, const int4 &v, const int4 &nb, int e, unsigned *ex,
+                          unsigned *ti)
+{
+    int ref = comp(nb, e);
+    int U = ref >> 2, f = ref & 3;
+    if (U < 0 || U >= d.cap || f > 2) return -1;
+    int4 uv = __ldcg(d.tv + U);
+    int4 un = __ldcg(d.tn + U);
+    if (!(uv.w & ALIVE) || comp(un, f) != ((t << 2) | e)) return -1;
+    int a = comp(v, (e + 1) % 3), b = comp(v, (e + 2) % 3);
+    if (comp(uv, (f + 1) % 3) != b || comp(uv, (f + 2) % 3) != a) return -1;
+    int dd = comp(uv, f);
+    int2 z = make_int2(0, 0);
+    int2 p0 = v.x >= 0 ? __ldcg(d.xy + v.x) : z;
+    int2 p1 = v.y >= 0 ? __ldcg(d.xy + v.y) : z;
+    int2 p2 = v.z >= 0 ? __ldcg(d.xy + v.z) : z;
+    int2 pd = dd >= 0 ? __ldcg(d.xy + dd) : z;
+    return conflict(v.x, v.y, v.z, p0, p1, p2, dd, pd, d.use_filter, ex, ti) ? 1 : 0;
+}
+
+__device__ void certify_one(const Dev &d, int t, int *viol, int *viol_count, int viol_cap, unsigned *ex,
+                            unsigned *ti)
+{
+    int4 v = __ldcg(d.tv + t);
+    if (!(v.w & ALIVE)) return;
+    int4 nb = __ldcg(d.tn + t);
+    if (v.x >= 0 && v.y >= 0 && v.z >= 0) {
+        if (orient2d(__ldcg(d.xy + v.x), __ldcg(d.xy + v.y), __ldcg(d.xy + v.z)) <= 0) {
+            atomicCAS(d.status, 0, DEV_INTERNAL);
+            return;
+        }
+    }
+    for (int e = 0; e < 3; ++e) {
+        int r = check_edge(d, t, v, nb, e, ex, ti);
+        if (r < 0) {
+            atomicCAS(d.status, 0, DEV_INTERNAL);
+            return;
+        }
+        if (r > 0) {
+            int pos = atomicAdd(viol_count, 1);
+            if (pos < viol_cap) viol[pos] = (t << 2) | e;
+        }
+    }
+}
+
+// certify the dirty slots [lo, *dirty_count) (the slots written in this step)
+__global__ void k_certify(Dev d, int lo, int *viol, int *viol_count, int viol_cap)
+{
+    int hi = *d.dirty_count;
+    if (hi > d.dirty_cap) hi = d.dirty_cap;
+    unsigned ex = 0, ti = 0;
+    for (int i = lo + blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += gridDim.x * blockDim.x)
+        certify_one(d, d.dirty[i], viol, viol_count, viol_cap, &ex, &ti);
+}
+
+// certify every slot (after a build, or when the dirty list overflowed)
+__global__ void k_certify_all(Dev d, int nslots, int *viol, int *viol_count, int viol_cap, int *wraps)
+{
+    unsigned ex = 0, ti = 0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nslots; t += gridDim.x * blockDim.x) {
+        certify_one(d, t, viol, viol_count, viol_cap, &ex, &ti);
+        int4 v = __ldcg(d.tv + t);
+        if ((v.w & ALIVE) && (v.x < 0 || v.y < 0 || v.z < 0)) {
+            int wr = hull_wrap(d, v, __ldcg(d.tn + t));
+            if (wr) atomicAdd(wraps, wr);
+        }
+    }
+}
+
+// Lawson repair of the edges the certification rejected (general flip algorithm:
+// every flip queues the four outer edges of its quadrilateral).
+__global__ void __launch_bounds__(WPB * 32) k_fixup(Dev d, const int *viol, int nviol)
+{
+    __shared__ WarpShared shs[WPB];
+    int wib = threadIdx.x >> 5;
+    int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+    int nw = gridDim.x * (blockDim.x >> 5);
+    Warp w = make_warp(&shs[wib], gw + 1, gw + 31 * d.stamp + 5);
+    for (int j = gw; j < nviol; j += nw) {
+        if (read_status(d)) break;
+        int r = viol[j];
+        if (w.lane == 0) w.sh->stack[0] = make_int2(r >> 2, r & 3);
+        __syncwarp();
+        lawson(w, d, 1, -2, false);
+    }
+    flush_counters(w, d);
+}
+
+// ------------------------------------------------------------------ build
+
+__global__ void k_range(const int2 *xy, int n, int bits, int *status, int *bbox)
+{
+    long long lim = 1ll << bits;
+    int mnx = INT_MAX, mny = INT_MAX, mxx = INT_MIN, mxy = INT_MIN;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int2 p = xy[i];
+        if (p.x < 0 || p.y < 0 || p.x >= lim || p.y >= lim) atomicCAS(status, 0, DEV_RANGE);
+        mnx = min(mnx, p.x);
+        mny = min(mny, p.y);
+        mxx = max(mxx, p.x);
+        mxy = max(mxy, p.y);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mnx = min(mnx, __shfl_xor_sync(FULL, mnx, o));
+        mny = min(mny, __shfl_xor_sync(FULL, mny, o));
+        mxx = max(mxx, __shfl_xor_sync(FULL, mxx, o));
+        mxy = max(mxy, __shfl_xor_sync(FULL, mxy, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(bbox + 0, mnx);
+        atomicMin(bbox + 1, mny);
+        atomicMax(bbox + 2, mxx);
+        atomicMax(bbox + 3, mxy);
+    }
+}
+
+// Hilbert index of cell (x, y) in a 2^k x 2^k grid (the rotate-and-accumulate
+// construction of the Hilbert curve).
+__device__ __forceinline__ unsigned hilbert_d(int k, unsigned x, unsigned y)
+{
+    unsigned nside = 1u << k, dsum = 0;
+    for (unsigned s = nside >> 1; s > 0; s >>= 1) {
+        unsigned rx = (x & s) ? 1u : 0u, ry = (y & s) ? 1u : 0u;
+        dsum += s * s * ((3u * rx) ^ ry);
+        if (ry == 0) {
+            if (rx == 1) {
+                x = nside - 1 - x;
+                y = nside - 1 - y;
+            }
+            unsigned t = x;
+            x = y;
+            y = t;
+        }
+    }
+    return dsum;
+}
+
+__global__ void k_hilbert(const int2 *xy, int n, const int *bbox, int k, int shift, unsigned *key, int *hist)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int2 p = xy[i];
+    unsigned cx = (unsigned)(p.x - bbox[0]) >> shift, cy = (unsigned)(p.y - bbox[1]) >> shift;
+    unsigned lim = (1u << k) - 1;
+    cx = min(cx, lim);
+    cy = min(cy, lim);
+    unsigned h = hilbert_d(k, cx, cy);
+    key[i] = h;
+    atomicAdd(hist + h, 1);
+}
+
+__global__ void k_place_order(int n, const unsigned *key, const int *off, int *fill, int *order)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned h = key[i];
+    order[off[h] + atomicAdd(fill + h, 1)] = i;
+}
+
+// first j >= 2 with orient(order[0], order[1], order[j]) != 0
+__global__ void k_third(const int2 *xy, int n, const int *order, int *third)
+{
+    int2 a = xy[order[0]], b = xy[order[1]];
+    for (int j = 2 + blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        if (orient2d(a, b, xy[order[j]]) != 0) atomicMin(third, j);
+}
+
+// The first triangle (a, b, c) and its three ghosts (c,b,inf), (a,c,inf), (b,a,inf).
+__global__ void k_init(Dev d, const int *order, const int *third, int *tri_count)
+{
+    int a = order[0], b = order[1], c = order[*third];
+    if (orient2d(d.xy[a], d.xy[b], d.xy[c]) < 0) {
+        int t = b;
+        b = c;
+        c = t;
+    }
+    const int G = KDT_GHOST;
+    d.tv[0] = make_int4(a, b, c, ALIVE);
+    d.tn[0] = make_int4((1 << 2) | 2, (2 << 2) | 2, (3 << 2) | 2, 0);
+    d.tv[1] = make_int4(c, b, G, ALIVE);
+    d.tn[1] = make_int4((3 << 2) | 1, (2 << 2) | 0, (0 << 2) | 0, 0);
+    d.tv[2] = make_int4(a, c, G, ALIVE);
+    d.tn[2] = make_int4((1 << 2) | 1, (3 << 2) | 0, (0 << 2) | 1, 0);
+    d.tv[3] = make_int4(b, a, G, ALIVE);
+    d.tn[3] = make_int4((2 << 2) | 1, (1 << 2) | 0, (0 << 2) | 2, 0);
+    d.pt_tri[a] = 0;
+    d.pt_tri[b] = 0;
+    d.pt_tri[c] = 0;
+    *tri_count = 4;
+}
+
+// Insert the points at sorted positions (2j+1) * 2^level, each starting its walk at
+// the triangle of its Hilbert predecessor (2j) * 2^level, already inserted.
+__global__ void __launch_bounds__(WPB * 32) k_insert_level(Dev d, const int *order, int level, int items,
+                                                           int *tri_count)
+{
+    __shared__ WarpShared shs[WPB];
+    int wib = threadIdx.x >> 5;
+    int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+    int nw = gridDim.x * (blockDim.x >> 5);
+    Warp w = make_warp(&shs[wib], gw + 1, gw * 7 + level * 1315423911u);
+    for (int j = gw; j < items; j += nw) {
+        if (read_status(d)) break;
+        long long i = ((long long)(2 * j + 1)) << level;
+        if (i >= d.n) continue;
+        int v = order[i];
+        if (__shfl_sync(FULL, __ldcg(d.pt_tri + v), 0) >= 0) continue;  // one of the first three
+        int parent = order[i - (1ll << level)];
+        int start = __shfl_sync(FULL, __ldcg(d.pt_tri + parent), 0);
+        if (start < 0) start = 0;
+        int s = 0;
+        if (w.lane == 0) s = atomicAdd(tri_count, 2);
+        s = __shfl_sync(FULL, s, 0);
+        if (s + 1 >= d.cap) {
+            set_status(d, DEV_INTERNAL);
+            break;
+        }
+        int2 q = d.xy[v];
+        int rc = insert_point(w, d, v, q, start, s, s + 1, false);
+        if (rc) {
+            if (rc > 0) set_status(d, rc);
+            break;
+        }
+    }
+    flush_counters(w, d);
+}
+
+// ------------------------------------------------------------------ export
+
+__device__ __forceinline__ bool finite_alive(const int4 &v)
+{
+    return (v.w & ALIVE) && v.x >= 0 && v.y >= 0 && v.z >= 0;
+}
+
+__global__ void k_exp_count(const int4 *tv, int nslots, int *cnt)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nslots; t += gridDim.x * blockDim.x) {
+        int4 v = tv[t];
+        if (!finite_alive(v)) continue;
+        atomicAdd(cnt + min(v.x, min(v.y, v.z)), 1);
+    }
+}
+
+// rotate so the smallest id comes first (keeps the counter-clockwise order)
+__global__ void k_exp_place(const int4 *tv, int nslots, const int *off, int *fill, int3 *out)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nslots; t += gridDim.x * blockDim.x) {
+        int4 v = tv[t];
+        if (!finite_alive(v)) continue;
+        int3 r;
+        if (v.x < v.y && v.x < v.z) r = make_int3(v.x, v.y, v.z);
+        else if (v.y < v.z) r = make_int3(v.y, v.z, v.x);
+        else r = make_int3(v.z, v.x, v.y);
+        out[off[r.x] + atomicAdd(fill + r.x, 1)] = r;
+    }
+}
+
+// sort each first-vertex segment by (second, third): segments are short (<= degree)
+__global__ void k_exp_sortseg(int n, const int *off, const int *cnt, int3 *out)
+{
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
+        int c = cnt[a];
+        if (c < 2) continue;
+        int3 *s = out + off[a];
+        for (int i = 1; i < c; ++i) {
+            int3 x = s[i];
+            int j = i - 1;
+            while (j >= 0 && (s[j].y > x.y || (s[j].y == x.y && s[j].z > x.z))) {
+                s[j + 1] = s[j];
+                --j;
+            }
+            s[j + 1] = x;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ verifier
+
+__global__ void k_verify(Dev d, int nslots, int *bad, int *alive, int *wraps)
+{
+    unsigned ex = 0, ti = 0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nslots; t += gridDim.x * blockDim.x) {
+        int4 v = __ldcg(d.tv + t);
+        if (!(v.w & ALIVE)) continue;
+        atomicAdd(alive, 1);
+        int4 nb = __ldcg(d.tn + t);
+        int ghosts = (v.x < 0) + (v.y < 0) + (v.z < 0);
+        if (ghosts > 1 || (v.x == v.y || v.y == v.z || v.x == v.z)) {
+            atomicAdd(bad, 1);
+            continue;
+        }
+        if (ghosts == 0 && orient2d(d.xy[v.x], d.xy[v.y], d.xy[v.z]) <= 0) atomicAdd(bad, 1);
+        if (nb.w != 0) atomicAdd(bad, 1);  // a claim left behind
+        for (int e = 0; e < 3; ++e)
+            if (check_edge(d, t, v, nb, e, &ex, &ti) != 0) atomicAdd(bad, 1);
+        if (ghosts == 1) {
+            int wr = hull_wrap(d, v, nb);
+            if (wr) atomicAdd(wraps, wr);
+        }
+    }
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < d.n; p += gridDim.x * blockDim.x) {
+        int t = d.pt_tri[p];
+        if (t < 0 || t >= nslots) {
+            atomicAdd(bad, 1);
+            continue;
+        }
+        int4 v = d.tv[t];
+        if (!(v.w & ALIVE) || (v.x != p && v.y != p && v.z != p)) atomicAdd(bad, 1);
+    }
+}
+
+// ------------------------------------------------------------------ misc
+
+__global__ void k_set_positions(int2 *xy, const int3 *moves, int m)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) xy[moves[i].x] = make_int2(moves[i].y, moves[i].z);
+}
+
+__global__ void k_restore_positions(int2 *xy, const int3 *moves, const int2 *old_xy, int m)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) xy[moves[i].x] = old_xy[i];
+}
+
+__global__ void k_fill_int(int *p, int n, int v)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
+}
+
+__global__ void k_predicates(const int2 *xy, const int4 *quads, int m, int4 *out, int use_filter)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int4 q = quads[i];
+    int2 a = xy[q.x], b = xy[q.y], c = xy[q.z], dd = xy[q.w];
+    unsigned ex = 0, ti = 0;
+    out[i] = make_int4(orient2d(a, b, c), incircle_exact(a, b, c, dd), incircle_filter(a, b, c, dd),
+                       incircle_sos(q.x, q.y, q.z, q.w, a, b, c, dd, use_filter != 0, &ex, &ti));
+}
+
+}  // namespace kd

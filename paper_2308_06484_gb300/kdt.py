@@ -1,0 +1,227 @@
+"""Python binding of libkdt.so (argument marshalling only).
+
+Every step of the method runs in the CUDA library behind the C ABI declared in
+include/kdt.h; this module only converts arrays to pointers and codes to
+exceptions.  There is no fallback: if the library cannot be loaded, importing
+anything that needs it raises.
+
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA); they must be
+int32 and C-contiguous.  PyTorch is used only for device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+KDT_OK = 0
+ERRORS = {
+    -1: "KDT_ERR_ARG", -2: "KDT_ERR_RANGE", -3: "KDT_ERR_DUPLICATE", -4: "KDT_ERR_DEGENERATE",
+    -5: "KDT_ERR_CAPACITY", -6: "KDT_ERR_RETRY_EXHAUSTED", -7: "KDT_ERR_CUDA",
+    -8: "KDT_ERR_INTERNAL", -9: "KDT_ERR_STATE",
+}
+
+
+class KDTError(RuntimeError):
+    def __init__(self, code, where=""):
+        super().__init__("%s: %s (%d)" % (where, ERRORS.get(code, "?"), code))
+        self.code = code
+        self.name = ERRORS.get(code, "?")
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_int32), ("domain_bits", ctypes.c_int32),
+                ("retry_cap", ctypes.c_int32), ("fallback", ctypes.c_int32),
+                ("rebuild_ratio", ctypes.c_float), ("filter", ctypes.c_int32),
+                ("verify", ctypes.c_int32), ("timing", ctypes.c_int32),
+                ("warps_per_block", ctypes.c_int32), ("build_warps", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+_STAT_FIELDS = ["steps", "moves", "rebuilds", "fallbacks", "kernel_launches", "flips", "retries",
+                "walk_steps", "exact_incircle", "sos_ties", "deferred", "violations", "fixup_flips",
+                "deleted_degree_sum", "stack_drops", "edge_splits", "ghost_splits", "deletes",
+                "inserts", "flip_tests"]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = ([(f, ctypes.c_int64) for f in _STAT_FIELDS]
+                + [("kinetic_kernel_ms", ctypes.c_double), ("kinetic_kernel_timed", ctypes.c_int64),
+                   ("reserved", ctypes.c_int64 * 8)])
+
+
+_lib = None
+
+# every symbol include/kdt.h declares (checked by the loader test)
+SYMBOLS = ["kdt_default_config", "kdt_create", "kdt_destroy", "kdt_build", "kdt_step",
+           "kdt_rebuild", "kdt_export_triangles", "kdt_export_points", "kdt_verify",
+           "kdt_num_points", "kdt_get_stats", "kdt_reset_stats", "kdt_error_string",
+           "kdt_version", "kdt_eval_predicates"]
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load(build_if_stale: bool = True):
+    """Load libkdt.so (compiling it first when sources are newer and nvcc exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_stale and _build.stale():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("libkdt.so is missing; run __graft_entry__.build()")
+    L = ctypes.CDLL(_build.LIB)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    L.kdt_default_config.argtypes = [ctypes.POINTER(Config)]
+    L.kdt_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Config), i32, vp]
+    L.kdt_destroy.argtypes = [vp]
+    L.kdt_build.argtypes = [vp, vp, i64]
+    L.kdt_step.argtypes = [vp, vp, i64]
+    L.kdt_rebuild.argtypes = [vp]
+    L.kdt_export_triangles.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
+    L.kdt_export_points.argtypes = [vp, vp, i64]
+    L.kdt_verify.argtypes = [vp, ctypes.POINTER(i64)]
+    L.kdt_num_points.argtypes = [vp]
+    L.kdt_num_points.restype = i64
+    L.kdt_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+    L.kdt_reset_stats.argtypes = [vp]
+    L.kdt_error_string.argtypes = [i32]
+    L.kdt_error_string.restype = ctypes.c_char_p
+    L.kdt_version.restype = i32
+    L.kdt_eval_predicates.argtypes = [vp, vp, i64, vp, i32, vp]
+    for s in SYMBOLS:
+        getattr(L, s)
+    _lib = L
+    return L
+
+
+def _ptr(a, nd_last=None):
+    """(pointer, n_rows) of an int32 C-contiguous numpy array or torch tensor."""
+    if a is None:
+        return None, 0
+    if hasattr(a, "data_ptr"):  # torch tensor
+        import torch
+        if a.dtype != torch.int32 or not a.is_contiguous():
+            raise ValueError("expected a contiguous int32 tensor")
+        return ctypes.c_void_p(a.data_ptr()), a.shape[0] if a.dim() else 0
+    if not isinstance(a, np.ndarray) or a.dtype != np.int32 or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("expected a C-contiguous int32 numpy array")
+    return ctypes.c_void_p(a.ctypes.data), a.shape[0] if a.ndim else 0
+
+
+def _check(rc, where):
+    if rc != KDT_OK:
+        raise KDTError(rc, where)
+
+
+def default_config(**kw) -> Config:
+    c = Config()
+    load().kdt_default_config(ctypes.byref(c))
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+class Triangulation:
+    """One kinetic Delaunay triangulation on one GPU (a kdt handle)."""
+
+    def __init__(self, config: Config | None = None, device: int = 0, stream=None, **kw):
+        self.L = load()
+        if config is None:
+            config = default_config(**kw)
+        self.config = config
+        h = ctypes.c_void_p()
+        _check(self.L.kdt_create(ctypes.byref(h), ctypes.byref(config), device,
+                                 _stream_handle(stream)), "kdt_create")
+        self.h = h
+
+    # lifecycle
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.L.kdt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # the method
+    def build(self, xy):
+        p, n = _ptr(xy)
+        _check(self.L.kdt_build(self.h, p, n), "kdt_build")
+
+    def step(self, moves):
+        p, m = _ptr(moves)
+        _check(self.L.kdt_step(self.h, p, m), "kdt_step")
+
+    def rebuild(self):
+        _check(self.L.kdt_rebuild(self.h), "kdt_rebuild")
+
+    @property
+    def n(self):
+        return int(self.L.kdt_num_points(self.h))
+
+    def export_triangles(self, out=None):
+        """Canonical sorted (T, 3) triangle list; into `out` (numpy / torch) if given."""
+        nt = ctypes.c_int64(0)
+        if out is None:
+            rc = self.L.kdt_export_triangles(self.h, None, 0, ctypes.byref(nt))
+            if rc not in (KDT_OK, -5):
+                _check(rc, "kdt_export_triangles")
+            out = np.empty((nt.value, 3), dtype=np.int32)
+        p, cap = _ptr(out)
+        _check(self.L.kdt_export_triangles(self.h, p, cap, ctypes.byref(nt)), "kdt_export_triangles")
+        return out[: nt.value]
+
+    def export_points(self):
+        out = np.empty((self.n, 2), dtype=np.int32)
+        p, cap = _ptr(out)
+        _check(self.L.kdt_export_points(self.h, p, cap), "kdt_export_points")
+        return out
+
+    def verify(self) -> int:
+        bad = ctypes.c_int64(0)
+        _check(self.L.kdt_verify(self.h, ctypes.byref(bad)), "kdt_verify")
+        return int(bad.value)
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(self.L.kdt_get_stats(self.h, ctypes.byref(s)), "kdt_get_stats")
+        d = {f: int(getattr(s, f)) for f in _STAT_FIELDS}
+        d["kinetic_kernel_ms"] = float(s.kinetic_kernel_ms)
+        d["kinetic_kernel_timed"] = int(s.kinetic_kernel_timed)
+        return d
+
+    def reset_stats(self):
+        _check(self.L.kdt_reset_stats(self.h), "kdt_reset_stats")
+
+
+def eval_predicates(xy_dev, quads_dev, out_dev, use_filter: bool = True, stream=None):
+    """Device predicates on (a,b,c,d) rows: orient, exact incircle, filter verdict, SoS."""
+    L = load()
+    px, _ = _ptr(xy_dev)
+    pq, m = _ptr(quads_dev)
+    po, _ = _ptr(out_dev)
+    _check(L.kdt_eval_predicates(px, pq, m, po, int(use_filter), _stream_handle(stream)),
+           "kdt_eval_predicates")
