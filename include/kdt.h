@@ -78,7 +78,10 @@ typedef struct {
     int32_t timing;        /* 1: time the kinetic kernel with CUDA events (kdt_stats)       */
     int32_t warps_per_block; /* kinetic kernel launch shape (default 4)                      */
     int32_t build_warps;   /* warps inserting concurrently during a build (0 = auto)         */
-    int32_t reserved[6];
+    int32_t kinetic_warps; /* warps moving points concurrently in a step (0 = one per cell)  */
+    int32_t debug;         /* bit 0: on an in-step failure keep the failed state (no
+                              fallback, no roll-back) so kdt_export_store can inspect it     */
+    int32_t reserved[4];
 } kdt_config;
 
 /* Counters since creation (or kdt_reset_stats). */
@@ -89,7 +92,9 @@ typedef struct {
     int64_t ghost_splits, deletes, inserts, flip_tests;
     double kinetic_kernel_ms; /* sum of event-timed kinetic kernel durations (timing = 1) */
     int64_t kinetic_kernel_timed; /* launches included in kinetic_kernel_ms               */
-    int64_t reserved[8];
+    int64_t last_fallback_reason; /* internal status that triggered the last fallback     */
+    int64_t last_fallback_point;  /* point whose operation reported it (-1 if unknown)     */
+    int64_t reserved[6];
 } kdt_stats;
 
 /* ---- lifecycle ------------------------------------------------------------------ */
@@ -157,6 +162,11 @@ const char *kdt_error_string(int code);
 int kdt_version(void);
 
 /* ---- diagnostics ---------------------------------------------------------------- */
+
+/* Copy the raw triangle store into host buffers (diagnostics): tv and tn receive
+ * 4 int32 per slot (cap_slots >= 2n - 2; see the store layout in the design notes),
+ * pt_tri n int32.  Any pointer may be NULL to skip it. */
+int kdt_export_store(kdt *h, int32_t *tv, int32_t *tn, int32_t *pt_tri, int64_t cap_slots);
 
 /* Evaluate the device predicates on m quadruples of point indices (Section I,
  * empty-circumcircle test).  xy: device, 2 int32 per point; quads: device, 4 int32

@@ -199,6 +199,7 @@ int thread_grid(kdt *h, long long items, int threads)
 int certify_and_repair(kdt *h, bool all, int *dev_status)
 {
     Dev d = make_dev(h);
+    if (all && d.retry_cap < 4096) d.retry_cap = 4096;
     bool full = all;
     int lo = 0;
     for (int round = 0; round < 64; ++round) {
@@ -249,6 +250,7 @@ int rebuild_positions(kdt *h)
     h->stamp++;
     Dev d = make_dev(h);
     d.dirty_cap = 0;  // the build certifies every slot instead
+    if (d.retry_cap < 4096) d.retry_cap = 4096;  // the step's cap does not apply to builds
     CK(cudaMemsetAsync(h->scal, 0, S_NUM * sizeof(int), st));
     int init_bbox[4] = {INT_MAX, INT_MAX, INT_MIN, INT_MIN};
     CK(cudaMemcpyAsync(h->scal + S_MINX, init_bbox, sizeof init_bbox, cudaMemcpyHostToDevice, st));
@@ -578,7 +580,12 @@ int kdt_step(kdt *h, const kdt_move *moves, int64_t m)
     k_scatter<<<(mi + 255) / 256, 256, 0, st>>>(mi, h->move_cell, h->cell_off, h->cell_fill, h->order,
                                                 h->scal + S_STATUS);
     if (h->cfg.timing) CK(cudaEventRecord(h->ev0, st));
-    k_kinetic<<<warp_grid(h, h->ncells, 64), WPB * 32, 0, st>>>(d, h->moves, h->order, h->cell_cnt, h->cell_off,
+    int kblocks = warp_grid(h, h->ncells, 64), kthreads = WPB * 32;
+    if (h->cfg.kinetic_warps > 0) {
+        kblocks = (h->cfg.kinetic_warps + WPB - 1) / WPB;
+        if (h->cfg.kinetic_warps < WPB) kthreads = 32 * h->cfg.kinetic_warps;
+    }
+    k_kinetic<<<kblocks, kthreads, 0, st>>>(d, h->moves, h->order, h->cell_cnt, h->cell_off,
                                                                 h->ncells, h->deferred, h->scal + S_DEFER,
                                                                 h->mcap);
     if (h->cfg.timing) CK(cudaEventRecord(h->ev1, st));
@@ -657,6 +664,13 @@ int kdt_step(kdt *h, const kdt_move *moves, int64_t m)
         // the step failed while running: finish it by a full rebuild of the final
         // positions (the certified fallback); if those are invalid, roll back
         h->stats.fallbacks++;
+        h->stats.last_fallback_reason = s;
+        h->stats.last_fallback_point = h->hscal[S_FAILPT];
+        if (h->cfg.debug & 1) {
+            h->built = true;  // keep the failed state for kdt_export_store
+            add_counters(h);
+            return dev_to_abi(s);
+        }
         bool allow = h->cfg.fallback || s == DEV_DUPLICATE || s == DEV_DEGENERATE;
         int rc2 = KDT_ERR_RETRY_EXHAUSTED;
         if (allow) {
@@ -754,6 +768,19 @@ int kdt_reset_stats(kdt *h)
 {
     if (!h) return KDT_ERR_ARG;
     memset(&h->stats, 0, sizeof h->stats);
+    return KDT_OK;
+}
+
+int kdt_export_store(kdt *h, int32_t *tv, int32_t *tn, int32_t *pt_tri, int64_t cap_slots)
+{
+    if (!h || cap_slots < 0) return KDT_ERR_ARG;
+    if (h->n == 0) return KDT_ERR_STATE;
+    if (cap_slots < h->cap) return KDT_ERR_CAPACITY;
+    CK(cudaSetDevice(h->device));
+    CK(cudaStreamSynchronize(h->stream));
+    if (tv) CK(cudaMemcpy(tv, h->tv, (size_t)h->cap * sizeof(int4), cudaMemcpyDeviceToHost));
+    if (tn) CK(cudaMemcpy(tn, h->tn, (size_t)h->cap * sizeof(int4), cudaMemcpyDeviceToHost));
+    if (pt_tri) CK(cudaMemcpy(pt_tri, h->pt_tri, (size_t)h->n * sizeof(int), cudaMemcpyDeviceToHost));
     return KDT_OK;
 }
 

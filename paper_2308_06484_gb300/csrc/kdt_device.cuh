@@ -30,7 +30,7 @@ constexpr int KMAX = 64;               // largest vertex degree a deletion handl
 constexpr int MAXC = 2 * KMAX + 16;    // claims one warp may hold
 constexpr int STACK = 96;              // Lawson flip stack per warp
 constexpr int WALK_CAP = 1 << 12;      // steps before a walk restarts
-constexpr int WALK_RESTARTS = 64;      // restarts before point location gives up
+constexpr int WALK_RESTARTS = 1024;    // restarts before point location gives up
 constexpr int ALIVE = 1;
 
 // device status codes (first error wins); mapped to the C-ABI codes on the host
@@ -454,7 +454,7 @@ __device__ int insert_outside(Warp &w, const Dev &d, int p, int2 q, int V0, int 
     // backward neighbour (hull edge ending at v): edge index g+1; forward (from u): g+2.
     int cur = V0, eb_ref = -1;
     for (int s = 0;; ++s) {
-        if (s > KCH) return DEV_CAPACITY;
+        if (s > KCH) return 1;  // a transient loop, or a chain longer than KCH (retry budget decides)
         int4 v, nb;
         load_tri(w, d, cur, v, nb);
         int g = v.x == KDT_GHOST ? 0 : (v.y == KDT_GHOST ? 1 : (v.z == KDT_GHOST ? 2 : -1));
@@ -475,7 +475,7 @@ __device__ int insert_outside(Warp &w, const Dev &d, int p, int2 q, int V0, int 
     // forward from the first visible ghost, recording the chain in ccw order
     int k = 0, ef_ref = -1;
     while (true) {
-        if (k >= KCH) return DEV_CAPACITY;
+        if (k >= KCH) return 1;
         int4 v, nb;
         load_tri(w, d, cur, v, nb);
         int g = v.x == KDT_GHOST ? 0 : (v.y == KDT_GHOST ? 1 : (v.z == KDT_GHOST ? 2 : -1));
@@ -781,8 +781,11 @@ __device__ int delete_point(Warp &w, const Dev &d, int p, int &spare0, int &spar
     for (int attempt = 0;; ++attempt) {
         if (attempt > d.retry_cap) return DEV_RETRY;
         if (read_status(d)) return -1;
+        // an unclaimed walk around p can run round a transient loop while another warp
+        // is writing p's triangles: treat every failed gather as contention, and report
+        // a real degree overflow only when it persists for the whole retry budget
         int k = gather_star(w, d, p);
-        if (k == -2 && attempt >= 3) return DEV_DEGREE;
+        if (k == -2 && attempt == d.retry_cap) return DEV_DEGREE;
         if (k < 3) {
             backoff(w, attempt);
             continue;

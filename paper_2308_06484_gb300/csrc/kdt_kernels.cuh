@@ -17,7 +17,7 @@ constexpr int DEV_DUP_ID = 10;  // a move id repeated within one step (found at 
 enum Slot : int {
     S_STATUS = 0, S_DIRTY = 1, S_VIOL = 2, S_TRIS = 3, S_DEFER = 4, S_THIRD = 5,
     S_MINX = 6, S_MINY = 7, S_MAXX = 8, S_MAXY = 9, S_TOTAL = 10, S_BAD = 11, S_ALIVE = 12,
-    S_WRAPS = 13, S_NUM = 16
+    S_WRAPS = 13, S_FAILPT = 14, S_NUM = 16
 };
 
 __device__ __forceinline__ Warp make_warp(WarpShared *sh, int token, unsigned seed)
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(WPB * 32) k_kinetic(Dev d, const int3 *moves, 
             int s0, s1, hint;
             int rc = delete_point(w, d, p, s0, s1, hint);
             if (rc) {
-                if (rc > 0) set_status(d, rc);
+                if (rc > 0 && w.lane == 0 && atomicCAS(d.status, 0, rc) == 0) d.status[S_FAILPT] = p;
                 break;
             }
             // Update (Fig. 4): the point is out of the triangulation, move it
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(WPB * 32) k_kinetic(Dev d, const int3 *moves, 
                 w.cnt[C_DEFERRED]++;
                 __syncwarp();
             } else if (rc) {
-                if (rc > 0) set_status(d, rc);
+                if (rc > 0 && w.lane == 0 && atomicCAS(d.status, 0, rc) == 0) d.status[S_FAILPT] = p;
                 break;
             }
         }

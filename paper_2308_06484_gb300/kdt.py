@@ -38,7 +38,8 @@ class Config(ctypes.Structure):
                 ("rebuild_ratio", ctypes.c_float), ("filter", ctypes.c_int32),
                 ("verify", ctypes.c_int32), ("timing", ctypes.c_int32),
                 ("warps_per_block", ctypes.c_int32), ("build_warps", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("kinetic_warps", ctypes.c_int32), ("debug", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 _STAT_FIELDS = ["steps", "moves", "rebuilds", "fallbacks", "kernel_launches", "flips", "retries",
@@ -50,7 +51,8 @@ _STAT_FIELDS = ["steps", "moves", "rebuilds", "fallbacks", "kernel_launches", "f
 class Stats(ctypes.Structure):
     _fields_ = ([(f, ctypes.c_int64) for f in _STAT_FIELDS]
                 + [("kinetic_kernel_ms", ctypes.c_double), ("kinetic_kernel_timed", ctypes.c_int64),
-                   ("reserved", ctypes.c_int64 * 8)])
+                   ("last_fallback_reason", ctypes.c_int64), ("last_fallback_point", ctypes.c_int64),
+                   ("reserved", ctypes.c_int64 * 6)])
 
 
 _lib = None
@@ -59,7 +61,7 @@ _lib = None
 SYMBOLS = ["kdt_default_config", "kdt_create", "kdt_destroy", "kdt_build", "kdt_step",
            "kdt_rebuild", "kdt_export_triangles", "kdt_export_points", "kdt_verify",
            "kdt_num_points", "kdt_get_stats", "kdt_reset_stats", "kdt_error_string",
-           "kdt_version", "kdt_eval_predicates"]
+           "kdt_version", "kdt_eval_predicates", "kdt_export_store"]
 
 
 def lib_path():
@@ -94,6 +96,7 @@ def load(build_if_stale: bool = True):
     L.kdt_error_string.restype = ctypes.c_char_p
     L.kdt_version.restype = i32
     L.kdt_eval_predicates.argtypes = [vp, vp, i64, vp, i32, vp]
+    L.kdt_export_store.argtypes = [vp, vp, vp, vp, i64]
     for s in SYMBOLS:
         getattr(L, s)
     _lib = L
@@ -169,6 +172,7 @@ class Triangulation:
     # the method
     def build(self, xy):
         p, n = _ptr(xy)
+        self._n_hint = n
         _check(self.L.kdt_build(self.h, p, n), "kdt_build")
 
     def step(self, moves):
@@ -205,12 +209,27 @@ class Triangulation:
         _check(self.L.kdt_verify(self.h, ctypes.byref(bad)), "kdt_verify")
         return int(bad.value)
 
+    def export_store(self):
+        """(tv, tn, pt_tri) raw arrays of the triangle store (diagnostics)."""
+        n = self.L.kdt_num_points(self.h)
+        if n == 0:
+            n = self._n_hint
+        cap = 2 * n - 2
+        tv = np.empty((cap, 4), dtype=np.int32)
+        tn = np.empty((cap, 4), dtype=np.int32)
+        pt = np.empty(n, dtype=np.int32)
+        _check(self.L.kdt_export_store(self.h, ctypes.c_void_p(tv.ctypes.data), ctypes.c_void_p(tn.ctypes.data),
+                                       ctypes.c_void_p(pt.ctypes.data), cap), "kdt_export_store")
+        return tv, tn, pt
+
     def stats(self) -> dict:
         s = Stats()
         _check(self.L.kdt_get_stats(self.h, ctypes.byref(s)), "kdt_get_stats")
         d = {f: int(getattr(s, f)) for f in _STAT_FIELDS}
         d["kinetic_kernel_ms"] = float(s.kinetic_kernel_ms)
         d["kinetic_kernel_timed"] = int(s.kinetic_kernel_timed)
+        d["last_fallback_reason"] = int(s.last_fallback_reason)
+        d["last_fallback_point"] = int(s.last_fallback_point)
         return d
 
     def reset_stats(self):
