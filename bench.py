@@ -1,0 +1,348 @@
+"""Benchmark: moved-point updates per second of the kinetic Delaunay step.
+
+Workload (the configuration the headline metric is quoted on): 1,000,000 distinct
+integer points uniform on [0, 2^24)^2, 64 x 64 equal-area partitions, one moved point
+per partition per step (4,096 moves), each move 1-8 units right/left/up/down,
+synthetic and seeded.  A step is one call of kdt_step: bucket the moves per
+partition, delete + re-insert each moved point, certify the touched triangles.
+
+Printed JSON line (rank 0):
+  value      updates/s with the moves already resident in HBM (CUDA events around
+             every step, L2 flushed between steps: the 72 MB store fits in L2);
+  e2e        the same metric through the C ABI with the moves in pinned host memory
+             (host->device copy and the status read inside the timed region);
+  roofline   the kinetic kernel's algorithmic bytes (688 B per update) / its
+             event-timed duration, against the measured HBM copy bandwidth;
+  comparators  the GPU full rebuild per step, on the same GB300;
+  cpu_baseline the CPU oracle (a Bowyer-Watson rebuild per step) on the host cores.
+
+--impl reference times the oracle alone (the deliberately slow reference).
+Under torchrun (N > 1) every rank advances its own independent instance (replicas;
+"weak" scaling) and value = all ranks' updates / max-over-ranks time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+BYTES_PER_UPDATE = 688  # star triangles 32*(k_old+k_new) + back-pointers 16*(k_old+k_new) + coords 8*(k_old+k_new+2), k = 6
+METRIC = "moved-point updates/sec (1 GB300, bit-exact) vs plain GPU update and full rebuild"
+WORKLOAD = ("1e6 uniform points on [0,2^24)^2, 64x64 partitions, 4096 moves/step "
+            "(1 per partition, 1-8 units R/L/U/D)")
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def aggregate(local_updates, local_seconds, local_e2e_seconds, group=None):
+    """Whole-job numbers: sum of updates over ranks, max of times over ranks."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized():
+        return local_updates, local_seconds, local_e2e_seconds
+    dev = "cuda" if dist.get_backend(group) == "nccl" else "cpu"
+    u = torch.tensor([float(local_updates)], dtype=torch.float64, device=dev)
+    t = torch.tensor([float(local_seconds), float(local_e2e_seconds)], dtype=torch.float64, device=dev)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM, group=group)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    return float(u.item()), float(t[0].item()), float(t[1].item())
+
+
+def oracle_baseline(snapshots, moves_per_step, threads):
+    """Time the oracle (rebuild from scratch) on `threads` step snapshots in parallel."""
+    import oracle
+    oracle.lib()
+    t0 = time.perf_counter()
+    out = [None] * len(snapshots)
+
+    def run(i):
+        out[i] = oracle.delaunay(snapshots[i]).shape[0]
+
+    ths = [threading.Thread(target=run, args=(i,)) for i in range(len(snapshots))]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    dt = time.perf_counter() - t0
+    return len(snapshots) * moves_per_step / dt, dt
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    """--impl reference: the oracle as it stands, on the host cores."""
+    ws, rank, _ = dist_info()
+    if ws > 1 and rank != 0:
+        return
+    from paper_2308_06484_gb300 import workloads as W
+    w = W.c2(n=args.n, grid=args.grid)
+    threads = max(1, min(host_cores(), 16, args.ref_threads))
+    steps_times = []
+    total_moves = 0
+    for s in range(args.warmup + args.steps):
+        snaps = []
+        for _ in range(threads):
+            mv = w.next_moves()
+            snaps.append(w.positions)
+        ups, dt = oracle_baseline(snaps, mv.shape[0], threads)
+        if s >= args.warmup:
+            steps_times.append(dt)
+            total_moves += threads * mv.shape[0]
+    tot = sum(steps_times)
+    value = total_moves / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "updates/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * tot / max(1, args.steps * threads),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64+int128 exact", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": args.n, "grid": args.grid},
+        "cpu_baseline": {"value": value, "unit": "updates/s", "cores": threads, "kind": "oracle",
+                         "sample": "%d steps x %d parallel oracle rebuilds of the %d-point set" %
+                                   (args.steps, threads, args.n)},
+        "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--grid", type=int, default=64)
+    ap.add_argument("--rebuild-steps", type=int, default=5)
+    ap.add_argument("--cpu-threads", type=int, default=4)
+    ap.add_argument("--ref-threads", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--check", action="store_true", help="compare the final state with the oracle")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2308_06484_gb300 import kdt, workloads as W
+
+    ws, rank, local = dist_info()
+    if ws > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    # workload: every rank its own seeded instance
+    w = W.c2(n=args.n, grid=args.grid, seed=2 + 1000 * rank)
+    xy0 = w.positions
+    nsteps = args.warmup + args.steps
+    moves = [w.next_moves() for _ in range(nsteps)]
+    m = moves[0].shape[0]
+    d_moves = [torch.from_numpy(mv).to(dev) for mv in moves]
+    h_moves = [torch.from_numpy(mv).pin_memory() for mv in moves]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    cfg = kdt.default_config(grid=args.grid, domain_bits=24, timing=1)
+    tri = kdt.Triangulation(cfg, device=local)
+    tri.build(torch.from_numpy(xy0).to(dev))
+
+    # ---- value: device-resident moves
+    for i in range(args.warmup):
+        tri.step(d_moves[i])
+    tri.reset_stats()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        i = args.warmup + k
+        ev[k][0].record()
+        tri.step(d_moves[i])
+        ev[k][1].record()
+        flush.zero_()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    st = tri.stats()
+    local_sec = sum(step_ms) / 1000.0
+    local_updates = st["moves"]
+    launches = st["kernel_launches"]
+    kin_ms = st["kinetic_kernel_ms"] / max(1, st["kinetic_kernel_timed"])
+    fallbacks = st["fallbacks"]
+    final_xy = w.positions.copy()
+
+    # ---- e2e: host (pinned) moves through the C ABI, on a fresh instance of the same workload
+    w2 = W.c2(n=args.n, grid=args.grid, seed=2 + 1000 * rank)
+    tri2 = kdt.Triangulation(kdt.default_config(grid=args.grid, domain_bits=24), device=local)
+    tri2.build(torch.from_numpy(w2.positions).to(dev))
+    for i in range(args.warmup):
+        tri2.step(h_moves[i])
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        i = args.warmup + k
+        ev2[k][0].record()
+        tri2.step(h_moves[i])
+        ev2[k][1].record()
+        flush.zero_()
+    torch.cuda.synchronize()
+    e2e_sec = sum(a.elapsed_time(b) for a, b in ev2) / 1000.0
+    tri2.close()
+
+    # ---- comparator: GPU full rebuild of the same point set per step
+    tri.reset_stats()
+    evr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.rebuild_steps)]
+    for k in range(args.rebuild_steps):
+        evr[k][0].record()
+        tri.rebuild()
+        evr[k][1].record()
+        flush.zero_()
+    torch.cuda.synchronize()
+    rebuild_ms = statistics.median(a.elapsed_time(b) for a, b in evr)
+
+    check = None
+    if args.check:
+        import oracle
+        check = bool(np.array_equal(tri.export_triangles(), oracle.delaunay(final_xy)))
+
+    updates, seconds, e2e_seconds = aggregate(local_updates, local_sec, e2e_sec)
+    value = updates / seconds
+    e2e_value = updates / e2e_seconds
+
+    if rank == 0:
+        peak, peak_kind = measured_peaks()
+        achieved = BYTES_PER_UPDATE * m / (kin_ms / 1000.0) / 1e9
+        line = {
+            "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * seconds / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64+int128 exact (fp32 filter)", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": args.n, "grid": args.grid, "moves_per_step": m,
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "e2e": {"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": 12 * m,
+                    "d2h_bytes_per_step": 64},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_kinetic", "kernel_ms": kin_ms, "bytes_per_update": BYTES_PER_UPDATE,
+                         "peak_kind": peak_kind},
+            "comparators": {
+                "gpu_kinetic_plain": {"value": value, "unit": "updates/s"},
+                "gpu_full_rebuild": {"value": m / (rebuild_ms / 1000.0), "unit": "updates/s",
+                                     "ms_per_rebuild": rebuild_ms},
+            },
+            "gpu_launches": int(launches),
+            "fallbacks": int(fallbacks),
+            "clocks": clk,
+        }
+        if check is not None:
+            line["final_state_matches_oracle"] = check
+        if not args.no_cpu_baseline and ws == 1:
+            threads = max(1, min(host_cores(), args.cpu_threads))
+            snaps = []
+            wb = W.c2(n=args.n, grid=args.grid, seed=77)
+            for _ in range(threads):
+                wb.next_moves()
+                snaps.append(wb.positions)
+            ups, dt = oracle_baseline(snaps, m, threads)
+            line["cpu_baseline"] = {"value": ups, "unit": "updates/s", "cores": threads, "kind": "oracle",
+                                    "sample": "%d oracle rebuilds of the %d-point set (one per step), "
+                                              "in parallel on %d threads, %.1f s wall" % (threads, args.n, threads, dt)}
+        print(json.dumps(line), flush=True)
+    tri.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
