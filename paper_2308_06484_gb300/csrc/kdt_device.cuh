@@ -32,6 +32,8 @@ constexpr int STACK = 96;              // Lawson flip stack per warp
 constexpr int WALK_CAP = 1 << 12;      // steps before a walk restarts
 constexpr int WALK_RESTARTS = 1024;    // restarts before point location gives up
 constexpr int ALIVE = 1;
+constexpr int LM = 64;                 // triangles a staged region holds
+constexpr int LV = 96;                 // vertices a staged region holds
 
 // device status codes (first error wins); mapped to the C-ABI codes on the host
 enum DevStatus : int {
@@ -80,6 +82,12 @@ struct WarpShared {
     int2 LX[KMAX];         // link coordinates
     int2 stack[STACK];     // flip stack: (slot, edge)
     int tmp[64];
+    // staged region of a fused move (kdt_local.cuh)
+    int lslot[LM];         // global slot of each staged triangle
+    int4 lv[LM];           // its vertices and flags
+    int4 ln[LM];           // its neighbour refs (global)
+    int vid[LV];           // staged vertex ids
+    int2 vxy[LV];          // and their coordinates
 };
 
 struct Warp {

@@ -6,7 +6,7 @@
 //            -> k_insert_level (one launch per level) -> k_certify_all (-> k_fixup ...)
 //   export:  k_exp_count -> scan -> k_exp_place -> k_exp_sortseg
 #pragma once
-#include "kdt_device.cuh"
+#include "kdt_local.cuh"
 
 namespace kd {
 
@@ -176,7 +176,7 @@ __global__ void k_scatter(int m, const int *move_cell, const int *cell_off, int 
 // triangulation in HBM, so the hand-off of Fig. 4 is an ownership change, not a
 // message.  A point whose target is still occupied by a point that has not moved
 // yet is deferred to k_deferred.
-__global__ void __launch_bounds__(WPB * 32) k_kinetic(Dev d, const int3 *moves, const int *order,
+__global__ void __launch_bounds__(WPB * 32, 8) k_kinetic(Dev d, const int3 *moves, const int *order,
                                                       const int *cell_cnt, const int *cell_off, int ncells,
                                                       int4 *deferred, int *defer_count, int defer_cap)
 {
@@ -193,20 +193,19 @@ __global__ void __launch_bounds__(WPB * 32) k_kinetic(Dev d, const int3 *moves, 
             if (read_status(d)) break;
             int3 mv = moves[order[off + j]];
             int p = mv.x;
-            int s0, s1, hint;
-            int rc = delete_point(w, d, p, s0, s1, hint);
-            if (rc) {
-                if (rc > 0 && w.lane == 0 && atomicCAS(d.status, 0, rc) == 0) d.status[S_FAILPT] = p;
-                break;
+            int2 q = make_int2(mv.y, mv.z);
+            int s0 = -1, s1 = -1, hint = -1;
+            // Delete + Update + Insert of Fig. 4 as one staged operation
+            int rc = move_point(w, d, p, q, s0, s1, hint);
+            if (rc == MV_GLOBAL) {
+                if (w.lane == 0) {
+                    d.xy[p] = q;
+                    __threadfence();
+                }
+                __syncwarp();
+                rc = insert_point(w, d, p, q, hint, s0, s1, true);
             }
-            // Update (Fig. 4): the point is out of the triangulation, move it
-            if (w.lane == 0) {
-                d.xy[p] = make_int2(mv.y, mv.z);
-                __threadfence();
-            }
-            __syncwarp();
-            rc = insert_point(w, d, p, make_int2(mv.y, mv.z), hint, s0, s1, true);
-            if (rc == 1) {
+            if (rc == MV_DEFER || rc == 1) {
                 if (w.lane == 0) {
                     int pos = atomicAdd(defer_count, 1);
                     if (pos < defer_cap) deferred[pos] = make_int4(p, s0, s1, hint);
