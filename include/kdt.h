@@ -52,6 +52,7 @@ extern "C" {
 #define KDT_ERR_CUDA (-7)            /* a CUDA runtime call failed                         */
 #define KDT_ERR_INTERNAL (-8)        /* an internal consistency check failed               */
 #define KDT_ERR_STATE (-9)           /* call out of order (e.g. kdt_step before kdt_build) */
+#define KDT_ERR_TOO_LARGE (-10)      /* more points than kdt_export_triangles_noalloc serves */
 
 /* ---- types -------------------------------------------------------------------- */
 typedef struct kdt kdt; /* opaque handle, owned by the library */
@@ -142,6 +143,30 @@ int kdt_export_triangles(kdt *h, int32_t *out, int64_t cap, int64_t *n_tri);
 
 /* Copy the current positions (2 int32 per point) into xy (host or device). */
 int kdt_export_points(kdt *h, int32_t *xy, int64_t cap_points);
+
+/* Export without allocating (the paper has no counterpart; this serves callers).
+ * kdt_export_triangles grows its own device scratch and staging buffers on first use
+ * and whenever the point count grows, so it calls cudaMalloc.  Some callers cannot
+ * allow that: an application that reserved the whole device memory budget for its
+ * own pool before creating the handle, or a per-step output loop that must not take
+ * the driver's allocation path.  This entry point produces the same canonical list
+ * (same order, same rows) and allocates nothing: its scratch (per-vertex counts and
+ * offsets, scan partial sums) is one file-scope device array of
+ * KDT_NOALLOC_MAX_POINTS * 8 + 4 KiB bytes (about 8 MiB), which every GPU that
+ * loads the library holds until the process exits.
+ *   out:   DEVICE pointer (this handle's GPU), capacity `cap` rows of 3 int32; a host
+ *          pointer is rejected with KDT_ERR_ARG (copying to it would need staging).
+ *   n_tri: receives the row count, also on KDT_ERR_CAPACITY.
+ * Errors: KDT_ERR_TOO_LARGE when the handle holds more than KDT_NOALLOC_MAX_POINTS
+ * points (nothing is launched); KDT_ERR_CAPACITY, KDT_ERR_ARG, KDT_ERR_STATE,
+ * KDT_ERR_CUDA.
+ * The first call on a device looks the scratch array's device address up
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that first
+ * call before any stream capture.  All calls share the one array, so calls that
+ * overlap on the GPU (other handles' streams, other host threads) race; serialise
+ * them.  Each call clears what must start at zero. */
+#define KDT_NOALLOC_MAX_POINTS (1 << 20)
+int kdt_export_triangles_noalloc(kdt *h, int32_t *out, int64_t cap, int64_t *n_tri);
 
 /* Full GPU verifier: every triangle alive and counter-clockwise, adjacency
  * reciprocal, every edge locally Delaunay (SoS), 2n - 2 triangles with ghosts, every

@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "../../include/kdt.h"
@@ -444,6 +445,7 @@ const char *kdt_error_string(int code)
     case KDT_ERR_CUDA: return "CUDA runtime error";
     case KDT_ERR_INTERNAL: return "internal consistency check failed";
     case KDT_ERR_STATE: return "call out of order";
+    case KDT_ERR_TOO_LARGE: return "more points than the allocation-free export serves";
     default: return "unknown error";
     }
 }
@@ -799,3 +801,75 @@ int kdt_eval_predicates(const int32_t *xy, const int32_t *quads, int64_t m, int3
 }
 
 }  // extern "C"
+
+// ====================================================================== allocation-free export
+//
+// The scratch of kdt_export_triangles_noalloc: counts (reused as fill cursors) and
+// offsets per point, then scan partial sums and the grand total.  Host code must not
+// use the symbol's name as a device address: the address is looked up per device
+// with cudaGetSymbolAddress and cached.
+namespace {
+
+constexpr int NOALLOC_TILES = KDT_NOALLOC_MAX_POINTS / SCAN_TILE + 8;
+constexpr size_t NOALLOC_WORDS = 2 * (size_t)KDT_NOALLOC_MAX_POINTS + 1024;
+static_assert(NOALLOC_TILES + 1 <= 1024, "tile sums must fit the reserved tail");
+
+static __device__ __align__(256) int g_noalloc_scratch[NOALLOC_WORDS];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+int *g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+std::mutex g_noalloc_mutex;
+
+// device address of the scratch on `device` (which must be current); nullptr on error
+int *noalloc_scratch(int device)
+{
+    if (device < 0 || device >= NOALLOC_MAX_DEVICES) return nullptr;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        g_noalloc_ptr[device] = (int *)p;
+    }
+    return g_noalloc_ptr[device];
+}
+
+}  // namespace
+
+extern "C" int kdt_export_triangles_noalloc(kdt *h, int32_t *out, int64_t cap, int64_t *n_tri)
+{
+    if (!h || !n_tri || cap < 0 || (cap > 0 && !out)) return KDT_ERR_ARG;
+    if (!h->built) return KDT_ERR_STATE;
+    if (h->n > KDT_NOALLOC_MAX_POINTS) return KDT_ERR_TOO_LARGE;
+    CK(cudaSetDevice(h->device));
+    if (cap > 0 && !is_device_ptr(out)) return KDT_ERR_ARG;
+    int *scratch = noalloc_scratch(h->device);
+    if (!scratch) return KDT_ERR_CUDA;
+    cudaStream_t st = h->stream;
+    const int n = (int)h->n;
+    int *cnt = scratch;                                   // counts, then fill cursors
+    int *off = scratch + KDT_NOALLOC_MAX_POINTS;          // exclusive offsets
+    int *tiles = scratch + 2 * (size_t)KDT_NOALLOC_MAX_POINTS;  // scan partial sums
+    int *total = tiles + 1023;                            // grand total
+    const int ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    CK(cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(int), st));
+    k_exp_count<<<thread_grid(h, h->cap, 256), 256, 0, st>>>(h->tv, h->cap, cnt);
+    k_scan_tile<<<ntiles, SCAN_THREADS, 0, st>>>(cnt, off, n, tiles);
+    k_scan_sums<<<1, 1024, 0, st>>>(tiles, ntiles, total);
+    k_scan_add<<<ntiles, SCAN_THREADS, 0, st>>>(off, n, tiles);
+    CK(cudaGetLastError());
+    int tot = 0;
+    CK(cudaMemcpyAsync(&tot, total, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *n_tri = tot;
+    if (tot > cap) return KDT_ERR_CAPACITY;
+    CK(cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(int), st));
+    k_exp_place<<<thread_grid(h, h->cap, 256), 256, 0, st>>>(h->tv, h->cap, off, cnt, (int3 *)out);
+    k_exp_sortseg<<<thread_grid(h, n, 256), 256, 0, st>>>(n, off, cnt, (int3 *)out);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    return KDT_OK;
+}
+

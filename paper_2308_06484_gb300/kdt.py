@@ -21,7 +21,7 @@ KDT_OK = 0
 ERRORS = {
     -1: "KDT_ERR_ARG", -2: "KDT_ERR_RANGE", -3: "KDT_ERR_DUPLICATE", -4: "KDT_ERR_DEGENERATE",
     -5: "KDT_ERR_CAPACITY", -6: "KDT_ERR_RETRY_EXHAUSTED", -7: "KDT_ERR_CUDA",
-    -8: "KDT_ERR_INTERNAL", -9: "KDT_ERR_STATE",
+    -8: "KDT_ERR_INTERNAL", -9: "KDT_ERR_STATE", -10: "KDT_ERR_TOO_LARGE",
 }
 
 
@@ -61,7 +61,8 @@ _lib = None
 SYMBOLS = ["kdt_default_config", "kdt_create", "kdt_destroy", "kdt_build", "kdt_step",
            "kdt_rebuild", "kdt_export_triangles", "kdt_export_points", "kdt_verify",
            "kdt_num_points", "kdt_get_stats", "kdt_reset_stats", "kdt_error_string",
-           "kdt_version", "kdt_eval_predicates", "kdt_export_store"]
+           "kdt_version", "kdt_eval_predicates", "kdt_export_store",
+           "kdt_export_triangles_noalloc"]
 
 
 def lib_path():
@@ -97,6 +98,7 @@ def load(build_if_stale: bool = True):
     L.kdt_version.restype = i32
     L.kdt_eval_predicates.argtypes = [vp, vp, i64, vp, i32, vp]
     L.kdt_export_store.argtypes = [vp, vp, vp, vp, i64]
+    L.kdt_export_triangles_noalloc.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
     for s in SYMBOLS:
         getattr(L, s)
     _lib = L
@@ -197,6 +199,15 @@ class Triangulation:
         p, cap = _ptr(out)
         _check(self.L.kdt_export_triangles(self.h, p, cap, ctypes.byref(nt)), "kdt_export_triangles")
         return out[: nt.value]
+
+    def export_triangles_noalloc(self, out):
+        """Canonical list into the CUDA int32 tensor `out` (rows x 3) without any
+        device allocation by the library; returns the row count."""
+        nt = ctypes.c_int64(0)
+        p, cap = _ptr(out)
+        _check(self.L.kdt_export_triangles_noalloc(self.h, p, cap, ctypes.byref(nt)),
+               "kdt_export_triangles_noalloc")
+        return int(nt.value)
 
     def export_points(self):
         out = np.empty((self.n, 2), dtype=np.int32)
