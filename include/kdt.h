@@ -82,7 +82,8 @@ typedef struct {
     int32_t kinetic_warps; /* warps moving points concurrently in a step (0 = one per cell)  */
     int32_t debug;         /* bit 0: on an in-step failure keep the failed state (no
                               fallback, no roll-back) so kdt_export_store can inspect it     */
-    int32_t reserved[4];
+    int32_t use_graph;     /* 1: launch each step as one captured CUDA graph (default)       */
+    int32_t reserved[3];
 } kdt_config;
 
 /* Counters since creation (or kdt_reset_stats). */
@@ -95,7 +96,11 @@ typedef struct {
     int64_t kinetic_kernel_timed; /* launches included in kinetic_kernel_ms               */
     int64_t last_fallback_reason; /* internal status that triggered the last fallback     */
     int64_t last_fallback_point;  /* point whose operation reported it (-1 if unknown)     */
-    int64_t reserved[6];
+    int64_t staged_to_global;     /* moves that left the staged region (long / hull moves)  */
+    int64_t cycles_move;          /* SM cycles summed over moved points (kinetic kernel)   */
+    int64_t cycles_move_max;      /* longest single move, cycles                            */
+    int64_t cycles_gather, cycles_claim, cycles_local, cycles_writeback; /* phase sums    */
+    int64_t reserved[8];
 } kdt_stats;
 
 /* ---- lifecycle ------------------------------------------------------------------ */

@@ -59,6 +59,14 @@ struct kdt {
     int scan_tmp_cap = 0;
     // build / export temporaries (kept between calls)
     Buf key, bord, hist, hoff, exp_cnt, exp_off, exp_fill, exp_out, in_xy;
+    // graph-launched step: control words (moves, stamp) and the captured graph
+    int *ctl = nullptr;    // device
+    int *hctl = nullptr;   // pinned host
+    cudaStream_t cstream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int graph_gen = -1;    // buffer generation the graph was captured for
+    int gen = 0;           // bumped whenever step buffers are (re)allocated
     // host side
     int *hscal = nullptr;  // pinned copy of the scalars
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -149,11 +157,12 @@ Dev make_dev(kdt *h)
     d.counters = h->counters;
     d.use_filter = h->cfg.filter;
     d.retry_cap = h->cfg.retry_cap;
+    d.ctl = nullptr;
     return d;
 }
 
 // exclusive scan in place (or out of place) of n ints; *total receives the sum
-int scan(kdt *h, const int *in, int *out, int n, int *total)
+int scan(kdt *h, const int *in, int *out, int n, int *total, cudaStream_t st)
 {
     int tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (tiles < 1) tiles = 1;
@@ -161,10 +170,11 @@ int scan(kdt *h, const int *in, int *out, int n, int *total)
         int c = tiles + 1024;
         if (dalloc(&h->scan_tmp, (size_t)c)) return KDT_ERR_CUDA;
         h->scan_tmp_cap = c;
+        h->gen++;  // a captured step graph holds the old pointer
     }
-    k_scan_tile<<<tiles, SCAN_THREADS, 0, h->stream>>>(in, out, n, h->scan_tmp);
-    k_scan_sums<<<1, 1024, 0, h->stream>>>(h->scan_tmp, tiles, total);
-    k_scan_add<<<tiles, SCAN_THREADS, 0, h->stream>>>(out, n, h->scan_tmp);
+    k_scan_tile<<<tiles, SCAN_THREADS, 0, st>>>(in, out, n, h->scan_tmp);
+    k_scan_sums<<<1, 1024, 0, st>>>(h->scan_tmp, tiles, total);
+    k_scan_add<<<tiles, SCAN_THREADS, 0, st>>>(out, n, h->scan_tmp);
     h->stats.kernel_launches += 3;
     CK(cudaGetLastError());
     return 0;
@@ -280,7 +290,7 @@ int rebuild_positions(kdt *h)
     CK(cudaMemsetAsync(hist, 0, ncell * 4, st));
     k_hilbert<<<(n + 255) / 256, 256, 0, st>>>(h->xy, n, h->scal + S_MINX, k, shift, key, hist);
     h->stats.kernel_launches++;
-    if (scan(h, hist, hoff, (int)ncell, h->scal + S_TOTAL)) return KDT_ERR_CUDA;
+    if (scan(h, hist, hoff, (int)ncell, h->scal + S_TOTAL, st)) return KDT_ERR_CUDA;
     CK(cudaMemsetAsync(hist, 0, ncell * 4, st));
     k_place_order<<<(n + 255) / 256, 256, 0, st>>>(n, key, hoff, hist, order);
     k_third<<<thread_grid(h, n, 256), 256, 0, st>>>(h->xy, n, order, h->scal + S_THIRD);
@@ -333,6 +343,7 @@ int ensure_moves(kdt *h, int64_t m)
     if (dc > (1ll << 30)) dc = 1ll << 30;
     if (dalloc(&h->dirty, (size_t)dc)) return KDT_ERR_CUDA;
     h->dirty_cap = (int)dc;
+    h->gen++;
     return 0;
 }
 
@@ -359,8 +370,19 @@ int alloc_state(kdt *h, int64_t n)
     return 0;
 }
 
+void drop_graph(kdt *h)
+{
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->gexec = nullptr;
+    h->graph = nullptr;
+    h->graph_gen = -1;
+}
+
 void free_state(kdt *h)
 {
+    drop_graph(h);
+    h->gen++;
     void *ps[] = {h->xy, h->pt_tri, h->pt_stamp, h->tv, h->tn, h->viol, h->moves, h->old_xy, h->move_cell,
                   h->order, h->deferred, h->dirty, h->cell_cnt, h->cell_off, h->cell_fill, h->scan_tmp};
     for (void *p : ps)
@@ -380,7 +402,7 @@ void free_state(kdt *h)
 
 void add_counters(kdt *h)
 {
-    unsigned long long c[C_NUM];
+    unsigned long long c[C_NUM + 1];
     if (cudaMemcpy(c, h->counters, sizeof c, cudaMemcpyDeviceToHost) != cudaSuccess) return;
     cudaMemset(h->counters, 0, sizeof c);
     kdt_stats &s = h->stats;
@@ -398,6 +420,13 @@ void add_counters(kdt *h)
     s.deletes += c[C_DELETES];
     s.inserts += c[C_INSERTS];
     s.flip_tests += c[C_FLIP_TESTS];
+    s.staged_to_global += c[C_MV_GLOBAL];
+    s.cycles_move += (int64_t)c[C_CYC_MOVE] << 6;
+    if ((int64_t)(c[C_CYC_MAX] << 6) > s.cycles_move_max) s.cycles_move_max = (int64_t)(c[C_CYC_MAX] << 6);
+    s.cycles_gather += (int64_t)c[C_CYC_GATHER] << 6;
+    s.cycles_claim += (int64_t)c[C_CYC_CLAIM] << 6;
+    s.cycles_local += (int64_t)c[C_CYC_LOCAL] << 6;
+    s.cycles_writeback += (int64_t)c[C_CYC_WB] << 6;
 }
 
 // Undo a step that failed after it started: restore the old positions and rebuild.
@@ -421,6 +450,40 @@ int verify_state(kdt *h, int64_t *bad)
     if (h->hscal[S_ALIVE] != h->cap) b += 1;
     if (h->hscal[S_WRAPS] != 1) b += 1;  // the hull must wind exactly once
     *bad = b;
+    return 0;
+}
+
+// Issue one step's kernels on `st`: intake, per-partition counting sort, the kinetic
+// kernel, deferred insertions, certification, and the copy of the status scalars to
+// the host.  With from_ctl the grids do not depend on m (the kernels read m and the
+// stamp from h->ctl), so the sequence can be captured once into a CUDA graph.
+int enqueue_step(kdt *h, cudaStream_t st, const Dev &d, int mi, bool from_ctl)
+{
+    int cap = from_ctl ? h->mcap : mi;
+    CK(cudaMemsetAsync(h->scal, 0, S_NUM * sizeof(int), st));
+    CK(cudaMemsetAsync(h->cell_cnt, 0, (size_t)h->ncells * sizeof(int), st));
+    k_intake<<<thread_grid(h, cap, 256), 256, 0, st>>>(d, h->moves, mi, h->grid, h->cfg.domain_bits, h->cell_cnt,
+                                                       h->old_xy, h->move_cell);
+    if (scan(h, h->cell_cnt, h->cell_off, h->ncells, h->scal + S_TOTAL, st)) return KDT_ERR_CUDA;
+    h->stats.kernel_launches -= 3;  // counted by the caller
+    CK(cudaMemsetAsync(h->cell_fill, 0, (size_t)h->ncells * sizeof(int), st));
+    k_scatter<<<thread_grid(h, cap, 256), 256, 0, st>>>(mi, h->move_cell, h->cell_off, h->cell_fill, h->order,
+                                                        h->scal + S_STATUS, from_ctl ? h->ctl : nullptr);
+    // inside a capture an event record must be an external node to keep its timestamp
+    unsigned evflags = from_ctl ? cudaEventRecordExternal : cudaEventRecordDefault;
+    if (h->cfg.timing) CK(cudaEventRecordWithFlags(h->ev0, st, evflags));
+    int kblocks = warp_grid(h, h->ncells, 64), kthreads = WPB * 32;
+    if (h->cfg.kinetic_warps > 0) {
+        kblocks = (h->cfg.kinetic_warps + WPB - 1) / WPB;
+        if (h->cfg.kinetic_warps < WPB) kthreads = 32 * h->cfg.kinetic_warps;
+    }
+    k_kinetic<<<kblocks, kthreads, 0, st>>>(d, h->moves, h->order, h->cell_cnt, h->cell_off, h->ncells,
+                                            h->deferred, h->scal + S_DEFER, h->mcap);
+    if (h->cfg.timing) CK(cudaEventRecordWithFlags(h->ev1, st, evflags));
+    k_deferred<<<2, WPB * 32, 0, st>>>(d, h->deferred, h->scal + S_DEFER, h->mcap);
+    k_certify<<<thread_grid(h, 64ll * cap, 256), 256, 0, st>>>(d, 0, h->viol, h->scal + S_VIOL, h->viol_cap);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->hscal, h->scal, S_NUM * sizeof(int), cudaMemcpyDeviceToHost, st));
     return 0;
 }
 
@@ -463,6 +526,7 @@ int kdt_default_config(kdt_config *cfg)
     cfg->verify = 0;
     cfg->timing = 0;
     cfg->warps_per_block = WPB;
+    cfg->use_graph = 1;
     return KDT_OK;
 }
 
@@ -483,14 +547,17 @@ int kdt_create(kdt **out, const kdt_config *cfg, int device, void *cuda_stream)
     h->stream = (cudaStream_t)cuda_stream;
     h->cfg = c;
     if (cudaMalloc(&h->scal, S_NUM * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&h->counters, C_NUM * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&h->counters, (C_NUM + 1) * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost(&h->hscal, S_NUM * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&h->ctl, 4 * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&h->hctl, 4 * sizeof(int)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
         kdt_destroy(h);
         return KDT_ERR_CUDA;
     }
     cudaMemset(h->scal, 0, S_NUM * sizeof(int));
-    cudaMemset(h->counters, 0, C_NUM * sizeof(unsigned long long));
+    cudaMemset(h->counters, 0, (C_NUM + 1) * sizeof(unsigned long long));
     *out = h;
     return KDT_OK;
 }
@@ -505,6 +572,9 @@ int kdt_destroy(kdt *h)
     if (h->scal) cudaFree(h->scal);
     if (h->counters) cudaFree(h->counters);
     if (h->hscal) cudaFreeHost(h->hscal);
+    if (h->ctl) cudaFree(h->ctl);
+    if (h->hctl) cudaFreeHost(h->hctl);
+    if (h->cstream) cudaStreamDestroy(h->cstream);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     delete h;
@@ -553,15 +623,15 @@ int kdt_step(kdt *h, const kdt_move *moves, int64_t m)
                        is_device_ptr(moves) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     h->stamp++;
     Dev d = make_dev(h);
-    CK(cudaMemsetAsync(h->scal, 0, S_NUM * sizeof(int), st));
-    CK(cudaMemsetAsync(h->cell_cnt, 0, (size_t)h->ncells * sizeof(int), st));
-    k_intake<<<(mi + 255) / 256, 256, 0, st>>>(d, h->moves, mi, h->grid, h->cfg.domain_bits, h->cell_cnt,
-                                               h->old_xy, h->move_cell);
-    h->stats.kernel_launches++;
     bool large = h->cfg.fallback && (double)m > (double)h->cfg.rebuild_ratio * (double)h->n;
     if (large) {
         // a step this large is cheaper as a rebuild (Abstract: "if the points move so
         // far, it's better to rebuild the triangulation")
+        CK(cudaMemsetAsync(h->scal, 0, S_NUM * sizeof(int), st));
+        CK(cudaMemsetAsync(h->cell_cnt, 0, (size_t)h->ncells * sizeof(int), st));
+        k_intake<<<(mi + 255) / 256, 256, 0, st>>>(d, h->moves, mi, h->grid, h->cfg.domain_bits, h->cell_cnt,
+                                                   h->old_xy, h->move_cell);
+        h->stats.kernel_launches++;
         if (sync_scalars(h)) return KDT_ERR_CUDA;
         if (h->hscal[S_STATUS]) return dev_to_abi(h->hscal[S_STATUS]);
         k_set_positions<<<(mi + 255) / 256, 256, 0, st>>>(h->xy, h->moves, mi);
@@ -577,25 +647,37 @@ int kdt_step(kdt *h, const kdt_move *moves, int64_t m)
         add_counters(h);
         return KDT_OK;
     }
-    if (scan(h, h->cell_cnt, h->cell_off, h->ncells, h->scal + S_TOTAL)) return KDT_ERR_CUDA;
-    CK(cudaMemsetAsync(h->cell_fill, 0, (size_t)h->ncells * sizeof(int), st));
-    k_scatter<<<(mi + 255) / 256, 256, 0, st>>>(mi, h->move_cell, h->cell_off, h->cell_fill, h->order,
-                                                h->scal + S_STATUS);
-    if (h->cfg.timing) CK(cudaEventRecord(h->ev0, st));
-    int kblocks = warp_grid(h, h->ncells, 64), kthreads = WPB * 32;
-    if (h->cfg.kinetic_warps > 0) {
-        kblocks = (h->cfg.kinetic_warps + WPB - 1) / WPB;
-        if (h->cfg.kinetic_warps < WPB) kthreads = 32 * h->cfg.kinetic_warps;
+    if (h->cfg.use_graph) {
+        // one graph launch per step: the kernels read m and the stamp from ctl
+        if (h->graph_gen != h->gen) {
+            drop_graph(h);
+            // nothing may allocate while capturing: size the scan scratch first
+            if (scan(h, h->cell_cnt, h->cell_off, h->ncells, h->scal + S_TOTAL, st)) return KDT_ERR_CUDA;
+            Dev dg = d;
+            dg.ctl = h->ctl;
+            CK(cudaStreamBeginCapture(h->cstream, cudaStreamCaptureModeThreadLocal));
+            int er = enqueue_step(h, h->cstream, dg, 0, true);
+            cudaGraph_t g = nullptr;
+            cudaError_t ce = cudaStreamEndCapture(h->cstream, &g);
+            if (er || ce != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return KDT_ERR_CUDA;
+            }
+            h->graph = g;
+            CK(cudaGraphInstantiate(&h->gexec, h->graph, 0));
+            h->graph_gen = h->gen;
+        }
+        h->hctl[0] = mi;
+        h->hctl[1] = h->stamp;
+        CK(cudaMemcpyAsync(h->ctl, h->hctl, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
+        CK(cudaGraphLaunch(h->gexec, st));
+        h->stats.kernel_launches += 8;
+        CK(cudaStreamSynchronize(st));
+    } else {
+        if (enqueue_step(h, st, d, mi, false)) return KDT_ERR_CUDA;
+        h->stats.kernel_launches += 8;
+        CK(cudaStreamSynchronize(st));
     }
-    k_kinetic<<<kblocks, kthreads, 0, st>>>(d, h->moves, h->order, h->cell_cnt, h->cell_off,
-                                                                h->ncells, h->deferred, h->scal + S_DEFER,
-                                                                h->mcap);
-    if (h->cfg.timing) CK(cudaEventRecord(h->ev1, st));
-    k_deferred<<<2, WPB * 32, 0, st>>>(d, h->deferred, h->scal + S_DEFER, h->mcap);
-    k_certify<<<thread_grid(h, 64ll * m, 256), 256, 0, st>>>(d, 0, h->viol, h->scal + S_VIOL, h->viol_cap);
-    h->stats.kernel_launches += 4;
-    CK(cudaGetLastError());
-    if (sync_scalars(h)) return KDT_ERR_CUDA;
     if (h->cfg.timing) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) {
@@ -613,7 +695,6 @@ int kdt_step(kdt *h, const kdt_move *moves, int64_t m)
         int nv = h->hscal[S_VIOL];
         bool overflow = h->hscal[S_DIRTY] > h->dirty_cap;
         if (nv > 0 || overflow) {
-            h->stats.violations += overflow ? 0 : 0;
             int ds = 0;
             if (overflow) {
                 if (certify_and_repair(h, true, &ds)) return KDT_ERR_CUDA;
@@ -715,7 +796,7 @@ int kdt_export_triangles(kdt *h, int32_t *out, int64_t cap, int64_t *n_tri)
     CK(cudaMemsetAsync(cnt, 0, (size_t)n * 4, st));
     k_exp_count<<<thread_grid(h, h->cap, 256), 256, 0, st>>>(h->tv, h->cap, cnt);
     h->stats.kernel_launches++;
-    if (scan(h, cnt, off, n, h->scal + S_TOTAL)) return KDT_ERR_CUDA;
+    if (scan(h, cnt, off, n, h->scal + S_TOTAL, st)) return KDT_ERR_CUDA;
     if (sync_scalars(h)) return KDT_ERR_CUDA;
     int64_t total = h->hscal[S_TOTAL];
     *n_tri = total;

@@ -52,7 +52,9 @@ enum DevStatus : int {
 enum Counter : int {
     C_FLIPS = 0, C_RETRIES, C_WALK_STEPS, C_EXACT, C_TIES, C_DEFERRED, C_VIOL, C_FIX_FLIPS,
     C_DEG_DEL, C_STACK_DROP, C_SPLIT_EDGE, C_SPLIT_GHOST, C_DELETES, C_INSERTS, C_FLIP_TESTS,
-    C_NUM
+    C_MV_GLOBAL, C_CYC_MOVE, C_CYC_GATHER, C_CYC_CLAIM, C_CYC_LOCAL, C_CYC_WB,
+    C_NUM,
+    C_CYC_MAX = C_NUM  // a second device slot, updated with atomicMax
 };
 
 struct Dev {
@@ -68,6 +70,7 @@ struct Dev {
     int dirty_cap;
     int *pt_stamp;       // step stamp of points moved in this step
     int stamp;
+    const int *ctl;      // graph-launched steps: ctl[0] = moves, ctl[1] = stamp (device)
     unsigned long long *counters;
     int use_filter;
     int retry_cap;
@@ -97,6 +100,7 @@ struct Warp {
     int ncl;
     unsigned rng;
     unsigned cnt[C_NUM];
+    unsigned cyc_max;   // longest single move (cycles / 64)
 };
 
 // ------------------------------------------------------------------ helpers
@@ -185,6 +189,7 @@ __device__ __forceinline__ void flush_counters(const Warp &w, const Dev &d)
     if (w.lane == 0 && d.counters) {
         for (int i = 0; i < C_NUM; ++i)
             if (w.cnt[i]) atomicAdd(d.counters + i, (unsigned long long)w.cnt[i]);
+        if (w.cyc_max) atomicMax(d.counters + C_CYC_MAX, (unsigned long long)w.cyc_max);
     }
 }
 

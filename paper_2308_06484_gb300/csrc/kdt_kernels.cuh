@@ -31,6 +31,7 @@ __device__ __forceinline__ Warp make_warp(WarpShared *sh, int token, unsigned se
     if (w.rng == 0) w.rng = 1;
 #pragma unroll
     for (int i = 0; i < C_NUM; ++i) w.cnt[i] = 0;
+    w.cyc_max = 0;
     return w;
 }
 
@@ -132,39 +133,45 @@ __global__ void k_scan_add(int *out, int n, const int *tile_sums)
 __global__ void k_intake(Dev d, const int3 *moves, int m, int grid, int bits, int *cell_cnt,
                          int2 *old_xy, int *move_cell)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    int3 mv = moves[i];
-    if (mv.x < 0 || mv.x >= d.n) {
-        atomicCAS(d.status, 0, DEV_ARG);
-        return;
+    if (d.ctl) {
+        m = __ldcg(d.ctl);
+        d.stamp = __ldcg(d.ctl + 1);
     }
     long long lim = 1ll << bits;
-    if (mv.y < 0 || mv.z < 0 || mv.y >= lim || mv.z >= lim) {
-        atomicCAS(d.status, 0, DEV_RANGE);
-        return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        int3 mv = moves[i];
+        if (mv.x < 0 || mv.x >= d.n) {
+            atomicCAS(d.status, 0, DEV_ARG);
+            continue;
+        }
+        if (mv.y < 0 || mv.z < 0 || mv.y >= lim || mv.z >= lim) {
+            atomicCAS(d.status, 0, DEV_RANGE);
+            continue;
+        }
+        int prev = atomicExch(d.pt_stamp + mv.x, d.stamp);
+        if (prev == d.stamp) {
+            atomicCAS(d.status, 0, DEV_DUP_ID);
+            continue;
+        }
+        int2 o = d.xy[mv.x];
+        old_xy[i] = o;
+        int cx = (int)(((long long)o.x * grid) >> bits);
+        int cy = (int)(((long long)o.y * grid) >> bits);
+        int c = cy * grid + cx;
+        move_cell[i] = c;
+        atomicAdd(cell_cnt + c, 1);
     }
-    int prev = atomicExch(d.pt_stamp + mv.x, d.stamp);
-    if (prev == d.stamp) {
-        atomicCAS(d.status, 0, DEV_DUP_ID);
-        return;
-    }
-    int2 o = d.xy[mv.x];
-    old_xy[i] = o;
-    int cx = (int)(((long long)o.x * grid) >> bits);
-    int cy = (int)(((long long)o.y * grid) >> bits);
-    int c = cy * grid + cx;
-    move_cell[i] = c;
-    atomicAdd(cell_cnt + c, 1);
 }
 
 __global__ void k_scatter(int m, const int *move_cell, const int *cell_off, int *cell_fill, int *order,
-                          const int *status)
+                          const int *status, const int *ctl)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m || *status) return;
-    int c = move_cell[i];
-    order[cell_off[c] + atomicAdd(cell_fill + c, 1)] = i;
+    if (*status) return;
+    if (ctl) m = __ldcg(ctl);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        int c = move_cell[i];
+        order[cell_off[c] + atomicAdd(cell_fill + c, 1)] = i;
+    }
 }
 
 // ------------------------------------------------------------------ step: kinetic
@@ -180,6 +187,7 @@ __global__ void __launch_bounds__(WPB * 32, 8) k_kinetic(Dev d, const int3 *move
                                                       const int *cell_cnt, const int *cell_off, int ncells,
                                                       int4 *deferred, int *defer_count, int defer_cap)
 {
+    if (d.ctl) d.stamp = __ldcg(d.ctl + 1);
     __shared__ WarpShared shs[WPB];
     int wib = threadIdx.x >> 5;
     int gw = blockIdx.x * (blockDim.x >> 5) + wib;
@@ -195,15 +203,22 @@ __global__ void __launch_bounds__(WPB * 32, 8) k_kinetic(Dev d, const int3 *move
             int p = mv.x;
             int2 q = make_int2(mv.y, mv.z);
             int s0 = -1, s1 = -1, hint = -1;
+            long long c0 = clock64();
             // Delete + Update + Insert of Fig. 4 as one staged operation
             int rc = move_point(w, d, p, q, s0, s1, hint);
             if (rc == MV_GLOBAL) {
+                w.cnt[C_MV_GLOBAL]++;
                 if (w.lane == 0) {
                     d.xy[p] = q;
                     __threadfence();
                 }
                 __syncwarp();
                 rc = insert_point(w, d, p, q, hint, s0, s1, true);
+            }
+            {
+                unsigned c = (unsigned)((clock64() - c0) >> 6);
+                w.cnt[C_CYC_MOVE] += c;
+                w.cyc_max = c > w.cyc_max ? c : w.cyc_max;
             }
             if (rc == MV_DEFER || rc == 1) {
                 if (w.lane == 0) {
@@ -227,6 +242,7 @@ __global__ void __launch_bounds__(WPB * 32, 8) k_kinetic(Dev d, const int3 *move
 __global__ void __launch_bounds__(WPB * 32) k_deferred(Dev d, const int4 *deferred, const int *defer_count,
                                                        int defer_cap)
 {
+    if (d.ctl) d.stamp = __ldcg(d.ctl + 1);
     __shared__ WarpShared shs[WPB];
     int wib = threadIdx.x >> 5;
     int gw = blockIdx.x * (blockDim.x >> 5) + wib;

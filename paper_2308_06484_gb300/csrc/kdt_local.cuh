@@ -312,7 +312,10 @@ __device__ int move_point(Warp &w, const Dev &d, int p, int2 q, int &s0, int &s1
     for (int attempt = 0;; ++attempt) {
         if (attempt > d.retry_cap) return DEV_RETRY;
         if (read_status(d)) return MV_ABORT;
+        long long t0 = clock64();
         int k = gather_star(w, d, p);
+        long long t1 = clock64();
+        w.cnt[C_CYC_GATHER] += (unsigned)((t1 - t0) >> 6);
         if (k == -2 && attempt == d.retry_cap) return DEV_DEGREE;
         if (k < 3 || 2 * k + 8 > LM) {
             if (k >= 3) {
@@ -358,6 +361,8 @@ __device__ int move_point(Warp &w, const Dev &d, int p, int2 q, int &s0, int &s1
             backoff(w, attempt);
             continue;
         }
+        long long t2 = clock64();
+        w.cnt[C_CYC_CLAIM] += (unsigned)((t2 - t1) >> 6);
         // vertex table: link vertices (coordinates into LX too) and ring apexes
         for (int i = w.lane; i < k; i += 32) {
             int lv = sh->L[i];
@@ -591,7 +596,10 @@ __device__ int move_point(Warp &w, const Dev &d, int p, int2 q, int &s0, int &s1
         if (left > 0 && w.lane == 0)
             for (int j = 0; j < left; ++j) sh->stack[j] = make_int2(sh->lslot[sh->stack[j].x], sh->stack[j].y);
         __syncwarp();
+        long long t3 = clock64();
+        w.cnt[C_CYC_LOCAL] += (unsigned)((t3 - t2) >> 6);
         write_back(w, d, R);
+        w.cnt[C_CYC_WB] += (unsigned)((clock64() - t3) >> 6);
         if (left > 0) lawson(w, d, left, p, true);
         return MV_DONE;
     }

@@ -39,7 +39,7 @@ class Config(ctypes.Structure):
                 ("verify", ctypes.c_int32), ("timing", ctypes.c_int32),
                 ("warps_per_block", ctypes.c_int32), ("build_warps", ctypes.c_int32),
                 ("kinetic_warps", ctypes.c_int32), ("debug", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 _STAT_FIELDS = ["steps", "moves", "rebuilds", "fallbacks", "kernel_launches", "flips", "retries",
@@ -48,11 +48,16 @@ _STAT_FIELDS = ["steps", "moves", "rebuilds", "fallbacks", "kernel_launches", "f
                 "inserts", "flip_tests"]
 
 
+_STAT_FIELDS2 = ["staged_to_global", "cycles_move", "cycles_move_max", "cycles_gather", "cycles_claim",
+                 "cycles_local", "cycles_writeback"]
+
+
 class Stats(ctypes.Structure):
     _fields_ = ([(f, ctypes.c_int64) for f in _STAT_FIELDS]
                 + [("kinetic_kernel_ms", ctypes.c_double), ("kinetic_kernel_timed", ctypes.c_int64),
-                   ("last_fallback_reason", ctypes.c_int64), ("last_fallback_point", ctypes.c_int64),
-                   ("reserved", ctypes.c_int64 * 6)])
+                   ("last_fallback_reason", ctypes.c_int64), ("last_fallback_point", ctypes.c_int64)]
+                + [(f, ctypes.c_int64) for f in _STAT_FIELDS2]
+                + [("reserved", ctypes.c_int64 * 8)])
 
 
 _lib = None
@@ -241,6 +246,8 @@ class Triangulation:
         d["kinetic_kernel_timed"] = int(s.kinetic_kernel_timed)
         d["last_fallback_reason"] = int(s.last_fallback_reason)
         d["last_fallback_point"] = int(s.last_fallback_point)
+        for f in _STAT_FIELDS2:
+            d[f] = int(getattr(s, f))
         return d
 
     def reset_stats(self):
