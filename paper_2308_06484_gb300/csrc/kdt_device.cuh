@@ -28,12 +28,11 @@ namespace kd {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int KMAX = 64;               // largest vertex degree a deletion handles
 constexpr int MAXC = 2 * KMAX + 16;    // claims one warp may hold
-constexpr int STACK = 96;              // Lawson flip stack per warp
+constexpr int STACK = 64;              // Lawson flip stack per warp
 constexpr int WALK_CAP = 1 << 12;      // steps before a walk restarts
 constexpr int WALK_RESTARTS = 1024;    // restarts before point location gives up
 constexpr int ALIVE = 1;
 constexpr int LM = 64;                 // triangles a staged region holds
-constexpr int LV = 96;                 // vertices a staged region holds
 
 // device status codes (first error wins); mapped to the C-ABI codes on the host
 enum DevStatus : int {
@@ -88,9 +87,10 @@ struct WarpShared {
     // staged region of a fused move (kdt_local.cuh)
     int lslot[LM];         // global slot of each staged triangle
     int4 lv[LM];           // its vertices and flags
-    int4 ln[LM];           // its neighbour refs (global)
-    int vid[LV];           // staged vertex ids
-    int2 vxy[LV];          // and their coordinates
+    int4 ln[LM];           // its neighbour refs (global: slot << 2 | edge)
+    int4 lnl[LM];          // the same neighbours as staged indices (-1: not staged)
+    int2 lp[LM][3];        // coordinates of its three vertices
+    int EO[KMAX];          // staged outer ref (index << 2 | edge) of each link edge
 };
 
 struct Warp {
@@ -251,7 +251,7 @@ enum Where : int { W_INSIDE = 0, W_EDGE = 1, W_VERTEX = 2, W_GHOST = 3, W_FAIL =
 // coinciding vertex for W_VERTEX.  Reads are unclaimed; callers re-check after
 // claiming.  A random start edge breaks ties so walks cannot cycle forever in the
 // non-Delaunay states other warps may leave transiently.
-__device__ int walk(Warp &w, const Dev &d, int t, int2 q, int &where, int &e, int &vtx)
+__device__ __noinline__ int walk(Warp &w, const Dev &d, int t, int2 q, int &where, int &e, int &vtx)
 {
     where = W_FAIL;
     for (int steps = 0; steps < WALK_CAP; ++steps) {
@@ -361,7 +361,7 @@ __device__ void do_flip(Warp &w, const Dev &d, int T, int e, const int4 &tv_, co
 // pushed.  Tests are made on unclaimed reads; only an indicated flip is claimed and
 // re-checked.  An edge that cannot be settled here is left to the certification
 // pass that follows every step, so correctness never depends on this stack.
-__device__ int lawson(Warp &w, const Dev &d, int top, int p, bool insertion_mode)
+__device__ __noinline__ int lawson(Warp &w, const Dev &d, int top, int p, bool insertion_mode)
 {
     WarpShared *sh = w.sh;
     int attempts = 0;
@@ -459,7 +459,7 @@ __device__ int lawson(Warp &w, const Dev &d, int top, int p, bool insertion_mode
 // one claimed operation keeps the hull convex whenever nothing is claimed, so no
 // other warp can ever mistake a pocket of a half-repaired hull for the outside.
 // Returns 0 when written, 1 to retry (contention or stale reads), or an error.
-__device__ int insert_outside(Warp &w, const Dev &d, int p, int2 q, int V0, int spare0, int spare1, int &m_out)
+__device__ __noinline__ int insert_outside(Warp &w, const Dev &d, int p, int2 q, int V0, int spare0, int spare1, int &m_out)
 {
     WarpShared *sh = w.sh;
     const int KCH = 60;
@@ -590,7 +590,7 @@ __device__ int insert_outside(Warp &w, const Dev &d, int p, int2 q, int V0, int 
 // spare0 / spare1 are two dead slots owned by the caller (a deletion's leftovers or
 // fresh slots during a build).  Returns 0, 1 = deferred (p lands on a vertex that is
 // still moving in this step), or a DevStatus error.
-__device__ int insert_point(Warp &w, const Dev &d, int p, int2 q, int start, int spare0, int spare1,
+__device__ __noinline__ int insert_point(Warp &w, const Dev &d, int p, int2 q, int start, int spare0, int spare1,
                             bool allow_defer)
 {
     WarpShared *sh = w.sh;
@@ -788,7 +788,7 @@ __device__ bool ear_valid(const int *EL, const int2 *EX, int m, int i, const Dev
 // star-shaped hole by Delaunay ears (the simple deletion the paper prefers, Section
 // IV), release.  On success the two slots the hole no longer needs are returned
 // dead in spare0/spare1 and `hint` is a new triangle next to p's old position.
-__device__ int delete_point(Warp &w, const Dev &d, int p, int &spare0, int &spare1, int &hint)
+__device__ __noinline__ int delete_point(Warp &w, const Dev &d, int p, int &spare0, int &spare1, int &hint)
 {
     WarpShared *sh = w.sh;
     for (int attempt = 0;; ++attempt) {

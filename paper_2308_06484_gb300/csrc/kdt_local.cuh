@@ -3,18 +3,24 @@
 // The paper's per-block update (Fig. 4: Update, Delete, Insert; Section IV) touches
 // the star of the moved point p and, for a short move, the star of its new position
 // q, which overlaps it.  This operation claims p's star and the ring of triangles
-// around it in one batch, copies them (and their vertices' coordinates) into the
-// warp's shared memory, and there
+// around it in one batch, copies them into the warp's shared memory (vertices,
+// neighbours as global refs and as staged indices, and the coordinates of every
+// vertex, so no lookup is needed later), and there
 //   1. deletes p by Delaunay ears (the simple deletion Section IV prefers),
 //   2. locates q among the staged triangles,
 //   3. splits the containing triangle (1->3, or 2->4 when q is on an edge),
-//   4. runs the Lawson flips of the edges opposite q, claiming and staging further
-//      triangles only when a flip reaches outside the region,
+//   4. runs the Lawson flips of the edges opposite q with the flip stack in shared
+//      memory, claiming and staging further triangles only when a flip reaches
+//      outside the region,
 // then writes every modified triangle back and releases the claims.  Global memory
 // sees one claim batch, one validation pass and one write-back instead of a round
 // trip per ear and per flip.  When q is not inside the staged region (a long move,
 // a move outside the hull) or a claim needed later fails, the work done so far is
 // written back (a valid triangulation) and the caller continues on the global path.
+//
+// Staged values every lane computes identically are written to shared memory by all
+// lanes (same value, same address); only lane-parallel writes are followed by a
+// warp barrier.
 #pragma once
 #include "kdt_device.cuh"
 
@@ -22,6 +28,11 @@ namespace kd {
 
 // outcome of move_point
 enum MoveResult : int { MV_DONE = 0, MV_DEFER = 1, MV_GLOBAL = 2, MV_ABORT = -1 };
+
+struct Region {
+    int cnt;                   // staged triangles
+    unsigned long long dirty;  // modified staged triangles
+};
 
 __device__ __forceinline__ int local_find(const WarpShared *sh, int cnt, int slot)
 {
@@ -38,98 +49,59 @@ __device__ __forceinline__ int local_find(const WarpShared *sh, int cnt, int slo
     return idx;
 }
 
-__device__ __forceinline__ int vtx_find(const WarpShared *sh, int cnt, int id)
+__device__ __forceinline__ int ic(const int4 &v, int i) { return i == 0 ? v.x : (i == 1 ? v.y : v.z); }
+
+// neighbour of staged triangle j across edge e: staged index and global ref (uniform write)
+__device__ __forceinline__ void set_nb(WarpShared *sh, int j, int e, int lj, int gref)
 {
-    int idx = -1;
-    for (int base = 0; base < cnt; base += 32) {
-        int j = base + (threadIdx.x & 31);
-        bool hit = j < cnt && sh->vid[j] == id;
-        unsigned b = __ballot_sync(FULL, hit);
-        if (b) {
-            idx = base + __ffs(b) - 1;
-            break;
-        }
-    }
-    return idx;
+    reinterpret_cast<int *>(&sh->lnl[j])[e] = lj;
+    reinterpret_cast<int *>(&sh->ln[j])[e] = gref;
 }
 
-struct Region {
-    int cnt;             // staged triangles
-    int vcnt;            // staged vertices
-    unsigned long long dirty;  // modified staged triangles
-};
-
-__device__ __forceinline__ int2 vxy_of(const WarpShared *sh, const Region &R, int id)
+__device__ __forceinline__ int gref_of(const WarpShared *sh, int lref)
 {
-    if (id < 0) return make_int2(0, 0);
-    int j = vtx_find(sh, R.vcnt, id);
-    return j >= 0 ? sh->vxy[j] : make_int2(0, 0);
+    return (sh->lslot[lref >> 2] << 2) | (lref & 3);
 }
 
-// stage the vertices of triangle v that are not yet known (one round trip)
-__device__ bool stage_vertices(Warp &w, const Dev &d, Region &R, int4 v)
-{
-    WarpShared *sh = w.sh;
-    int ids[3] = {v.x, v.y, v.z};
-    for (int c = 0; c < 3; ++c) {
-        int id = ids[c];
-        if (id < 0) continue;
-        if (vtx_find(sh, R.vcnt, id) >= 0) continue;
-        if (R.vcnt >= LV) return false;
-        int2 x = make_int2(0, 0);
-        if (w.lane == 0) x = __ldcg(d.xy + id);
-        x = bcast2(x, 0);
-        if (w.lane == 0) {
-            sh->vid[R.vcnt] = id;
-            sh->vxy[R.vcnt] = x;
-        }
-        __syncwarp();
-        R.vcnt++;
-    }
-    return true;
-}
-
-// Claim and stage one more triangle (read under the claim, so no validation is
-// needed).  Returns its staged index, or -1 when the claim fails or space runs out.
-__device__ int ensure_local(Warp &w, const Dev &d, Region &R, int slot)
+// Claim and stage one more triangle, read under the claim (so no validation is
+// needed), with its vertex coordinates and its links to the staged triangles.
+// Returns its staged index, or -1 when the claim fails or space runs out.
+__device__ __noinline__ int ensure_local(Warp &w, const Dev &d, Region &R, int slot)
 {
     WarpShared *sh = w.sh;
     int j = local_find(sh, R.cnt, slot);
     if (j >= 0) return j;
-    if (R.cnt >= LM || w.ncl >= MAXC) return -1;
+    if (R.cnt >= LM || w.ncl >= MAXC || slot < 0 || slot >= d.cap) return -1;
     int mine = w.lane == 0 ? slot : -1;
     if (!claim_lanes(w, d, mine, 1)) return -1;
     int4 v, nb;
     load_tri(w, d, slot, v, nb);
     if (!(v.w & ALIVE)) return -1;
-    if (w.lane == 0) {
-        sh->lslot[R.cnt] = slot;
-        sh->lv[R.cnt] = v;
-        sh->ln[R.cnt] = nb;
+    int2 p0, p1, p2, pz;
+    load_xy4(w, d, v.x, v.y, v.z, KDT_GHOST, p0, p1, p2, pz);
+    j = R.cnt++;
+    sh->lslot[j] = slot;
+    sh->lv[j] = v;
+    sh->ln[j] = nb;
+    sh->lp[j][0] = p0;
+    sh->lp[j][1] = p1;
+    sh->lp[j][2] = p2;
+    for (int e = 0; e < 3; ++e) {
+        int r = ic(nb, e);
+        int k = local_find(sh, R.cnt, r >> 2);
+        reinterpret_cast<int *>(&sh->lnl[j])[e] = k;
+        if (k >= 0) reinterpret_cast<int *>(&sh->lnl[k])[r & 3] = j;
     }
     __syncwarp();
-    j = R.cnt++;
-    if (!stage_vertices(w, d, R, v)) return -1;
     return j;
 }
 
-// set component e of the neighbour refs of the staged triangle with global ref `ref`
-__device__ __forceinline__ bool set_local_backptr(Warp &w, Region &R, int ref, int val)
+// make sure the neighbour of staged j across edge e is staged; its staged index or -1
+__device__ __forceinline__ int nb_staged(Warp &w, const Dev &d, Region &R, int j, int e)
 {
-    WarpShared *sh = w.sh;
-    int j = local_find(sh, R.cnt, ref >> 2);
-    if (j < 0) return false;
-    if (w.lane == 0) {
-        int4 n = sh->ln[j];
-        int e = ref & 3;
-        if (e == 0) n.x = val;
-        else if (e == 1) n.y = val;
-        else n.z = val;
-        sh->ln[j] = n;
-    }
-    __syncwarp();
-    R.dirty |= 1ull << j;
-    return true;
+    int k = ic(w.sh->lnl[j], e);
+    if (k >= 0) return k;
+    return ensure_local(w, d, R, ic(w.sh->ln[j], e) >> 2);
 }
 
 // Write every modified staged triangle back (lane-parallel), update pt_tri of their
@@ -137,6 +109,7 @@ __device__ __forceinline__ bool set_local_backptr(Warp &w, Region &R, int ref, i
 __device__ void write_back(Warp &w, const Dev &d, Region &R)
 {
     WarpShared *sh = w.sh;
+    __syncwarp();
     unsigned long long m = R.dirty;
     int nd = __popcll(m);
     int base = 0;
@@ -165,36 +138,17 @@ __device__ void write_back(Warp &w, const Dev &d, Region &R)
     release_all(w, d);
 }
 
-// Ear validity on the staged link (same rule as ear_valid).
-__device__ bool ear_ok(const WarpShared *sh, int m, int i, const Dev &d, unsigned *ex, unsigned *ti)
-{
-    return ear_valid(sh->L, sh->LX, m, i, d, ex, ti);
-}
-
 // Locate q in staged triangle j: -1 not inside, 0 inside, 1 on edge (*e), 2 on a vertex
 // (*vtx), 3 strictly outside a ghost's hull edge.
-__device__ __forceinline__ int locate_in(const WarpShared *sh, const Region &R, int j, int2 q, int *e, int *vtx)
+__device__ __forceinline__ int locate_in(const WarpShared *sh, int j, int2 q, int *e, int *vtx)
 {
     int4 v = sh->lv[j];
     if (!(v.w & ALIVE)) return -1;
-    int g = v.x == KDT_GHOST ? 0 : (v.y == KDT_GHOST ? 1 : (v.z == KDT_GHOST ? 2 : -1));
-    // coordinates through the staged vertex table (lane-local search)
-    int2 p[3];
-    int ids[3] = {v.x, v.y, v.z};
-    for (int c = 0; c < 3; ++c) {
-        p[c] = make_int2(0, 0);
-        if (ids[c] < 0) continue;
-        for (int t = 0; t < R.vcnt; ++t)
-            if (sh->vid[t] == ids[c]) {
-                p[c] = sh->vxy[t];
-                break;
-            }
-    }
-    if (g >= 0) {
-        int2 pu = p[(g + 1) % 3], pv = p[(g + 2) % 3];
-        return orient2d(pu, pv, q) > 0 ? 3 : -1;
-    }
-    int o0 = orient2d(p[1], p[2], q), o1 = orient2d(p[2], p[0], q), o2 = orient2d(p[0], p[1], q);
+    int2 p0 = sh->lp[j][0], p1 = sh->lp[j][1], p2 = sh->lp[j][2];
+    if (v.x == KDT_GHOST) return orient2d(p1, p2, q) > 0 ? 3 : -1;
+    if (v.y == KDT_GHOST) return orient2d(p2, p0, q) > 0 ? 3 : -1;
+    if (v.z == KDT_GHOST) return orient2d(p0, p1, q) > 0 ? 3 : -1;
+    int o0 = orient2d(p1, p2, q), o1 = orient2d(p2, p0, q), o2 = orient2d(p0, p1, q);
     if (o0 < 0 || o1 < 0 || o2 < 0) return -1;
     int zeros = (o0 == 0) + (o1 == 0) + (o2 == 0);
     if (zeros == 0) return 0;
@@ -206,97 +160,97 @@ __device__ __forceinline__ int locate_in(const WarpShared *sh, const Region &R, 
     return 2;
 }
 
-// Staged fan around q: triangles (q, W[k], W[k+1]) into staged entries X[k]; O[k]
-// is the global ref of the outer neighbour across (W[k], W[k+1]) (staged).
-__device__ bool local_fan(Warp &w, Region &R, int q, const int *W, const int *O, const int *X, int m)
+// Staged fan around q: triangles (q, W[k], W[k+1]) into staged entries X[k]; OL[k] is
+// the staged ref (index << 2 | edge) of the outer neighbour across (W[k], W[k+1]).
+__device__ void local_fan(WarpShared *sh, Region &R, int q, int2 pq, const int *W, const int2 *WX,
+                          const int *OL, const int *X, int m)
 {
-    WarpShared *sh = w.sh;
-    if (w.lane == 0) {
-        for (int k = 0; k < m; ++k) {
-            int kn = (k + 1) % m, kp = (k + m - 1) % m;
-            sh->lv[X[k]] = make_int4(q, W[k], W[kn], ALIVE);
-            sh->ln[X[k]] = make_int4(O[k], (sh->lslot[X[kn]] << 2) | 2, (sh->lslot[X[kp]] << 2) | 1, 0);
-        }
-    }
-    __syncwarp();
     for (int k = 0; k < m; ++k) {
-        R.dirty |= 1ull << X[k];
-        if (!set_local_backptr(w, R, O[k], (sh->lslot[X[k]] << 2) | 0)) return false;
+        int kn = k + 1 == m ? 0 : k + 1, kp = k == 0 ? m - 1 : k - 1;
+        int x = X[k], o = OL[k];
+        sh->lv[x] = make_int4(q, W[k], W[kn], ALIVE);
+        sh->lp[x][0] = pq;
+        sh->lp[x][1] = WX[k];
+        sh->lp[x][2] = WX[kn];
+        set_nb(sh, x, 0, o >> 2, gref_of(sh, o));
+        set_nb(sh, x, 1, X[kn], (sh->lslot[X[kn]] << 2) | 2);
+        set_nb(sh, x, 2, X[kp], (sh->lslot[X[kp]] << 2) | 1);
+        set_nb(sh, o >> 2, o & 3, x, (sh->lslot[x] << 2) | 0);
+        R.dirty |= (1ull << x) | (1ull << (o >> 2));
     }
-    return true;
 }
 
-// Lawson flips of the edges opposite p on the staged region.  Entries are (staged
-// index, edge).  A flip whose quadrilateral or outer ring leaves the region stages
-// the missing triangles first; if that fails the remaining stack is returned to the
-// caller (converted to global slots) with *top_out > 0.
-__device__ void local_lawson(Warp &w, const Dev &d, Region &R, int p, int top, int *top_out, bool *aborted)
+// Lawson flips of the edges opposite p on the staged region (stack entries: staged
+// index, edge).  Triangles a flip needs beyond the region are claimed and staged; if
+// that fails, the remaining stack is handed back with *top_out > 0.
+__device__ void local_lawson(Warp &w, const Dev &d, Region &R, int p, int top, int *top_out)
 {
     WarpShared *sh = w.sh;
-    *aborted = false;
     while (top > 0) {
         int2 ent = sh->stack[top - 1];
-        __syncwarp();
         --top;
         int T = ent.x, e = ent.y;
-        int4 v = sh->lv[T], nb = sh->ln[T];
-        if (!(v.w & ALIVE) || comp(v, e) != p) continue;
-        int ref = comp(nb, e);
-        int U = ensure_local(w, d, R, ref >> 2);
+        int4 v = sh->lv[T];
+        if (!(v.w & ALIVE) || ic(v, e) != p) continue;
+        int U = nb_staged(w, d, R, T, e);
         if (U < 0) {
-            // push the entry back and hand the rest to the global path
-            if (w.lane == 0) sh->stack[top] = ent;
             __syncwarp();
+            sh->stack[top] = ent;
             *top_out = top + 1;
-            *aborted = true;
             return;
         }
-        int f = ref & 3;
-        int4 uv = sh->lv[U], un = sh->ln[U];
-        int a = comp(v, (e + 1) % 3), b = comp(v, (e + 2) % 3), dd = comp(uv, f);
-        int2 pv[3];
-        pv[e] = vxy_of(sh, R, p);
-        pv[(e + 1) % 3] = vxy_of(sh, R, a);
-        pv[(e + 2) % 3] = vxy_of(sh, R, b);
-        int2 pd = vxy_of(sh, R, dd);
+        int f = ic(sh->ln[T], e) & 3;
+        int4 uv = sh->lv[U];
+        int e1 = e == 2 ? 0 : e + 1, e2 = e == 0 ? 2 : e - 1;
+        int f1 = f == 2 ? 0 : f + 1, f2 = f == 0 ? 2 : f - 1;
+        int a = ic(v, e1), b = ic(v, e2), dd = ic(uv, f);
+        int2 pp = sh->lp[T][e], pa = sh->lp[T][e1], pb = sh->lp[T][e2], pd = sh->lp[U][f];
         w.cnt[C_FLIP_TESTS]++;
-        if (!conflict(v.x, v.y, v.z, pv[0], pv[1], pv[2], dd, pd, d.use_filter, &w.cnt[C_EXACT], &w.cnt[C_TIES]))
+        // the test is on the triangle in its stored rotation
+        int2 q0 = sh->lp[T][0], q1 = sh->lp[T][1], q2 = sh->lp[T][2];
+        if (!conflict(v.x, v.y, v.z, q0, q1, q2, dd, pd, d.use_filter, &w.cnt[C_EXACT], &w.cnt[C_TIES]))
             continue;
-        // stage the four outer neighbours (back-pointers change)
-        int nt_a = comp(nb, (e + 1) % 3), nt_b = comp(nb, (e + 2) % 3);
-        int nu_b = comp(un, (f + 1) % 3), nu_a = comp(un, (f + 2) % 3);
-        bool ok = ensure_local(w, d, R, nt_a >> 2) >= 0 && ensure_local(w, d, R, nt_b >> 2) >= 0 &&
-                  ensure_local(w, d, R, nu_a >> 2) >= 0 && ensure_local(w, d, R, nu_b >> 2) >= 0;
-        if (!ok) {
-            if (w.lane == 0) sh->stack[top] = ent;
+        // the four outer neighbours get new back-pointers: stage them
+        int Ta = nb_staged(w, d, R, T, e1), Tb = nb_staged(w, d, R, T, e2);
+        int Ub = Ta >= 0 && Tb >= 0 ? nb_staged(w, d, R, U, f1) : -1;
+        int Ua = Ub >= 0 ? nb_staged(w, d, R, U, f2) : -1;
+        if (Ua < 0) {
             __syncwarp();
+            sh->stack[top] = ent;
             *top_out = top + 1;
-            *aborted = true;
             return;
         }
+        int ga = ic(sh->ln[T], e1), gb = ic(sh->ln[T], e2);    // nt_a, nt_b
+        int hb = ic(sh->ln[U], f1), ha = ic(sh->ln[U], f2);    // nu_b, nu_a
         int sT = sh->lslot[T], sU = sh->lslot[U];
-        if (w.lane == 0) {
-            sh->lv[T] = make_int4(p, a, dd, ALIVE);
-            sh->ln[T] = make_int4(nu_b, (sU << 2) | 2, nt_b, 0);
-            sh->lv[U] = make_int4(p, dd, b, ALIVE);
-            sh->ln[U] = make_int4(nu_a, nt_a, (sT << 2) | 1, 0);
-        }
-        __syncwarp();
-        R.dirty |= (1ull << T) | (1ull << U);
-        set_local_backptr(w, R, nu_b, (sT << 2) | 0);
-        set_local_backptr(w, R, nt_b, (sT << 2) | 2);
-        set_local_backptr(w, R, nu_a, (sU << 2) | 0);
-        set_local_backptr(w, R, nt_a, (sU << 2) | 1);
+        __syncwarp();  // every lane has read T, U and the entry before any lane writes
+        // T = (p, a, d), U = (p, d, b)
+        sh->lv[T] = make_int4(p, a, dd, ALIVE);
+        sh->lp[T][0] = pp;
+        sh->lp[T][1] = pa;
+        sh->lp[T][2] = pd;
+        sh->lv[U] = make_int4(p, dd, b, ALIVE);
+        sh->lp[U][0] = pp;
+        sh->lp[U][1] = pd;
+        sh->lp[U][2] = pb;
+        set_nb(sh, T, 0, Ub, hb);
+        set_nb(sh, T, 1, U, (sU << 2) | 2);
+        set_nb(sh, T, 2, Tb, gb);
+        set_nb(sh, U, 0, Ua, ha);
+        set_nb(sh, U, 1, Ta, ga);
+        set_nb(sh, U, 2, T, (sT << 2) | 1);
+        set_nb(sh, Ub, hb & 3, T, (sT << 2) | 0);
+        set_nb(sh, Tb, gb & 3, T, (sT << 2) | 2);
+        set_nb(sh, Ua, ha & 3, U, (sU << 2) | 0);
+        set_nb(sh, Ta, ga & 3, U, (sU << 2) | 1);
+        R.dirty |= (1ull << T) | (1ull << U) | (1ull << Ta) | (1ull << Tb) | (1ull << Ua) | (1ull << Ub);
         w.cnt[C_FLIPS]++;
         if (top + 2 > STACK) {
             w.cnt[C_STACK_DROP]++;
             continue;
         }
-        if (w.lane == 0) {
-            sh->stack[top] = make_int2(T, 0);
-            sh->stack[top + 1] = make_int2(U, 0);
-        }
-        __syncwarp();
+        sh->stack[top] = make_int2(T, 0);
+        sh->stack[top + 1] = make_int2(U, 0);
         top += 2;
     }
     *top_out = 0;
@@ -329,7 +283,6 @@ __device__ int move_point(Warp &w, const Dev &d, int p, int2 q, int &s0, int &s1
         // speculative read of the star and the ring (one round trip), then claim both
         Region R;
         R.cnt = 2 * k;
-        R.vcnt = 0;
         R.dirty = 0;
         for (int i = w.lane; i < 2 * k; i += 32) {
             int slot = i < k ? sh->S[i] : (sh->ON[i - k] >> 2);
@@ -340,7 +293,7 @@ __device__ int move_point(Warp &w, const Dev &d, int p, int2 q, int &s0, int &s1
         __syncwarp();
         bool ok = claim_list(w, d, sh->lslot, 2 * k);
         if (ok) {
-            // validate under the claims; stage the vertex coordinates in the same pass
+            // validate under the claims and load every vertex's coordinates (one pass)
             bool good = true;
             for (int i = w.lane; i < 2 * k; i += 32) {
                 int slot = sh->lslot[i];
@@ -350,9 +303,13 @@ __device__ int move_point(Warp &w, const Dev &d, int p, int2 q, int &s0, int &s1
                        nb.y == n0.y && nb.z == n0.z && (v.w & ALIVE);
                 if (i < k) {
                     int I = sh->I[i];
-                    good = good && comp(v, I) == p && comp(v, (I + 1) % 3) == sh->L[i] && comp(nb, I) == sh->ON[i] &&
-                           (comp(nb, (I + 1) % 3) >> 2) == sh->S[(i + 1) % k];
+                    good = good && ic(v, I) == p && ic(v, (I + 1) % 3) == sh->L[i] && ic(nb, I) == sh->ON[i] &&
+                           (ic(nb, (I + 1) % 3) >> 2) == sh->S[(i + 1) % k];
                 }
+                int2 z = make_int2(0, 0);
+                sh->lp[i][0] = v.x >= 0 ? __ldcg(d.xy + v.x) : z;
+                sh->lp[i][1] = v.y >= 0 ? __ldcg(d.xy + v.y) : z;
+                sh->lp[i][2] = v.z >= 0 ? __ldcg(d.xy + v.z) : z;
             }
             ok = __all_sync(FULL, good);
         }
@@ -363,26 +320,32 @@ __device__ int move_point(Warp &w, const Dev &d, int p, int2 q, int &s0, int &s1
         }
         long long t2 = clock64();
         w.cnt[C_CYC_CLAIM] += (unsigned)((t2 - t1) >> 6);
-        // vertex table: link vertices (coordinates into LX too) and ring apexes
-        for (int i = w.lane; i < k; i += 32) {
-            int lv = sh->L[i];
-            int2 x = lv >= 0 ? __ldcg(d.xy + lv) : make_int2(0, 0);
-            sh->LX[i] = x;
-            sh->vid[i] = lv;
-            sh->vxy[i] = x;
-            int4 rv = sh->lv[k + i];
-            int ap = comp(rv, sh->ON[i] & 3);
-            sh->vid[k + i] = ap;
-            sh->vxy[k + i] = ap >= 0 ? __ldcg(d.xy + ap) : make_int2(0, 0);
-        }
-        __syncwarp();
-        R.vcnt = 2 * k;
-        // ring duplicates (a triangle adjacent to two link edges) keep their first copy:
-        // point later copies at an unused slot id so lookups find the first one
+        // a ring triangle adjacent to two link edges is staged once: later copies get
+        // an unused negative slot id so that lookups find the first one
         for (int i = w.lane; i < k; i += 32) {
             int slot = sh->lslot[k + i];
             for (int j = 0; j < i; ++j)
                 if (sh->lslot[k + j] == slot) sh->lslot[k + i] = -2 - i;
+        }
+        __syncwarp();
+        // staged neighbour indices, link coordinates and outer refs of the link edges
+        for (int i = w.lane; i < 2 * k; i += 32) {
+            int4 nb = sh->ln[i];
+            int l0 = -1, l1 = -1, l2 = -1;
+            for (int t = 0; t < 2 * k; ++t) {
+                int s = sh->lslot[t];
+                if (l0 < 0 && s == (nb.x >> 2)) l0 = t;
+                if (l1 < 0 && s == (nb.y >> 2)) l1 = t;
+                if (l2 < 0 && s == (nb.z >> 2)) l2 = t;
+            }
+            sh->lnl[i] = make_int4(l0, l1, l2, 0);
+            if (i < k) {
+                int I = sh->I[i];
+                sh->LX[i] = sh->lp[i][(I + 1) % 3];
+                // the outer triangle of link edge i: the neighbour of star triangle i across I
+                int o = I == 0 ? l0 : (I == 1 ? l1 : l2);
+                sh->EO[i] = (o << 2) | (sh->ON[i] & 3);
+            }
         }
         __syncwarp();
         // ---- degenerate check (as in delete_point)
@@ -398,7 +361,7 @@ __device__ int move_point(Warp &w, const Dev &d, int p, int2 q, int &s0, int &s1
                 bool finite_ring = false;
                 for (int i = 0; i < k; ++i) {
                     if (sh->L[i] == KDT_GHOST || sh->L[(i + 1) % k] == KDT_GHOST) continue;
-                    int4 ov = sh->lv[k + i];
+                    int4 ov = sh->lv[sh->EO[i] >> 2];
                     if (ov.x != KDT_GHOST && ov.y != KDT_GHOST && ov.z != KDT_GHOST) finite_ring = true;
                 }
                 if (!finite_ring) {
@@ -414,7 +377,7 @@ __device__ int move_point(Warp &w, const Dev &d, int p, int2 q, int &s0, int &s1
             unsigned ex = 0, ti = 0;
             for (int base = 0; base < m && chosen < 0; base += 32) {
                 int i = base + w.lane;
-                bool v = i < m && ear_ok(sh, m, i, d, &ex, &ti);
+                bool v = i < m && ear_valid(sh->L, sh->LX, m, i, d, &ex, &ti);
                 unsigned bm = __ballot_sync(FULL, v);
                 if (bm) chosen = base + __ffs(bm) - 1;
             }
@@ -424,46 +387,52 @@ __device__ int move_point(Warp &w, const Dev &d, int p, int2 q, int &s0, int &s1
                 release_all(w, d);
                 return DEV_INTERNAL;
             }
-            int i = chosen, i1 = (i + 1) % m, i2 = (i + 2) % m;
+            int i = chosen, i1 = i + 1 == m ? 0 : i + 1, i2 = i1 + 1 == m ? 0 : i1 + 1;
             int X = newc++;  // staged index == star position
-            int sX = sh->S[X];
-            int on_i = sh->ON[i], on_i1 = sh->ON[i1];
-            if (w.lane == 0) {
-                sh->lv[X] = make_int4(sh->L[i], sh->L[i1], sh->L[i2], ALIVE);
-                sh->ln[X] = make_int4(on_i1, -1, on_i, 0);
-                sh->ON[i] = (sX << 2) | 1;
-            }
+            int eo_i = sh->EO[i], eo_i1 = sh->EO[i1];
+            int Li = sh->L[i], Li1 = sh->L[i1], Li2 = sh->L[i2];
+            int2 Xi = sh->LX[i], Xi1 = sh->LX[i1], Xi2 = sh->LX[i2];
+            int sX = sh->lslot[X];
+            __syncwarp();  // every lane has read before any lane writes
+            sh->lv[X] = make_int4(Li, Li1, Li2, ALIVE);
+            sh->lp[X][0] = Xi;
+            sh->lp[X][1] = Xi1;
+            sh->lp[X][2] = Xi2;
+            set_nb(sh, X, 0, eo_i1 >> 2, gref_of(sh, eo_i1));
+            set_nb(sh, X, 1, -1, -1);  // the new diagonal: set when it is consumed
+            set_nb(sh, X, 2, eo_i >> 2, gref_of(sh, eo_i));
+            set_nb(sh, eo_i1 >> 2, eo_i1 & 3, X, (sX << 2) | 0);
+            set_nb(sh, eo_i >> 2, eo_i & 3, X, (sX << 2) | 2);
+            R.dirty |= (1ull << X) | (1ull << (eo_i >> 2)) | (1ull << (eo_i1 >> 2));
+            sh->EO[i] = (X << 2) | 1;
             __syncwarp();
-            R.dirty |= 1ull << X;
-            set_local_backptr(w, R, on_i1, (sX << 2) | 0);
-            set_local_backptr(w, R, on_i, (sX << 2) | 2);
-            // remove element i1
-            int lv = 0, onv = 0;
+            // remove element i1 (shift the tail down by one)
+            int lv = 0, eov = 0;
             int2 xv = make_int2(0, 0);
             int j = w.lane;
             bool mv = j >= i1 && j < m - 1;
             if (mv) {
                 lv = sh->L[j + 1];
-                onv = sh->ON[j + 1];
+                eov = sh->EO[j + 1];
                 xv = sh->LX[j + 1];
             }
             bool mv2 = j + 32 >= i1 && j + 32 < m - 1;
-            int lv2 = 0, onv2 = 0;
+            int lv2 = 0, eov2 = 0;
             int2 xv2 = make_int2(0, 0);
             if (mv2) {
                 lv2 = sh->L[j + 33];
-                onv2 = sh->ON[j + 33];
+                eov2 = sh->EO[j + 33];
                 xv2 = sh->LX[j + 33];
             }
             __syncwarp();
             if (mv) {
                 sh->L[j] = lv;
-                sh->ON[j] = onv;
+                sh->EO[j] = eov;
                 sh->LX[j] = xv;
             }
             if (mv2) {
                 sh->L[j + 32] = lv2;
-                sh->ON[j + 32] = onv2;
+                sh->EO[j + 32] = eov2;
                 sh->LX[j + 32] = xv2;
             }
             __syncwarp();
@@ -471,48 +440,46 @@ __device__ int move_point(Warp &w, const Dev &d, int p, int2 q, int &s0, int &s1
         }
         {
             int X = newc++;
-            int sX = sh->S[X];
-            int on0 = sh->ON[0], on1 = sh->ON[1], on2 = sh->ON[2];
-            if (w.lane == 0) {
-                sh->lv[X] = make_int4(sh->L[0], sh->L[1], sh->L[2], ALIVE);
-                sh->ln[X] = make_int4(on1, on2, on0, 0);
-            }
+            int e0 = sh->EO[0], e1 = sh->EO[1], e2 = sh->EO[2];
+            int L0 = sh->L[0], L1 = sh->L[1], L2 = sh->L[2];
+            int2 P0 = sh->LX[0], P1 = sh->LX[1], P2 = sh->LX[2];
+            int sX = sh->lslot[X];
             __syncwarp();
-            R.dirty |= 1ull << X;
-            set_local_backptr(w, R, on1, (sX << 2) | 0);
-            set_local_backptr(w, R, on2, (sX << 2) | 1);
-            set_local_backptr(w, R, on0, (sX << 2) | 2);
+            sh->lv[X] = make_int4(L0, L1, L2, ALIVE);
+            sh->lp[X][0] = P0;
+            sh->lp[X][1] = P1;
+            sh->lp[X][2] = P2;
+            set_nb(sh, X, 0, e1 >> 2, gref_of(sh, e1));
+            set_nb(sh, X, 1, e2 >> 2, gref_of(sh, e2));
+            set_nb(sh, X, 2, e0 >> 2, gref_of(sh, e0));
+            set_nb(sh, e1 >> 2, e1 & 3, X, (sX << 2) | 0);
+            set_nb(sh, e2 >> 2, e2 & 3, X, (sX << 2) | 1);
+            set_nb(sh, e0 >> 2, e0 & 3, X, (sX << 2) | 2);
+            R.dirty |= (1ull << X) | (1ull << (e0 >> 2)) | (1ull << (e1 >> 2)) | (1ull << (e2 >> 2));
         }
         // spares: staged entries k-2, k-1 (dead)
-        int X0 = k - 2, X1 = k - 1;
-        if (w.lane == 0) {
-            sh->lv[X0] = make_int4(0, 0, 0, 0);
-            sh->lv[X1] = make_int4(0, 0, 0, 0);
-            d.pt_tri[p] = -1;
-        }
-        __syncwarp();
+        const int X0 = k - 2, X1 = k - 1;
+        sh->lv[X0] = make_int4(0, 0, 0, 0);
+        sh->lv[X1] = make_int4(0, 0, 0, 0);
+        sh->lnl[X0] = make_int4(-1, -1, -1, 0);
+        sh->lnl[X1] = make_int4(-1, -1, -1, 0);
+        if (w.lane == 0) d.pt_tri[p] = -1;
         R.dirty |= (1ull << X0) | (1ull << X1);
         w.cnt[C_DEG_DEL] += k;
         w.cnt[C_DELETES]++;
-        s0 = sh->S[X0];
-        s1 = sh->S[X1];
-        hint = sh->S[0];
+        s0 = sh->lslot[X0];
+        s1 = sh->lslot[X1];
+        hint = sh->lslot[0];
         // Update (Fig. 4): p takes its new position
         if (w.lane == 0) d.xy[p] = q;
-        // q joins the vertex table
-        if (w.lane == 0) {
-            sh->vid[R.vcnt] = p;
-            sh->vxy[R.vcnt] = q;
-        }
         __syncwarp();
-        R.vcnt++;
         // ---- 2. locate q among the staged triangles
         int where = -1, te = 0, tvtx = -1, tj = -1;
         for (int base = 0; base < R.cnt && tj < 0; base += 32) {
             int j = base + w.lane;
             int e = 0, vt = -1;
-            int r = j < R.cnt && sh->lslot[j] >= 0 ? locate_in(sh, R, j, q, &e, &vt) : -1;
-            // prefer a finite hit; a ghost hit (outside the hull) goes to the global path
+            int r = j < R.cnt && sh->lslot[j] >= 0 ? locate_in(sh, j, q, &e, &vt) : -1;
+            // a finite hit; a ghost hit (outside the hull) goes to the global path
             unsigned bm = __ballot_sync(FULL, r >= 0 && r <= 2);
             if (bm) {
                 int src = __ffs(bm) - 1;
@@ -533,68 +500,63 @@ __device__ int move_point(Warp &w, const Dev &d, int p, int2 q, int &s0, int &s1
             if (st == d.stamp) return MV_DEFER;
             return DEV_DUPLICATE;
         }
-        // ---- 3. split (staged); make sure every triangle whose refs change is staged
-        int4 v = sh->lv[tj], nb = sh->ln[tj];
-        int *W = sh->tmp, *O = sh->tmp + 8, *Xs = sh->tmp + 16;
+        // ---- 3. split (staged); every triangle whose refs change must be staged
+        int4 v = sh->lv[tj];
+        int *W = sh->tmp, *OL = sh->tmp + 8, *Xs = sh->tmp + 16;
+        int2 *WX = reinterpret_cast<int2 *>(sh->tmp + 24);
         int mf;
-        bool okf = true;
+        bool okf;
         if (where == 1) {
-            int e = te;
-            int Uj = ensure_local(w, d, R, comp(nb, e) >> 2);
-            okf = Uj >= 0;
-            int4 uv = make_int4(0, 0, 0, 0), un = make_int4(0, 0, 0, 0);
-            int f = comp(nb, e) & 3;
+            int e = te, e1 = (e + 1) % 3, e2 = (e + 2) % 3;
+            int Uj = nb_staged(w, d, R, tj, e);
+            int f = ic(sh->ln[tj], e) & 3, f1 = (f + 1) % 3, f2 = (f + 2) % 3;
+            okf = Uj >= 0 && nb_staged(w, d, R, tj, e1) >= 0 && nb_staged(w, d, R, tj, e2) >= 0 &&
+                  nb_staged(w, d, R, Uj, f1) >= 0 && nb_staged(w, d, R, Uj, f2) >= 0;
             if (okf) {
-                uv = sh->lv[Uj];
-                un = sh->ln[Uj];
-                okf = ensure_local(w, d, R, comp(nb, (e + 1) % 3) >> 2) >= 0 &&
-                      ensure_local(w, d, R, comp(nb, (e + 2) % 3) >> 2) >= 0 &&
-                      ensure_local(w, d, R, comp(un, (f + 1) % 3) >> 2) >= 0 &&
-                      ensure_local(w, d, R, comp(un, (f + 2) % 3) >> 2) >= 0;
-            }
-            if (okf && w.lane == 0) {
-                int a = comp(v, e), b = comp(v, (e + 1) % 3), c = comp(v, (e + 2) % 3), dd = comp(uv, f);
-                W[0] = a; W[1] = b; W[2] = dd; W[3] = c;
-                O[0] = comp(nb, (e + 2) % 3);
-                O[1] = comp(un, (f + 1) % 3);
-                O[2] = comp(un, (f + 2) % 3);
-                O[3] = comp(nb, (e + 1) % 3);
+                int4 uv = sh->lv[Uj];
+                W[0] = ic(v, e);  WX[0] = sh->lp[tj][e];
+                W[1] = ic(v, e1); WX[1] = sh->lp[tj][e1];
+                W[2] = ic(uv, f); WX[2] = sh->lp[Uj][f];
+                W[3] = ic(v, e2); WX[3] = sh->lp[tj][e2];
+                // outer staged refs: (a,b) t opp c; (b,d) u opp c; (d,c) u opp b; (c,a) t opp b
+                OL[0] = (ic(sh->lnl[tj], e2) << 2) | (ic(sh->ln[tj], e2) & 3);
+                OL[1] = (ic(sh->lnl[Uj], f1) << 2) | (ic(sh->ln[Uj], f1) & 3);
+                OL[2] = (ic(sh->lnl[Uj], f2) << 2) | (ic(sh->ln[Uj], f2) & 3);
+                OL[3] = (ic(sh->lnl[tj], e1) << 2) | (ic(sh->ln[tj], e1) & 3);
                 Xs[0] = tj; Xs[1] = Uj; Xs[2] = X0; Xs[3] = X1;
+                w.cnt[C_SPLIT_EDGE]++;
             }
             mf = 4;
-            if (okf) w.cnt[C_SPLIT_EDGE]++;
         } else {
-            okf = ensure_local(w, d, R, nb.x >> 2) >= 0 && ensure_local(w, d, R, nb.y >> 2) >= 0 &&
-                  ensure_local(w, d, R, nb.z >> 2) >= 0;
-            if (okf && w.lane == 0) {
+            okf = nb_staged(w, d, R, tj, 0) >= 0 && nb_staged(w, d, R, tj, 1) >= 0 &&
+                  nb_staged(w, d, R, tj, 2) >= 0;
+            if (okf) {
                 W[0] = v.x; W[1] = v.y; W[2] = v.z;
-                O[0] = nb.z; O[1] = nb.x; O[2] = nb.y;
+                WX[0] = sh->lp[tj][0]; WX[1] = sh->lp[tj][1]; WX[2] = sh->lp[tj][2];
+                OL[0] = (sh->lnl[tj].z << 2) | (sh->ln[tj].z & 3);
+                OL[1] = (sh->lnl[tj].x << 2) | (sh->ln[tj].x & 3);
+                OL[2] = (sh->lnl[tj].y << 2) | (sh->ln[tj].y & 3);
                 Xs[0] = tj; Xs[1] = X0; Xs[2] = X1;
             }
             mf = 3;
         }
-        __syncwarp();
         if (!okf) {
             write_back(w, d, R);
             return MV_GLOBAL;
         }
-        // the spare entries get slots s0, s1 already (lslot of X0 / X1)
-        if (!local_fan(w, R, p, W, O, Xs, mf)) {
-            // a needed neighbour was not staged (cannot happen after ensure_local)
-            write_back(w, d, R);
-            return DEV_INTERNAL;
-        }
+        local_fan(sh, R, p, q, W, WX, OL, Xs, mf);
         w.cnt[C_INSERTS]++;
         // ---- 4. Lawson flips of the edges opposite q
-        if (w.lane == 0)
-            for (int j = 0; j < mf; ++j) sh->stack[j] = make_int2(Xs[j], 0);
         __syncwarp();
+        for (int j = 0; j < mf; ++j) sh->stack[j] = make_int2(Xs[j], 0);
         int left = 0;
-        bool aborted = false;
-        local_lawson(w, d, R, p, mf, &left, &aborted);
+        local_lawson(w, d, R, p, mf, &left);
         // convert what is left to global (slot, edge) entries before the region goes
-        if (left > 0 && w.lane == 0)
-            for (int j = 0; j < left; ++j) sh->stack[j] = make_int2(sh->lslot[sh->stack[j].x], sh->stack[j].y);
+        __syncwarp();
+        for (int j = w.lane; j < left; j += 32) {
+            int2 en = sh->stack[j];
+            sh->stack[j] = make_int2(sh->lslot[en.x], en.y);
+        }
         __syncwarp();
         long long t3 = clock64();
         w.cnt[C_CYC_LOCAL] += (unsigned)((t3 - t2) >> 6);
