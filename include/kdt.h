@@ -100,7 +100,8 @@ typedef struct {
     int64_t cycles_move;          /* SM cycles summed over moved points (kinetic kernel)   */
     int64_t cycles_move_max;      /* longest single move, cycles                            */
     int64_t cycles_gather, cycles_claim, cycles_local, cycles_writeback; /* phase sums    */
-    int64_t reserved[8];
+    double step_graph_ms;         /* event-timed control copy + step graph (timing = 1)     */
+    int64_t reserved[7];
 } kdt_stats;
 
 /* ---- lifecycle ------------------------------------------------------------------ */

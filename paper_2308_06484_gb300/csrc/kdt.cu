@@ -69,7 +69,7 @@ struct kdt {
     int gen = 0;           // bumped whenever step buffers are (re)allocated
     // host side
     int *hscal = nullptr;  // pinned copy of the scalars
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
     kdt_stats stats{};
 };
 
@@ -158,6 +158,9 @@ Dev make_dev(kdt *h)
     d.use_filter = h->cfg.filter;
     d.retry_cap = h->cfg.retry_cap;
     d.ctl = nullptr;
+    d.viol = h->viol;
+    d.viol_count = h->scal + S_VIOL;
+    d.viol_cap = h->viol_cap;
     return d;
 }
 
@@ -430,9 +433,9 @@ void add_counters(kdt *h)
 }
 
 // Undo a step that failed after it started: restore the old positions and rebuild.
-int roll_back(kdt *h, int m)
+int roll_back(kdt *h, const int3 *mp, int m)
 {
-    k_restore_positions<<<(m + 255) / 256, 256, 0, h->stream>>>(h->xy, h->moves, h->old_xy, m);
+    k_restore_positions<<<(m + 255) / 256, 256, 0, h->stream>>>(h->xy, mp, h->old_xy, m);
     h->stats.kernel_launches++;
     return rebuild_positions(h);
 }
@@ -457,18 +460,13 @@ int verify_state(kdt *h, int64_t *bad)
 // kernel, deferred insertions, certification, and the copy of the status scalars to
 // the host.  With from_ctl the grids do not depend on m (the kernels read m and the
 // stamp from h->ctl), so the sequence can be captured once into a CUDA graph.
-int enqueue_step(kdt *h, cudaStream_t st, const Dev &d, int mi, bool from_ctl)
+int enqueue_step(kdt *h, cudaStream_t st, const Dev &d, const int3 *mp, int mi, bool from_ctl)
 {
     int cap = from_ctl ? h->mcap : mi;
     CK(cudaMemsetAsync(h->scal, 0, S_NUM * sizeof(int), st));
-    CK(cudaMemsetAsync(h->cell_cnt, 0, (size_t)h->ncells * sizeof(int), st));
-    k_intake<<<thread_grid(h, cap, 256), 256, 0, st>>>(d, h->moves, mi, h->grid, h->cfg.domain_bits, h->cell_cnt,
-                                                       h->old_xy, h->move_cell);
-    if (scan(h, h->cell_cnt, h->cell_off, h->ncells, h->scal + S_TOTAL, st)) return KDT_ERR_CUDA;
-    h->stats.kernel_launches -= 3;  // counted by the caller
-    CK(cudaMemsetAsync(h->cell_fill, 0, (size_t)h->ncells * sizeof(int), st));
-    k_scatter<<<thread_grid(h, cap, 256), 256, 0, st>>>(mi, h->move_cell, h->cell_off, h->cell_fill, h->order,
-                                                        h->scal + S_STATUS, from_ctl ? h->ctl : nullptr);
+    CK(cudaMemsetAsync(h->cell_cnt, 0xff, (size_t)h->ncells * sizeof(int), st));  // empty lists
+    k_intake_link<<<thread_grid(h, cap, 256), 256, 0, st>>>(d, mp, mi, h->grid, h->cfg.domain_bits, h->cell_cnt,
+                                                            h->move_cell, h->old_xy);
     // inside a capture an event record must be an external node to keep its timestamp
     unsigned evflags = from_ctl ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (h->cfg.timing) CK(cudaEventRecordWithFlags(h->ev0, st, evflags));
@@ -477,11 +475,9 @@ int enqueue_step(kdt *h, cudaStream_t st, const Dev &d, int mi, bool from_ctl)
         kblocks = (h->cfg.kinetic_warps + WPB - 1) / WPB;
         if (h->cfg.kinetic_warps < WPB) kthreads = 32 * h->cfg.kinetic_warps;
     }
-    k_kinetic<<<kblocks, kthreads, 0, st>>>(d, h->moves, h->order, h->cell_cnt, h->cell_off, h->ncells,
-                                            h->deferred, h->scal + S_DEFER, h->mcap);
+    k_kinetic<<<kblocks, kthreads, 0, st>>>(d, mp, h->cell_cnt, h->move_cell, h->ncells, h->deferred,
+                                            h->scal + S_DEFER, h->mcap, h->viol, h->viol_cap);
     if (h->cfg.timing) CK(cudaEventRecordWithFlags(h->ev1, st, evflags));
-    k_deferred<<<2, WPB * 32, 0, st>>>(d, h->deferred, h->scal + S_DEFER, h->mcap);
-    k_certify<<<thread_grid(h, 64ll * cap, 256), 256, 0, st>>>(d, 0, h->viol, h->scal + S_VIOL, h->viol_cap);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->hscal, h->scal, S_NUM * sizeof(int), cudaMemcpyDeviceToHost, st));
     return 0;
@@ -552,7 +548,8 @@ int kdt_create(kdt **out, const kdt_config *cfg, int device, void *cuda_stream)
         cudaMalloc(&h->ctl, 4 * sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&h->hctl, 4 * sizeof(int)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+        cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
+        cudaEventCreate(&h->ev2) != cudaSuccess || cudaEventCreate(&h->ev3) != cudaSuccess) {
         kdt_destroy(h);
         return KDT_ERR_CUDA;
     }
@@ -577,6 +574,8 @@ int kdt_destroy(kdt *h)
     if (h->cstream) cudaStreamDestroy(h->cstream);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
+    if (h->ev2) cudaEventDestroy(h->ev2);
+    if (h->ev3) cudaEventDestroy(h->ev3);
     delete h;
     return KDT_OK;
 }
@@ -594,7 +593,6 @@ int kdt_build(kdt *h, const int32_t *xy, int64_t n)
     CK(cudaMemcpyAsync(h->xy, xy, (size_t)n * sizeof(int2),
                        is_device_ptr(xy) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
     rc = rebuild_positions(h);
-    add_counters(h);
     return rc;
 }
 
@@ -604,7 +602,6 @@ int kdt_rebuild(kdt *h)
     if (!h->built) return KDT_ERR_STATE;
     CK(cudaSetDevice(h->device));
     int rc = rebuild_positions(h);
-    add_counters(h);
     return rc;
 }
 
@@ -619,8 +616,12 @@ int kdt_step(kdt *h, const kdt_move *moves, int64_t m)
     if (rc) return rc;
     cudaStream_t st = h->stream;
     const int mi = (int)m;
-    CK(cudaMemcpyAsync(h->moves, moves, (size_t)m * sizeof(int3),
-                       is_device_ptr(moves) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    // device moves are read in place; host moves are copied in first
+    const int3 *mp = (const int3 *)moves;
+    if (!is_device_ptr(moves)) {
+        CK(cudaMemcpyAsync(h->moves, moves, (size_t)m * sizeof(int3), cudaMemcpyHostToDevice, st));
+        mp = h->moves;
+    }
     h->stamp++;
     Dev d = make_dev(h);
     bool large = h->cfg.fallback && (double)m > (double)h->cfg.rebuild_ratio * (double)h->n;
@@ -629,22 +630,20 @@ int kdt_step(kdt *h, const kdt_move *moves, int64_t m)
         // far, it's better to rebuild the triangulation")
         CK(cudaMemsetAsync(h->scal, 0, S_NUM * sizeof(int), st));
         CK(cudaMemsetAsync(h->cell_cnt, 0, (size_t)h->ncells * sizeof(int), st));
-        k_intake<<<(mi + 255) / 256, 256, 0, st>>>(d, h->moves, mi, h->grid, h->cfg.domain_bits, h->cell_cnt,
+        k_intake<<<(mi + 255) / 256, 256, 0, st>>>(d, mp, mi, h->grid, h->cfg.domain_bits, h->cell_cnt,
                                                    h->old_xy, h->move_cell);
         h->stats.kernel_launches++;
         if (sync_scalars(h)) return KDT_ERR_CUDA;
         if (h->hscal[S_STATUS]) return dev_to_abi(h->hscal[S_STATUS]);
-        k_set_positions<<<(mi + 255) / 256, 256, 0, st>>>(h->xy, h->moves, mi);
+        k_set_positions<<<(mi + 255) / 256, 256, 0, st>>>(h->xy, mp, mi);
         h->stats.kernel_launches++;
         rc = rebuild_positions(h);
         if (rc) {
-            int rr = roll_back(h, mi);
-            add_counters(h);
+            int rr = roll_back(h, mp, mi);
             return rr ? rr : rc;
         }
         h->stats.steps++;
         h->stats.moves += m;
-        add_counters(h);
         return KDT_OK;
     }
     if (h->cfg.use_graph) {
@@ -656,7 +655,7 @@ int kdt_step(kdt *h, const kdt_move *moves, int64_t m)
             Dev dg = d;
             dg.ctl = h->ctl;
             CK(cudaStreamBeginCapture(h->cstream, cudaStreamCaptureModeThreadLocal));
-            int er = enqueue_step(h, h->cstream, dg, 0, true);
+            int er = enqueue_step(h, h->cstream, dg, nullptr, 0, true);
             cudaGraph_t g = nullptr;
             cudaError_t ce = cudaStreamEndCapture(h->cstream, &g);
             if (er || ce != cudaSuccess) {
@@ -669,14 +668,27 @@ int kdt_step(kdt *h, const kdt_move *moves, int64_t m)
         }
         h->hctl[0] = mi;
         h->hctl[1] = h->stamp;
-        CK(cudaMemcpyAsync(h->ctl, h->hctl, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
+        unsigned long long pa = (unsigned long long)(uintptr_t)mp;
+        h->hctl[2] = (int)(unsigned)(pa & 0xffffffffu);
+        h->hctl[3] = (int)(unsigned)(pa >> 32);
+        if (h->cfg.timing) CK(cudaEventRecord(h->ev2, st));
+        CK(cudaMemcpyAsync(h->ctl, h->hctl, 4 * sizeof(int), cudaMemcpyHostToDevice, st));
         CK(cudaGraphLaunch(h->gexec, st));
-        h->stats.kernel_launches += 8;
+        if (h->cfg.timing) CK(cudaEventRecord(h->ev3, st));
+        h->stats.kernel_launches += 2;
         CK(cudaStreamSynchronize(st));
     } else {
-        if (enqueue_step(h, st, d, mi, false)) return KDT_ERR_CUDA;
-        h->stats.kernel_launches += 8;
+        if (enqueue_step(h, st, d, mp, mi, false)) return KDT_ERR_CUDA;
+        h->stats.kernel_launches += 2;
         CK(cudaStreamSynchronize(st));
+    }
+    if (h->hscal[S_CERTPEND] && !h->hscal[S_STATUS]) {
+        // a long dirty list (global-path writes): certify it here, appending to the
+        // violations the kinetic kernel already recorded
+        k_certify<<<thread_grid(h, h->hscal[S_DIRTY], 256), 256, 0, st>>>(d, 0, h->viol, h->scal + S_VIOL,
+                                                                          h->viol_cap);
+        h->stats.kernel_launches++;
+        if (sync_scalars(h)) return KDT_ERR_CUDA;
     }
     if (h->cfg.timing) {
         float ms = 0.f;
@@ -684,11 +696,12 @@ int kdt_step(kdt *h, const kdt_move *moves, int64_t m)
             h->stats.kinetic_kernel_ms += ms;
             h->stats.kinetic_kernel_timed++;
         }
+        if (h->cfg.use_graph && cudaEventElapsedTime(&ms, h->ev2, h->ev3) == cudaSuccess)
+            h->stats.step_graph_ms += ms;
     }
     int s = h->hscal[S_STATUS];
     if (s == DEV_ARG || s == DEV_RANGE || s == DEV_DUP_ID) {
         // found at intake: nothing was modified
-        add_counters(h);
         return dev_to_abi(s);
     }
     if (s == 0) {
@@ -751,19 +764,17 @@ int kdt_step(kdt *h, const kdt_move *moves, int64_t m)
         h->stats.last_fallback_point = h->hscal[S_FAILPT];
         if (h->cfg.debug & 1) {
             h->built = true;  // keep the failed state for kdt_export_store
-            add_counters(h);
             return dev_to_abi(s);
         }
         bool allow = h->cfg.fallback || s == DEV_DUPLICATE || s == DEV_DEGENERATE;
         int rc2 = KDT_ERR_RETRY_EXHAUSTED;
         if (allow) {
-            k_set_positions<<<(mi + 255) / 256, 256, 0, st>>>(h->xy, h->moves, mi);
+            k_set_positions<<<(mi + 255) / 256, 256, 0, st>>>(h->xy, mp, mi);
             h->stats.kernel_launches++;
             rc2 = rebuild_positions(h);
         }
         if (rc2) {
-            int rr = roll_back(h, mi);
-            add_counters(h);
+            int rr = roll_back(h, mp, mi);
             if (rr) return rr;
             return allow ? rc2 : dev_to_abi(s);
         }
@@ -775,11 +786,9 @@ int kdt_step(kdt *h, const kdt_move *moves, int64_t m)
         int vr = verify_state(h, &bad);
         if (vr) return vr;
         if (bad) {
-            add_counters(h);
             return KDT_ERR_INTERNAL;
         }
     }
-    add_counters(h);
     return KDT_OK;
 }
 
@@ -843,6 +852,10 @@ int kdt_verify(kdt *h, int64_t *bad)
 int kdt_get_stats(const kdt *h, kdt_stats *out)
 {
     if (!h || !out) return KDT_ERR_ARG;
+    kdt *hm = const_cast<kdt *>(h);  // the device counters are merged in lazily
+    cudaSetDevice(hm->device);
+    cudaStreamSynchronize(hm->stream);
+    add_counters(hm);
     *out = h->stats;
     return KDT_OK;
 }
@@ -850,6 +863,9 @@ int kdt_get_stats(const kdt *h, kdt_stats *out)
 int kdt_reset_stats(kdt *h)
 {
     if (!h) return KDT_ERR_ARG;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    add_counters(h);
     memset(&h->stats, 0, sizeof h->stats);
     return KDT_OK;
 }

@@ -69,7 +69,11 @@ struct Dev {
     int dirty_cap;
     int *pt_stamp;       // step stamp of points moved in this step
     int stamp;
-    const int *ctl;      // graph-launched steps: ctl[0] = moves, ctl[1] = stamp (device)
+    const int *ctl;      // graph-launched steps: ctl[0] = moves, ctl[1] = stamp,
+                         // ctl[2..3] = the moves' device address
+    int *viol;           // edges found not locally Delaunay: (slot << 2) | edge
+    int *viol_count;
+    int viol_cap;
     unsigned long long *counters;
     int use_filter;
     int retry_cap;
@@ -191,6 +195,31 @@ __device__ __forceinline__ void flush_counters(const Warp &w, const Dev &d)
             if (w.cnt[i]) atomicAdd(d.counters + i, (unsigned long long)w.cnt[i]);
         if (w.cyc_max) atomicMax(d.counters + C_CYC_MAX, (unsigned long long)w.cyc_max);
     }
+}
+
+// ------------------------------------------------------------------ certification
+
+// Is edge e of live triangle t locally Delaunay?  Also checks that the adjacency is
+// reciprocal and the triangle counter-clockwise.  Returns 0 (fine), 1 (not locally
+// Delaunay), -1 (store inconsistent).
+__device__ int check_edge(const Dev &d, int t, const int4 &v, const int4 &nb, int e, unsigned *ex,
+                          unsigned *ti)
+{
+    int ref = comp(nb, e);
+    int U = ref >> 2, f = ref & 3;
+    if (U < 0 || U >= d.cap || f > 2) return -1;
+    int4 uv = __ldcg(d.tv + U);
+    int4 un = __ldcg(d.tn + U);
+    if (!(uv.w & ALIVE) || comp(un, f) != ((t << 2) | e)) return -1;
+    int a = comp(v, (e + 1) % 3), b = comp(v, (e + 2) % 3);
+    if (comp(uv, (f + 1) % 3) != b || comp(uv, (f + 2) % 3) != a) return -1;
+    int dd = comp(uv, f);
+    int2 z = make_int2(0, 0);
+    int2 p0 = v.x >= 0 ? __ldcg(d.xy + v.x) : z;
+    int2 p1 = v.y >= 0 ? __ldcg(d.xy + v.y) : z;
+    int2 p2 = v.z >= 0 ? __ldcg(d.xy + v.z) : z;
+    int2 pd = dd >= 0 ? __ldcg(d.xy + dd) : z;
+    return conflict(v.x, v.y, v.z, p0, p1, p2, dd, pd, d.use_filter, ex, ti) ? 1 : 0;
 }
 
 // ------------------------------------------------------------------ claims

@@ -1,7 +1,7 @@
 // Kernels of the kinetic Delaunay library.  Included once, by kdt.cu.
 //
-//   step:    k_intake -> scan -> k_scatter -> k_kinetic -> k_deferred -> k_certify
-//            (-> k_fixup / k_certify until no violation)
+//   step:    k_intake_link -> k_kinetic (last warp: deferred points, certification of
+//            global-path writes) (-> k_fixup / k_certify until no violation)
 //   build:   k_range / k_bbox -> k_hilbert -> scan -> k_place_order -> k_third -> k_init
 //            -> k_insert_level (one launch per level) -> k_certify_all (-> k_fixup ...)
 //   export:  k_exp_count -> scan -> k_exp_place -> k_exp_sortseg
@@ -17,7 +17,7 @@ constexpr int DEV_DUP_ID = 10;  // a move id repeated within one step (found at 
 enum Slot : int {
     S_STATUS = 0, S_DIRTY = 1, S_VIOL = 2, S_TRIS = 3, S_DEFER = 4, S_THIRD = 5,
     S_MINX = 6, S_MINY = 7, S_MAXX = 8, S_MAXY = 9, S_TOTAL = 10, S_BAD = 11, S_ALIVE = 12,
-    S_WRAPS = 13, S_FAILPT = 14, S_NUM = 16
+    S_WRAPS = 13, S_FAILPT = 14, S_DONE = 15, S_CERTPEND = 16, S_NUM = 20
 };
 
 __device__ __forceinline__ Warp make_warp(WarpShared *sh, int token, unsigned seed)
@@ -163,14 +163,48 @@ __global__ void k_intake(Dev d, const int3 *moves, int m, int grid, int bits, in
     }
 }
 
-__global__ void k_scatter(int m, const int *move_cell, const int *cell_off, int *cell_fill, int *order,
-                          const int *status, const int *ctl)
+// The moves of a step, read from the control block when the step is a graph launch
+// (ctl[2..3] hold the pointer), else from the argument.
+__device__ __forceinline__ const int3 *step_moves(const Dev &d, const int3 *moves)
 {
-    if (*status) return;
-    if (ctl) m = __ldcg(ctl);
+    if (!d.ctl) return moves;
+    unsigned lo = (unsigned)__ldcg(d.ctl + 2), hi = (unsigned)__ldcg(d.ctl + 3);
+    return reinterpret_cast<const int3 *>(((unsigned long long)hi << 32) | lo);
+}
+
+// Intake and per-partition bucketing in one pass: validate each move (A2), stamp the
+// moved id, remember the old position, and push the move onto the list of the
+// partition that owns the point (its cell at the start of the step, Section III
+// blocks): next[i] = previous head of the cell's list.
+__global__ void k_intake_link(Dev d, const int3 *moves, int m, int grid, int bits, int *head, int *next,
+                              int2 *old_xy)
+{
+    if (d.ctl) {
+        m = __ldcg(d.ctl);
+        d.stamp = __ldcg(d.ctl + 1);
+    }
+    moves = step_moves(d, moves);
+    long long lim = 1ll << bits;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-        int c = move_cell[i];
-        order[cell_off[c] + atomicAdd(cell_fill + c, 1)] = i;
+        int3 mv = moves[i];
+        if (mv.x < 0 || mv.x >= d.n) {
+            atomicCAS(d.status, 0, DEV_ARG);
+            continue;
+        }
+        if (mv.y < 0 || mv.z < 0 || mv.y >= lim || mv.z >= lim) {
+            atomicCAS(d.status, 0, DEV_RANGE);
+            continue;
+        }
+        int prev = atomicExch(d.pt_stamp + mv.x, d.stamp);
+        if (prev == d.stamp) {
+            atomicCAS(d.status, 0, DEV_DUP_ID);
+            continue;
+        }
+        int2 o = d.xy[mv.x];
+        old_xy[i] = o;
+        int cx = (int)(((long long)o.x * grid) >> bits);
+        int cy = (int)(((long long)o.y * grid) >> bits);
+        next[i] = atomicExch(head + cy * grid + cx, i);
     }
 }
 
@@ -182,24 +216,27 @@ __global__ void k_scatter(int m, const int *move_cell, const int *cell_off, int 
 // partition border follows from its new position; all blocks share one
 // triangulation in HBM, so the hand-off of Fig. 4 is an ownership change, not a
 // message.  A point whose target is still occupied by a point that has not moved
-// yet is deferred to k_deferred.
-__global__ void __launch_bounds__(WPB * 32, 8) k_kinetic(Dev d, const int3 *moves, const int *order,
-                                                      const int *cell_cnt, const int *cell_off, int ncells,
-                                                      int4 *deferred, int *defer_count, int defer_cap)
+// yet is deferred.  The last warp to finish inserts the deferred points and
+// certifies the triangles written on the global-memory path.
+__device__ void step_tail(Warp &w, const Dev &d, const int4 *deferred, const int *defer_count, int defer_cap,
+                          int *viol, int viol_cap);
+
+__global__ void __launch_bounds__(WPB * 32, 8) k_kinetic(Dev d, const int3 *moves, const int *head, const int *next,
+                                                         int ncells, int4 *deferred, int *defer_count,
+                                                         int defer_cap, int *viol, int viol_cap)
 {
     if (d.ctl) d.stamp = __ldcg(d.ctl + 1);
+    moves = step_moves(d, moves);
     __shared__ WarpShared shs[WPB];
     int wib = threadIdx.x >> 5;
     int gw = blockIdx.x * (blockDim.x >> 5) + wib;
     int nw = gridDim.x * (blockDim.x >> 5);
     Warp w = make_warp(&shs[wib], gw + 1, gw + 17 * d.stamp);
     for (int c = gw; c < ncells; c += nw) {
-        int cnt = cell_cnt[c];
-        if (cnt == 0) continue;
-        int off = cell_off[c];
-        for (int j = 0; j < cnt; ++j) {
+        int i = __shfl_sync(FULL, __ldcg(head + c), 0);
+        while (i >= 0) {
             if (read_status(d)) break;
-            int3 mv = moves[order[off + j]];
+            int3 mv = moves[i];
             int p = mv.x;
             int2 q = make_int2(mv.y, mv.z);
             int s0 = -1, s1 = -1, hint = -1;
@@ -216,9 +253,9 @@ __global__ void __launch_bounds__(WPB * 32, 8) k_kinetic(Dev d, const int3 *move
                 rc = insert_point(w, d, p, q, hint, s0, s1, true);
             }
             {
-                unsigned c = (unsigned)((clock64() - c0) >> 6);
-                w.cnt[C_CYC_MOVE] += c;
-                w.cyc_max = c > w.cyc_max ? c : w.cyc_max;
+                unsigned cy = (unsigned)((clock64() - c0) >> 6);
+                w.cnt[C_CYC_MOVE] += cy;
+                w.cyc_max = cy > w.cyc_max ? cy : w.cyc_max;
             }
             if (rc == MV_DEFER || rc == 1) {
                 if (w.lane == 0) {
@@ -232,33 +269,20 @@ __global__ void __launch_bounds__(WPB * 32, 8) k_kinetic(Dev d, const int3 *move
                 if (rc > 0 && w.lane == 0 && atomicCAS(d.status, 0, rc) == 0) d.status[S_FAILPT] = p;
                 break;
             }
+            i = __shfl_sync(FULL, __ldcg(next + i), 0);
         }
     }
-    flush_counters(w, d);
-}
-
-// Deferred insertions: their targets were held by points that moved away later in
-// the step; any coincidence now is a genuine duplicate.
-__global__ void __launch_bounds__(WPB * 32) k_deferred(Dev d, const int4 *deferred, const int *defer_count,
-                                                       int defer_cap)
-{
-    if (d.ctl) d.stamp = __ldcg(d.ctl + 1);
-    __shared__ WarpShared shs[WPB];
-    int wib = threadIdx.x >> 5;
-    int gw = blockIdx.x * (blockDim.x >> 5) + wib;
-    int nw = gridDim.x * (blockDim.x >> 5);
-    Warp w = make_warp(&shs[wib], gw + 1, gw + 7919 * d.stamp);
-    int cnt = min(*defer_count, defer_cap);
-    for (int j = gw; j < cnt; j += nw) {
-        if (read_status(d)) break;
-        int4 e = deferred[j];
-        int2 q = __ldcg(d.xy + e.x);
-        q = bcast2(q, 0);
-        int rc = insert_point(w, d, e.x, q, e.w, e.y, e.z, false);
-        if (rc) {
-            if (rc > 0) set_status(d, rc);
-            break;
-        }
+    // the last warp to finish does the tail work
+    int done = 0;
+    __syncwarp();
+    if (w.lane == 0) {
+        __threadfence();
+        done = atomicAdd(d.status + S_DONE, 1);
+    }
+    done = __shfl_sync(FULL, done, 0);
+    if (done == nw - 1) {
+        __threadfence();
+        step_tail(w, d, deferred, defer_count, defer_cap, viol, viol_cap);
     }
     flush_counters(w, d);
 }
@@ -299,29 +323,6 @@ __device__ int hull_wrap(const Dev &d, const int4 &v, const int4 &nb)
 
 // ------------------------------------------------------------------ certification
 
-// Is edge e of live triangle t locally Delaunay?  Also checks that the adjacency is
-// reciprocal and the triangle counter-clockwise.  Returns 0 (fine), 1 (not locally
-// Delaunay), -1 (store inconsistent).
-__device__ int check_edge(const Dev &d, int t, const int4 &v, const int4 &nb, int e, unsigned *ex,
-                          unsigned *ti)
-{
-    int ref = comp(nb, e);
-    int U = ref >> 2, f = ref & 3;
-    if (U < 0 || U >= d.cap || f > 2) return -1;
-    int4 uv = __ldcg(d.tv + U);
-    int4 un = __ldcg(d.tn + U);
-    if (!(uv.w & ALIVE) || comp(un, f) != ((t << 2) | e)) return -1;
-    int a = comp(v, (e + 1) % 3), b = comp(v, (e + 2) % 3);
-    if (comp(uv, (f + 1) % 3) != b || comp(uv, (f + 2) % 3) != a) return -1;
-    int dd = comp(uv, f);
-    int2 z = make_int2(0, 0);
-    int2 p0 = v.x >= 0 ? __ldcg(d.xy + v.x) : z;
-    int2 p1 = v.y >= 0 ? __ldcg(d.xy + v.y) : z;
-    int2 p2 = v.z >= 0 ? __ldcg(d.xy + v.z) : z;
-    int2 pd = dd >= 0 ? __ldcg(d.xy + dd) : z;
-    return conflict(v.x, v.y, v.z, p0, p1, p2, dd, pd, d.use_filter, ex, ti) ? 1 : 0;
-}
-
 __device__ void certify_one(const Dev &d, int t, int *viol, int *viol_count, int viol_cap, unsigned *ex,
                             unsigned *ti)
 {
@@ -345,6 +346,37 @@ __device__ void certify_one(const Dev &d, int t, int *viol, int *viol_count, int
             if (pos < viol_cap) viol[pos] = (t << 2) | e;
         }
     }
+}
+
+// Tail of a step (one warp, after every other warp finished): insert the deferred
+// points, then certify the triangles written on the global-memory path (the staged
+// path certified its own).  A long dirty list is left to the host.
+__device__ void step_tail(Warp &w, const Dev &d, const int4 *deferred, const int *defer_count, int defer_cap,
+                          int *viol, int viol_cap)
+{
+    if (read_status(d)) return;
+    int cnt = __shfl_sync(FULL, __ldcg(defer_count), 0);
+    if (cnt > defer_cap) cnt = defer_cap;
+    for (int j = 0; j < cnt; ++j) {
+        if (read_status(d)) return;
+        int4 e = deferred[j];
+        int2 q = __ldcg(d.xy + e.x);
+        q = bcast2(q, 0);
+        int rc = insert_point(w, d, e.x, q, e.w, e.y, e.z, false);
+        if (rc) {
+            if (rc > 0) set_status(d, rc);
+            return;
+        }
+    }
+    __threadfence();
+    int hi = __shfl_sync(FULL, __ldcg(d.dirty_count), 0);
+    if (hi > 4096) {
+        if (w.lane == 0) d.status[S_CERTPEND] = 1;
+        return;
+    }
+    unsigned ex = 0, ti = 0;
+    for (int i = w.lane; i < hi; i += 32)
+        certify_one(d, d.dirty[i], viol, d.status + S_VIOL, viol_cap, &ex, &ti);
 }
 
 // certify the dirty slots [lo, *dirty_count) (the slots written in this step)

@@ -105,16 +105,12 @@ __device__ __forceinline__ int nb_staged(Warp &w, const Dev &d, Region &R, int j
 }
 
 // Write every modified staged triangle back (lane-parallel), update pt_tri of their
-// vertices, append them to the dirty list with one atomic, then release all claims.
+// vertices, release all claims, then certify the written triangles.
 __device__ void write_back(Warp &w, const Dev &d, Region &R)
 {
     WarpShared *sh = w.sh;
     __syncwarp();
     unsigned long long m = R.dirty;
-    int nd = __popcll(m);
-    int base = 0;
-    if (nd > 0 && w.lane == 0) base = atomicAdd(d.dirty_count, nd);
-    base = __shfl_sync(FULL, base, 0);
     for (int j0 = 0; j0 < R.cnt; j0 += 32) {
         int j = j0 + w.lane;
         if (j < R.cnt && ((m >> j) & 1ull)) {
@@ -128,14 +124,34 @@ __device__ void write_back(Warp &w, const Dev &d, Region &R)
                 if (v.y >= 0) d.pt_tri[v.y] = slot;
                 if (v.z >= 0) d.pt_tri[v.z] = slot;
             }
-            int pos = base + __popcll(m & ((1ull << j) - 1ull));
-            if (pos < d.dirty_cap) d.dirty[pos] = slot;
         }
     }
     __syncwarp();
     __threadfence();
     R.dirty = 0;
     release_all(w, d);
+    // certify what was written: an edge whose far side changes later is certified
+    // again by the operation that changes it, so the last writer of every edge checks
+    // it against final data.  A transiently inconsistent read goes to the dirty list,
+    // which is certified once the step is quiescent.
+    unsigned ex = 0, ti = 0;
+    for (int j = w.lane; j < R.cnt; j += 32) {
+        if (!((m >> j) & 1ull)) continue;
+        int4 v = sh->lv[j];
+        if (!(v.w & ALIVE)) continue;
+        int slot = sh->lslot[j];
+        int4 n = sh->ln[j];
+        for (int e = 0; e < 3; ++e) {
+            int r = check_edge(d, slot, v, n, e, &ex, &ti);
+            if (r > 0) {
+                int pos = atomicAdd(d.viol_count, 1);
+                if (pos < d.viol_cap) d.viol[pos] = (slot << 2) | e;
+            } else if (r < 0) {
+                dirty_push(d, slot);
+            }
+        }
+    }
+    __syncwarp();
 }
 
 // Locate q in staged triangle j: -1 not inside, 0 inside, 1 on edge (*e), 2 on a vertex

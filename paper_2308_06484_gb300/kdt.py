@@ -57,7 +57,7 @@ class Stats(ctypes.Structure):
                 + [("kinetic_kernel_ms", ctypes.c_double), ("kinetic_kernel_timed", ctypes.c_int64),
                    ("last_fallback_reason", ctypes.c_int64), ("last_fallback_point", ctypes.c_int64)]
                 + [(f, ctypes.c_int64) for f in _STAT_FIELDS2]
-                + [("reserved", ctypes.c_int64 * 8)])
+                + [("step_graph_ms", ctypes.c_double), ("reserved", ctypes.c_int64 * 7)])
 
 
 _lib = None
@@ -248,6 +248,7 @@ class Triangulation:
         d["last_fallback_point"] = int(s.last_fallback_point)
         for f in _STAT_FIELDS2:
             d[f] = int(getattr(s, f))
+        d["step_graph_ms"] = float(s.step_graph_ms)
         return d
 
     def reset_stats(self):
