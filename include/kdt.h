@@ -83,7 +83,10 @@ typedef struct {
     int32_t debug;         /* bit 0: on an in-step failure keep the failed state (no
                               fallback, no roll-back) so kdt_export_store can inspect it     */
     int32_t use_graph;     /* 1: launch each step as one captured CUDA graph (default)       */
-    int32_t reserved[3];
+    int32_t points_per_partition; /* partition size of batched instances (0 = 256)           */
+    int32_t warps_per_partition;  /* warps sharing one partition's moves (0 = 1)             */
+    int32_t autotune;      /* 1: time the first steps over points per partition {128, 256,
+                              512} x warps per partition {1, 2, 4} and keep the fastest       */
 } kdt_config;
 
 /* Counters since creation (or kdt_reset_stats). */
@@ -101,7 +104,8 @@ typedef struct {
     int64_t cycles_move_max;      /* longest single move, cycles                            */
     int64_t cycles_gather, cycles_claim, cycles_local, cycles_writeback; /* phase sums    */
     double step_graph_ms;         /* event-timed control copy + step graph (timing = 1)     */
-    int64_t reserved[7];
+    int64_t tuned_points_per_partition, tuned_warps_per_partition; /* autotuner choice   */
+    int64_t reserved[5];
 } kdt_stats;
 
 /* ---- lifecycle ------------------------------------------------------------------ */
@@ -126,7 +130,8 @@ int kdt_destroy(kdt *h);
  * KDT_ERR_DUPLICATE, KDT_ERR_DEGENERATE (n < 3 or all collinear), KDT_ERR_CUDA. */
 int kdt_build(kdt *h, const int32_t *xy, int64_t n);
 
-/* One time step (Fig. 4 loop body): the m moves (host or device; distinct ids) are
+/* One time step (Fig. 4 loop body) of a single-instance handle: the m moves (host or
+ * device; distinct ids) are
  * applied simultaneously and the triangulation of the new positions is restored:
  * per partition, each moved point is deleted from the triangulation and inserted at
  * its new position (Section IV).  The result does not depend on the order of the
@@ -135,6 +140,27 @@ int kdt_build(kdt *h, const int32_t *xy, int64_t n);
  * another final position), KDT_ERR_DEGENERATE (all final positions collinear),
  * KDT_ERR_RETRY_EXHAUSTED (only with fallback = 0), KDT_ERR_STATE, KDT_ERR_CUDA. */
 int kdt_step(kdt *h, const kdt_move *moves, int64_t m);
+
+/* Batched instances (many independent point sets advanced by one step launch; the
+ * paper's blocks of one data set generalised to blocks of many data sets).  xy holds
+ * the points of all instances back to back; offsets (host, n_inst + 1 entries,
+ * offsets[0] = 0) delimits them, every instance having at least 3 points.  Each
+ * instance gets its own triangulation; point ids inside an instance are local
+ * (0 .. n_i - 1) in the step and per-instance export calls, global (offsets[i] + local)
+ * in kdt_export_triangles / kdt_export_points.  Errors as kdt_build. */
+int kdt_build_batch(kdt *h, const int32_t *xy, const int64_t *offsets, int32_t n_inst);
+
+/* One time step of every instance of a batched handle: moves (host or device) with
+ * instance-local ids, move_offsets (host, n_inst + 1 entries) delimiting each
+ * instance's moves.  Errors as kdt_step. */
+int kdt_step_batch(kdt *h, const kdt_move *moves, const int64_t *move_offsets, int32_t n_inst);
+
+/* Canonical triangle list of one instance, with instance-local ids (as
+ * kdt_export_triangles for a single instance). */
+int kdt_export_triangles_inst(kdt *h, int32_t inst, int32_t *out, int64_t cap, int64_t *n_tri);
+
+/* Number of instances of the current state (0 before a build). */
+int32_t kdt_num_instances(const kdt *h);
 
 /* Rebuild the triangulation of the current positions from scratch on the GPU (the
  * full-rebuild comparator; the same code is the fallback of kdt_step). */

@@ -1,13 +1,23 @@
 // C-ABI and host orchestration of the GB300 kinetic Delaunay library.
 // The declarations, argument conventions and error behaviour are in include/kdt.h.
+//
+// A handle holds one or more independent instances in one store: instance i owns
+// the global point ids pofs[i] .. pofs[i+1]-1, the triangle slots tofs[i] ..
+// tofs[i+1]-1 (2 n_i - 2 of them) and the partitions cofs[i] .. cofs[i+1]-1.  Each
+// instance is its own triangulation (its own sphere with the shared vertex at
+// infinity), so every kernel works on the whole store at once; only builds and
+// exports go instance by instance.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <climits>
+#include <cmath>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "../../include/kdt.h"
 #include "kdt_kernels.cuh"
@@ -16,12 +26,17 @@ using namespace kd;
 
 namespace {
 
-constexpr int ABI_VERSION = 1;
+constexpr int ABI_VERSION = 2;
 
 struct Buf {
     void *p = nullptr;
     size_t bytes = 0;
 };
+
+// the partition sizes and warps per partition the autotuner tries
+constexpr int TUNE_PPP[3] = {128, 256, 512};
+constexpr int TUNE_WPP[3] = {1, 2, 4};
+constexpr int TUNE_STEPS = 2;  // timed steps per configuration
 
 }  // namespace
 
@@ -29,44 +44,55 @@ struct kdt {
     int device = 0;
     cudaStream_t stream = nullptr;
     kdt_config cfg{};
-    int grid = 1;  // partitions per side in use
-    int64_t n = 0;
-    int cap = 0;  // triangle slots (2n - 2)
+    int64_t n = 0;  // points (all instances)
+    int cap = 0;    // triangle slots (all instances)
     bool built = false;
     int stamp = 0;
+    // instances
+    int ninst = 0;
+    std::vector<int> pofs, tofs, cofs, igrid;  // host copies
+    int *d_pofs = nullptr, *d_cofs = nullptr, *d_grid = nullptr, *d_moff = nullptr;
+    int *h_moff = nullptr;  // pinned
+    int ncells = 0;          // partitions (all instances)
+    int ppp = 256;           // points per partition in use
+    int wpp = 1;             // warps per partition in use
     // state
     int2 *xy = nullptr;
     int *pt_tri = nullptr;
     int *pt_stamp = nullptr;
     int4 *tv = nullptr;
     int4 *tn = nullptr;
-    int *scal = nullptr;                       // S_NUM device scalars
-    unsigned long long *counters = nullptr;    // C_NUM
+    int *scal = nullptr;                     // S_NUM device scalars
+    unsigned long long *counters = nullptr;  // C_NUM + 1
     int *dirty = nullptr;
     int dirty_cap = 0;
     int *viol = nullptr;
     int viol_cap = 0;
     // step buffers
     int mcap = 0;
-    int3 *moves = nullptr;
+    int3 *moves = nullptr;   // host moves copied in
+    int3 *gmoves = nullptr;  // moves with global ids (written by the intake)
     int2 *old_xy = nullptr;
-    int *move_cell = nullptr;
-    int *order = nullptr;
+    int *next = nullptr;     // per-partition move lists
+    int *head = nullptr;
     int4 *deferred = nullptr;
-    int ncells = 0;
-    int *cell_cnt = nullptr, *cell_off = nullptr, *cell_fill = nullptr;
     int *scan_tmp = nullptr;
     int scan_tmp_cap = 0;
     // build / export temporaries (kept between calls)
-    Buf key, bord, hist, hoff, exp_cnt, exp_off, exp_fill, exp_out, in_xy;
-    // graph-launched step: control words (moves, stamp) and the captured graph
-    int *ctl = nullptr;    // device
-    int *hctl = nullptr;   // pinned host
+    Buf key, bord, hist, hoff, exp_cnt, exp_off, exp_fill, exp_out;
+    // graph-launched step: control words (moves, stamp, moves address) and the graph
+    int *ctl = nullptr;   // device
+    int *hctl = nullptr;  // pinned host
     cudaStream_t cstream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
-    int graph_gen = -1;    // buffer generation the graph was captured for
-    int gen = 0;           // bumped whenever step buffers are (re)allocated
+    int graph_gen = -1;  // buffer generation the graph was captured for
+    int gen = 0;         // bumped whenever step buffers or tables change
+    // autotuner state: configuration index being timed, accumulated times
+    int tune_idx = -1;
+    int tune_done = 0;
+    int tune_count = 0;
+    double tune_ms[9] = {0};
     // host side
     int *hscal = nullptr;  // pinned copy of the scalars
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
@@ -75,9 +101,9 @@ struct kdt {
 
 namespace {
 
-#define CK(call)                                   \
-    do {                                           \
-        cudaError_t e_ = (call);                   \
+#define CK(call)                                    \
+    do {                                            \
+        cudaError_t e_ = (call);                    \
         if (e_ != cudaSuccess) return KDT_ERR_CUDA; \
     } while (0)
 
@@ -161,10 +187,23 @@ Dev make_dev(kdt *h)
     d.viol = h->viol;
     d.viol_count = h->scal + S_VIOL;
     d.viol_cap = h->viol_cap;
+    d.rlo = 0;
+    d.rn = (int)std::max<int64_t>(h->n, 1);
     return d;
 }
 
-// exclusive scan in place (or out of place) of n ints; *total receives the sum
+Inst make_inst(kdt *h)
+{
+    Inst I;
+    I.pofs = h->d_pofs;
+    I.cofs = h->d_cofs;
+    I.grid = h->d_grid;
+    I.moff = h->d_moff;
+    I.ninst = h->ninst;
+    return I;
+}
+
+// exclusive scan of n ints; *total receives the sum
 int scan(kdt *h, const int *in, int *out, int n, int *total, cudaStream_t st)
 {
     int tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
@@ -173,7 +212,7 @@ int scan(kdt *h, const int *in, int *out, int n, int *total, cudaStream_t st)
         int c = tiles + 1024;
         if (dalloc(&h->scan_tmp, (size_t)c)) return KDT_ERR_CUDA;
         h->scan_tmp_cap = c;
-        h->gen++;  // a captured step graph holds the old pointer
+        h->gen++;  // a captured step graph may hold the old pointer
     }
     k_scan_tile<<<tiles, SCAN_THREADS, 0, st>>>(in, out, n, h->scan_tmp);
     k_scan_sums<<<1, 1024, 0, st>>>(h->scan_tmp, tiles, total);
@@ -208,20 +247,31 @@ int thread_grid(kdt *h, long long items, int threads)
     return (int)blocks;
 }
 
-// Certify (dirty range or everything), then repair until no violation is left.
-// Returns a device status (0 fine).
-int certify_and_repair(kdt *h, bool all, int *dev_status)
+// blocks of the kinetic kernel that fit on the GPU at once (persistent launch)
+int kinetic_blocks(kdt *h)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_kinetic, WPB * 32, 0) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 4;
+    return sm_count(h->device) * per_sm;
+}
+
+// Certify slots [s0, s0 + nslots) (or the dirty list when !full), then repair until
+// no violation is left.  A full pass must see `wraps` hull windings (one per
+// instance in the range).  Returns a CUDA/ABI error; the device status goes to
+// *dev_status.
+int certify_and_repair(kdt *h, bool full, int s0, int nslots, int wraps, int *dev_status)
 {
     Dev d = make_dev(h);
-    if (all && d.retry_cap < 4096) d.retry_cap = 4096;
-    bool full = all;
+    if (full && d.retry_cap < 4096) d.retry_cap = 4096;
     int lo = 0;
     for (int round = 0; round < 64; ++round) {
         CK(cudaMemsetAsync(h->scal + S_VIOL, 0, sizeof(int), h->stream));
         CK(cudaMemsetAsync(h->scal + S_WRAPS, 0, sizeof(int), h->stream));
         if (full) {
-            k_certify_all<<<thread_grid(h, h->cap, 256), 256, 0, h->stream>>>(
-                d, h->cap, h->viol, h->scal + S_VIOL, h->viol_cap, h->scal + S_WRAPS);
+            k_certify_all<<<thread_grid(h, nslots, 256), 256, 0, h->stream>>>(d, s0, nslots, h->viol, h->scal + S_VIOL,
+                                                                             h->viol_cap, h->scal + S_WRAPS);
         } else {
             k_certify<<<thread_grid(h, 65536, 256), 256, 0, h->stream>>>(d, lo, h->viol, h->scal + S_VIOL,
                                                                         h->viol_cap);
@@ -234,13 +284,12 @@ int certify_and_repair(kdt *h, bool all, int *dev_status)
         int nv = h->hscal[S_VIOL];
         h->stats.violations += nv;
         if (nv == 0) {
-            // every edge is locally Delaunay; after a full pass the hull must also wind once
-            if (full && h->hscal[S_WRAPS] != 1) *dev_status = DEV_INTERNAL;
+            // every edge is locally Delaunay; after a full pass each hull winds once
+            if (full && h->hscal[S_WRAPS] != wraps) *dev_status = DEV_INTERNAL;
             return 0;
         }
         if (nv > h->viol_cap) nv = h->viol_cap;  // the rest is found again next round
         int dirty_before = h->hscal[S_DIRTY];
-        full = all || dirty_before > h->dirty_cap;
         lo = dirty_before;
         k_fixup<<<warp_grid(h, nv, 16), WPB * 32, 0, h->stream>>>(d, h->viol, nv);
         h->stats.kernel_launches++;
@@ -248,37 +297,44 @@ int certify_and_repair(kdt *h, bool all, int *dev_status)
         if (sync_scalars(h)) return KDT_ERR_CUDA;
         *dev_status = h->hscal[S_STATUS];
         if (*dev_status) return 0;
-        if (!full && h->hscal[S_DIRTY] > h->dirty_cap) full = true;
+        if (!full && h->hscal[S_DIRTY] > h->dirty_cap) {
+            full = true;
+            s0 = 0;
+            nslots = h->cap;
+            wraps = h->ninst;
+        }
     }
     *dev_status = DEV_INTERNAL;
     return 0;
 }
 
-// Build the triangulation of the positions already in h->xy (kdt_build, kdt_rebuild
-// and the step fallback).  Returns an ABI code.
-int rebuild_positions(kdt *h)
+// Build the triangulation of instance i from the positions in h->xy: Hilbert order
+// over a grid on its bounding box, the first non-degenerate triangle, then parallel
+// insertion level by level (positions (2j+1) * 2^level walk from position 2j * 2^level),
+// then certification and repair.  Returns an ABI code.
+int rebuild_instance(kdt *h, int i)
 {
-    const int n = (int)h->n;
+    const int p0 = h->pofs[i], n = h->pofs[i + 1] - p0;
+    const int s0 = h->tofs[i], capi = h->tofs[i + 1] - s0;
     cudaStream_t st = h->stream;
-    h->built = false;
-    h->stamp++;
     Dev d = make_dev(h);
-    d.dirty_cap = 0;  // the build certifies every slot instead
+    d.dirty_cap = 0;  // the build certifies every slot of the instance instead
     if (d.retry_cap < 4096) d.retry_cap = 4096;  // the step's cap does not apply to builds
+    d.rlo = p0;
+    d.rn = n;
     CK(cudaMemsetAsync(h->scal, 0, S_NUM * sizeof(int), st));
     int init_bbox[4] = {INT_MAX, INT_MAX, INT_MIN, INT_MIN};
     CK(cudaMemcpyAsync(h->scal + S_MINX, init_bbox, sizeof init_bbox, cudaMemcpyHostToDevice, st));
     int third0 = INT_MAX;
     CK(cudaMemcpyAsync(h->scal + S_THIRD, &third0, sizeof(int), cudaMemcpyHostToDevice, st));
-    CK(cudaMemsetAsync(h->tv, 0, (size_t)h->cap * sizeof(int4), st));
-    CK(cudaMemsetAsync(h->tn, 0, (size_t)h->cap * sizeof(int4), st));
-    k_fill_int<<<thread_grid(h, n, 256), 256, 0, st>>>(h->pt_tri, n, -1);
-    k_range<<<thread_grid(h, n, 256), 256, 0, st>>>(h->xy, n, h->cfg.domain_bits, h->scal + S_STATUS,
+    CK(cudaMemsetAsync(h->tv + s0, 0, (size_t)capi * sizeof(int4), st));
+    CK(cudaMemsetAsync(h->tn + s0, 0, (size_t)capi * sizeof(int4), st));
+    k_fill_int<<<thread_grid(h, n, 256), 256, 0, st>>>(h->pt_tri + p0, n, -1);
+    k_range<<<thread_grid(h, n, 256), 256, 0, st>>>(h->xy + p0, n, h->cfg.domain_bits, h->scal + S_STATUS,
                                                     h->scal + S_MINX);
     h->stats.kernel_launches += 2;
     if (sync_scalars(h)) return KDT_ERR_CUDA;
     if (h->hscal[S_STATUS]) return dev_to_abi(h->hscal[S_STATUS]);
-    // spatial order: cells of a 2^k x 2^k grid over the bounding box, Hilbert order
     int k = 1;
     while ((1ll << (2 * k)) < (long long)n && k < 14) ++k;
     long long span = (long long)std::max(h->hscal[S_MAXX] - h->hscal[S_MINX], h->hscal[S_MAXY] - h->hscal[S_MINY]) + 1;
@@ -291,18 +347,17 @@ int rebuild_positions(kdt *h)
     unsigned *key = (unsigned *)h->key.p;
     int *order = (int *)h->bord.p, *hist = (int *)h->hist.p, *hoff = (int *)h->hoff.p;
     CK(cudaMemsetAsync(hist, 0, ncell * 4, st));
-    k_hilbert<<<(n + 255) / 256, 256, 0, st>>>(h->xy, n, h->scal + S_MINX, k, shift, key, hist);
+    k_hilbert<<<(n + 255) / 256, 256, 0, st>>>(h->xy + p0, n, h->scal + S_MINX, k, shift, key, hist);
     h->stats.kernel_launches++;
     if (scan(h, hist, hoff, (int)ncell, h->scal + S_TOTAL, st)) return KDT_ERR_CUDA;
     CK(cudaMemsetAsync(hist, 0, ncell * 4, st));
-    k_place_order<<<(n + 255) / 256, 256, 0, st>>>(n, key, hoff, hist, order);
+    k_place_order<<<(n + 255) / 256, 256, 0, st>>>(n, key, hoff, hist, order, p0);
     k_third<<<thread_grid(h, n, 256), 256, 0, st>>>(h->xy, n, order, h->scal + S_THIRD);
     h->stats.kernel_launches += 2;
     if (sync_scalars(h)) return KDT_ERR_CUDA;
     if (h->hscal[S_THIRD] == INT_MAX) return KDT_ERR_DEGENERATE;
-    k_init<<<1, 1, 0, st>>>(d, order, h->scal + S_THIRD, h->scal + S_TRIS);
+    k_init<<<1, 1, 0, st>>>(d, order, h->scal + S_THIRD, h->scal + S_TRIS, s0);
     h->stats.kernel_launches++;
-    // levels: sorted index i is inserted at level ctz(i), highest level first
     int K = 0;
     while ((1ll << (K + 1)) < (long long)n) ++K;
     long long inserted = 3;
@@ -318,17 +373,28 @@ int rebuild_positions(kdt *h)
             blocks = 1;
             threads = 32 * h->cfg.build_warps;
         }
-        k_insert_level<<<blocks, threads, 0, st>>>(d, order, lev, (int)items, h->scal + S_TRIS);
+        k_insert_level<<<blocks, threads, 0, st>>>(d, order, lev, (int)items, h->scal + S_TRIS, n, s0 + capi);
         h->stats.kernel_launches++;
         CK(cudaGetLastError());
         inserted += items;
     }
     if (sync_scalars(h)) return KDT_ERR_CUDA;
     if (h->hscal[S_STATUS]) return dev_to_abi(h->hscal[S_STATUS]);
-    if (h->hscal[S_TRIS] != h->cap) return KDT_ERR_INTERNAL;
+    if (h->hscal[S_TRIS] != s0 + capi) return KDT_ERR_INTERNAL;
     int ds = 0;
-    if (certify_and_repair(h, true, &ds)) return KDT_ERR_CUDA;
+    if (certify_and_repair(h, true, s0, capi, 1, &ds)) return KDT_ERR_CUDA;
     if (ds) return dev_to_abi(ds);
+    return KDT_OK;
+}
+
+int rebuild_all(kdt *h)
+{
+    h->built = false;
+    h->stamp++;
+    for (int i = 0; i < h->ninst; ++i) {
+        int rc = rebuild_instance(h, i);
+        if (rc) return rc;
+    }
     h->built = true;
     h->stats.rebuilds++;
     return KDT_OK;
@@ -338,7 +404,7 @@ int ensure_moves(kdt *h, int64_t m)
 {
     if (m <= h->mcap) return 0;
     int c = (int)std::max<int64_t>(m, 1024);
-    if (dalloc(&h->moves, c) || dalloc(&h->old_xy, c) || dalloc(&h->move_cell, c) || dalloc(&h->order, c) ||
+    if (dalloc(&h->moves, c) || dalloc(&h->gmoves, c) || dalloc(&h->old_xy, c) || dalloc(&h->next, c) ||
         dalloc(&h->deferred, c))
         return KDT_ERR_CUDA;
     h->mcap = c;
@@ -350,26 +416,35 @@ int ensure_moves(kdt *h, int64_t m)
     return 0;
 }
 
-int alloc_state(kdt *h, int64_t n)
+// partitions of every instance for `ppp` points per partition (or the configured
+// grid for a single instance), uploaded with the instance tables
+int set_partitions(kdt *h, int ppp)
 {
-    h->n = n;
-    h->cap = (int)(2 * n - 2);
-    h->built = false;
-    if (dalloc(&h->xy, n) || dalloc(&h->pt_tri, n) || dalloc(&h->pt_stamp, n) || dalloc(&h->tv, h->cap) ||
-        dalloc(&h->tn, h->cap))
-        return KDT_ERR_CUDA;
-    CK(cudaMemsetAsync(h->pt_stamp, 0, n * sizeof(int), h->stream));
-    h->viol_cap = std::max(4096, h->cap);
-    if (dalloc(&h->viol, (size_t)h->viol_cap)) return KDT_ERR_CUDA;
-    int G = h->cfg.grid;
-    if (G <= 0) {
-        G = 1;
-        while ((long long)G * G * 256 < n && G < 4096) G *= 2;
+    h->ppp = ppp;
+    h->cofs.assign(h->ninst + 1, 0);
+    h->igrid.assign(h->ninst, 1);
+    long long cells = 0;
+    for (int i = 0; i < h->ninst; ++i) {
+        int ni = h->pofs[i + 1] - h->pofs[i];
+        int G;
+        if (h->ninst == 1 && h->cfg.grid > 0) {
+            G = h->cfg.grid;
+        } else {
+            G = (int)std::lround(std::sqrt((double)ni / (double)ppp));
+            G = std::max(1, std::min(G, 4096));
+        }
+        h->igrid[i] = G;
+        h->cofs[i] = (int)cells;
+        cells += (long long)G * G;
     }
-    h->grid = G;
-    h->ncells = G * G;
-    if (dalloc(&h->cell_cnt, h->ncells) || dalloc(&h->cell_off, h->ncells) || dalloc(&h->cell_fill, h->ncells))
+    if (cells > INT_MAX / 8) return KDT_ERR_ARG;
+    h->cofs[h->ninst] = (int)cells;
+    h->ncells = (int)cells;
+    if (dalloc(&h->head, (size_t)cells) || dalloc(&h->d_cofs, h->ninst + 1) || dalloc(&h->d_grid, h->ninst))
         return KDT_ERR_CUDA;
+    CK(cudaMemcpy(h->d_cofs, h->cofs.data(), (h->ninst + 1) * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_grid, h->igrid.data(), h->ninst * sizeof(int), cudaMemcpyHostToDevice));
+    h->gen++;
     return 0;
 }
 
@@ -386,21 +461,55 @@ void free_state(kdt *h)
 {
     drop_graph(h);
     h->gen++;
-    void *ps[] = {h->xy, h->pt_tri, h->pt_stamp, h->tv, h->tn, h->viol, h->moves, h->old_xy, h->move_cell,
-                  h->order, h->deferred, h->dirty, h->cell_cnt, h->cell_off, h->cell_fill, h->scan_tmp};
+    void *ps[] = {h->xy, h->pt_tri, h->pt_stamp, h->tv, h->tn, h->viol, h->moves, h->gmoves, h->old_xy,
+                  h->next, h->head, h->deferred, h->dirty, h->scan_tmp, h->d_pofs, h->d_cofs, h->d_grid,
+                  h->d_moff};
     for (void *p : ps)
         if (p) cudaFree(p);
+    if (h->h_moff) cudaFreeHost(h->h_moff);
     h->xy = nullptr; h->pt_tri = nullptr; h->pt_stamp = nullptr; h->tv = nullptr; h->tn = nullptr;
-    h->viol = nullptr; h->moves = nullptr; h->old_xy = nullptr; h->move_cell = nullptr; h->order = nullptr;
-    h->deferred = nullptr; h->dirty = nullptr; h->cell_cnt = nullptr; h->cell_off = nullptr;
-    h->cell_fill = nullptr; h->scan_tmp = nullptr;
+    h->viol = nullptr; h->moves = nullptr; h->gmoves = nullptr; h->old_xy = nullptr; h->next = nullptr;
+    h->head = nullptr; h->deferred = nullptr; h->dirty = nullptr; h->scan_tmp = nullptr;
+    h->d_pofs = nullptr; h->d_cofs = nullptr; h->d_grid = nullptr; h->d_moff = nullptr; h->h_moff = nullptr;
     h->mcap = 0; h->dirty_cap = 0; h->scan_tmp_cap = 0;
-    Buf *bs[] = {&h->key, &h->bord, &h->hist, &h->hoff, &h->exp_cnt, &h->exp_off, &h->exp_fill, &h->exp_out,
-                 &h->in_xy};
+    Buf *bs[] = {&h->key, &h->bord, &h->hist, &h->hoff, &h->exp_cnt, &h->exp_off, &h->exp_fill, &h->exp_out};
     for (Buf *b : bs) free_buf(*b);
     h->n = 0;
     h->cap = 0;
+    h->ninst = 0;
     h->built = false;
+    h->tune_idx = -1;
+    h->tune_done = 0;
+}
+
+// state for instances with point offsets `offs` (host, n_inst + 1 entries)
+int alloc_state(kdt *h, const int64_t *offs, int n_inst)
+{
+    h->ninst = n_inst;
+    h->pofs.assign(n_inst + 1, 0);
+    h->tofs.assign(n_inst + 1, 0);
+    for (int i = 0; i <= n_inst; ++i) {
+        h->pofs[i] = (int)offs[i];
+        h->tofs[i] = (int)(2 * offs[i] - 2 * i);
+    }
+    h->n = offs[n_inst];
+    h->cap = h->tofs[n_inst];
+    h->built = false;
+    if (dalloc(&h->xy, h->n) || dalloc(&h->pt_tri, h->n) || dalloc(&h->pt_stamp, h->n) || dalloc(&h->tv, h->cap) ||
+        dalloc(&h->tn, h->cap) || dalloc(&h->d_pofs, n_inst + 1) || dalloc(&h->d_moff, n_inst + 1))
+        return KDT_ERR_CUDA;
+    if (cudaMallocHost(&h->h_moff, (n_inst + 1) * sizeof(int)) != cudaSuccess) return KDT_ERR_CUDA;
+    CK(cudaMemcpy(h->d_pofs, h->pofs.data(), (n_inst + 1) * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemsetAsync(h->pt_stamp, 0, h->n * sizeof(int), h->stream));
+    h->viol_cap = std::max(4096, h->cap);
+    if (dalloc(&h->viol, (size_t)h->viol_cap)) return KDT_ERR_CUDA;
+    int ppp = h->cfg.points_per_partition > 0 ? h->cfg.points_per_partition : 256;
+    h->wpp = h->cfg.warps_per_partition > 0 ? h->cfg.warps_per_partition : 1;
+    h->tune_idx = h->cfg.autotune ? 0 : -1;
+    h->tune_done = 0;
+    h->tune_count = 0;
+    for (double &x : h->tune_ms) x = 0.0;
+    return set_partitions(h, ppp);
 }
 
 void add_counters(kdt *h)
@@ -433,11 +542,11 @@ void add_counters(kdt *h)
 }
 
 // Undo a step that failed after it started: restore the old positions and rebuild.
-int roll_back(kdt *h, const int3 *mp, int m)
+int roll_back(kdt *h, int m)
 {
-    k_restore_positions<<<(m + 255) / 256, 256, 0, h->stream>>>(h->xy, mp, h->old_xy, m);
+    k_restore_positions<<<(m + 255) / 256, 256, 0, h->stream>>>(h->xy, h->gmoves, h->old_xy, m);
     h->stats.kernel_launches++;
-    return rebuild_positions(h);
+    return rebuild_all(h);
 }
 
 int verify_state(kdt *h, int64_t *bad)
@@ -451,36 +560,304 @@ int verify_state(kdt *h, int64_t *bad)
     if (sync_scalars(h)) return KDT_ERR_CUDA;
     int64_t b = h->hscal[S_BAD];
     if (h->hscal[S_ALIVE] != h->cap) b += 1;
-    if (h->hscal[S_WRAPS] != 1) b += 1;  // the hull must wind exactly once
+    if (h->hscal[S_WRAPS] != h->ninst) b += 1;  // every hull winds exactly once
     *bad = b;
     return 0;
 }
 
-// Issue one step's kernels on `st`: intake, per-partition counting sort, the kinetic
-// kernel, deferred insertions, certification, and the copy of the status scalars to
-// the host.  With from_ctl the grids do not depend on m (the kernels read m and the
-// stamp from h->ctl), so the sequence can be captured once into a CUDA graph.
+// Issue one step's kernels on `st`: intake + per-partition lists, the kinetic kernel
+// (whose last warp inserts deferred points and certifies global-path writes), and the
+// copy of the status scalars to the host.  With from_ctl the kernels read m, the
+// stamp and the moves' address from h->ctl, so the sequence can be captured once
+// into a CUDA graph.
 int enqueue_step(kdt *h, cudaStream_t st, const Dev &d, const int3 *mp, int mi, bool from_ctl)
 {
     int cap = from_ctl ? h->mcap : mi;
+    Inst I = make_inst(h);
     CK(cudaMemsetAsync(h->scal, 0, S_NUM * sizeof(int), st));
-    CK(cudaMemsetAsync(h->cell_cnt, 0xff, (size_t)h->ncells * sizeof(int), st));  // empty lists
-    k_intake_link<<<thread_grid(h, cap, 256), 256, 0, st>>>(d, mp, mi, h->grid, h->cfg.domain_bits, h->cell_cnt,
-                                                            h->move_cell, h->old_xy);
+    CK(cudaMemsetAsync(h->head, 0xff, (size_t)h->ncells * sizeof(int), st));  // empty lists
+    k_intake_link<<<thread_grid(h, cap, 256), 256, 0, st>>>(d, mp, mi, I, h->cfg.domain_bits, h->head, h->next,
+                                                            h->old_xy, h->gmoves);
     // inside a capture an event record must be an external node to keep its timestamp
     unsigned evflags = from_ctl ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (h->cfg.timing) CK(cudaEventRecordWithFlags(h->ev0, st, evflags));
-    int kblocks = warp_grid(h, h->ncells, 64), kthreads = WPB * 32;
+    int kblocks = kinetic_blocks(h), kthreads = WPB * 32;
     if (h->cfg.kinetic_warps > 0) {
         kblocks = (h->cfg.kinetic_warps + WPB - 1) / WPB;
         if (h->cfg.kinetic_warps < WPB) kthreads = 32 * h->cfg.kinetic_warps;
     }
-    k_kinetic<<<kblocks, kthreads, 0, st>>>(d, mp, h->cell_cnt, h->move_cell, h->ncells, h->deferred,
+    k_kinetic<<<kblocks, kthreads, 0, st>>>(d, h->gmoves, h->head, h->next, I, h->ncells, h->wpp, h->deferred,
                                             h->scal + S_DEFER, h->mcap, h->viol, h->viol_cap);
     if (h->cfg.timing) CK(cudaEventRecordWithFlags(h->ev1, st, evflags));
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->hscal, h->scal, S_NUM * sizeof(int), cudaMemcpyDeviceToHost, st));
     return 0;
+}
+
+// After the step kernels: repair the violations they recorded (general Lawson) and
+// certify what the repair wrote, until nothing is left.  Returns a CUDA/ABI error;
+// the device status goes to *ds.
+int repair_step(kdt *h, int *ds)
+{
+    cudaStream_t st = h->stream;
+    *ds = 0;
+    int nv = h->hscal[S_VIOL];
+    if (h->hscal[S_DIRTY] > h->dirty_cap) return certify_and_repair(h, true, 0, h->cap, h->ninst, ds);
+    if (nv == 0) return 0;
+    Dev d = make_dev(h);
+    h->stats.violations += nv;
+    for (int round = 0; round < 64; ++round) {
+        if (nv > h->viol_cap) nv = h->viol_cap;
+        int dirty_before = h->hscal[S_DIRTY];
+        k_fixup<<<warp_grid(h, nv, 16), WPB * 32, 0, st>>>(d, h->viol, nv);
+        h->stats.kernel_launches++;
+        CK(cudaGetLastError());
+        if (sync_scalars(h)) return KDT_ERR_CUDA;
+        *ds = h->hscal[S_STATUS];
+        if (*ds) return 0;
+        if (h->hscal[S_DIRTY] > h->dirty_cap) return certify_and_repair(h, true, 0, h->cap, h->ninst, ds);
+        CK(cudaMemsetAsync(h->scal + S_VIOL, 0, sizeof(int), st));
+        k_certify<<<thread_grid(h, 65536, 256), 256, 0, st>>>(d, dirty_before, h->viol, h->scal + S_VIOL,
+                                                             h->viol_cap);
+        h->stats.kernel_launches++;
+        if (sync_scalars(h)) return KDT_ERR_CUDA;
+        *ds = h->hscal[S_STATUS];
+        nv = h->hscal[S_VIOL];
+        if (*ds || nv == 0) return 0;
+        h->stats.violations += nv;
+    }
+    *ds = DEV_INTERNAL;
+    return 0;
+}
+
+// Autotuner: the first TUNE_STEPS steps of every (points per partition, warps per
+// partition) pair are timed with events around the step; then the fastest pair is
+// kept.  Results do not depend on the pair.  A single instance with a configured
+// grid tunes the warps per partition only.
+bool tune_fixed_grid(const kdt *h) { return h->ninst == 1 && h->cfg.grid > 0; }
+
+int autotune_before(kdt *h)
+{
+    if (h->tune_idx < 0 || h->tune_done) return 0;
+    int ppp = tune_fixed_grid(h) ? h->ppp : TUNE_PPP[h->tune_idx / 3];
+    if (ppp != h->ppp) {
+        int rc = set_partitions(h, ppp);
+        if (rc) return rc;
+    }
+    h->wpp = TUNE_WPP[h->tune_idx % 3];
+    return 0;
+}
+
+int autotune_after(kdt *h, float ms)
+{
+    if (h->tune_idx < 0 || h->tune_done) return 0;
+    h->tune_ms[h->tune_idx] += ms;
+    if (++h->tune_count < TUNE_STEPS) return 0;
+    h->tune_count = 0;
+    ++h->tune_idx;
+    int last = tune_fixed_grid(h) ? 3 : 9;
+    if (h->tune_idx < last) return 0;
+    int best = 0;
+    for (int k = 1; k < last; ++k)
+        if (h->tune_ms[k] < h->tune_ms[best]) best = k;
+    h->tune_done = 1;
+    int ppp = tune_fixed_grid(h) ? h->ppp : TUNE_PPP[best / 3];
+    if (ppp != h->ppp) {
+        int rc = set_partitions(h, ppp);
+        if (rc) return rc;
+    }
+    h->wpp = TUNE_WPP[best % 3];
+    h->stats.tuned_points_per_partition = h->ppp;
+    h->stats.tuned_warps_per_partition = h->wpp;
+    return 0;
+}
+
+// One step of every instance: moves (instance-local ids, host or device) with CSR
+// offsets moff (host, ninst + 1 entries).
+int step_impl(kdt *h, const kdt_move *moves, const int64_t *moff, int64_t m)
+{
+    if (m == 0) return KDT_OK;
+    if (m > h->n) return KDT_ERR_DUPLICATE;  // some id must repeat (or be out of range)
+    CK(cudaSetDevice(h->device));
+    int rc = ensure_moves(h, m);
+    if (rc) return rc;
+    cudaStream_t st = h->stream;
+    const int mi = (int)m;
+    const int3 *mp = (const int3 *)moves;
+    if (!is_device_ptr(moves)) {
+        CK(cudaMemcpyAsync(h->moves, moves, (size_t)m * sizeof(int3), cudaMemcpyHostToDevice, st));
+        mp = h->moves;
+    }
+    for (int i = 0; i <= h->ninst; ++i) h->h_moff[i] = (int)moff[i];
+    CK(cudaMemcpyAsync(h->d_moff, h->h_moff, (h->ninst + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+    h->stamp++;
+    Dev d = make_dev(h);
+    bool large = h->cfg.fallback && (double)m > (double)h->cfg.rebuild_ratio * (double)h->n;
+    if (large) {
+        // a step this large is cheaper as a rebuild (Abstract: "if the points move so
+        // far, it's better to rebuild the triangulation")
+        CK(cudaMemsetAsync(h->scal, 0, S_NUM * sizeof(int), st));
+        CK(cudaMemsetAsync(h->head, 0xff, (size_t)h->ncells * sizeof(int), st));
+        k_intake_link<<<thread_grid(h, mi, 256), 256, 0, st>>>(d, mp, mi, make_inst(h), h->cfg.domain_bits, h->head,
+                                                               h->next, h->old_xy, h->gmoves);
+        h->stats.kernel_launches++;
+        if (sync_scalars(h)) return KDT_ERR_CUDA;
+        if (h->hscal[S_STATUS]) return dev_to_abi(h->hscal[S_STATUS]);
+        k_set_positions<<<(mi + 255) / 256, 256, 0, st>>>(h->xy, h->gmoves, mi);
+        h->stats.kernel_launches++;
+        rc = rebuild_all(h);
+        if (rc) {
+            int rr = roll_back(h, mi);
+            return rr ? rr : rc;
+        }
+        h->stats.steps++;
+        h->stats.moves += m;
+        return KDT_OK;
+    }
+    rc = autotune_before(h);
+    if (rc) return rc;
+    bool timed = h->cfg.timing || (h->tune_idx >= 0 && !h->tune_done);
+    if (h->cfg.use_graph) {
+        // one graph launch per step
+        if (h->graph_gen != h->gen) {
+            drop_graph(h);
+            Dev dg = d;
+            dg.ctl = h->ctl;
+            CK(cudaStreamBeginCapture(h->cstream, cudaStreamCaptureModeThreadLocal));
+            int er = enqueue_step(h, h->cstream, dg, nullptr, 0, true);
+            cudaGraph_t g = nullptr;
+            cudaError_t ce = cudaStreamEndCapture(h->cstream, &g);
+            if (er || ce != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return KDT_ERR_CUDA;
+            }
+            h->graph = g;
+            CK(cudaGraphInstantiate(&h->gexec, h->graph, 0));
+            h->graph_gen = h->gen;
+        }
+        h->hctl[0] = mi;
+        h->hctl[1] = h->stamp;
+        unsigned long long pa = (unsigned long long)(uintptr_t)mp;
+        h->hctl[2] = (int)(unsigned)(pa & 0xffffffffu);
+        h->hctl[3] = (int)(unsigned)(pa >> 32);
+        if (timed) CK(cudaEventRecord(h->ev2, st));
+        CK(cudaMemcpyAsync(h->ctl, h->hctl, 4 * sizeof(int), cudaMemcpyHostToDevice, st));
+        CK(cudaGraphLaunch(h->gexec, st));
+        if (timed) CK(cudaEventRecord(h->ev3, st));
+    } else {
+        if (timed) CK(cudaEventRecord(h->ev2, st));
+        if (enqueue_step(h, st, d, mp, mi, false)) return KDT_ERR_CUDA;
+        if (timed) CK(cudaEventRecord(h->ev3, st));
+    }
+    h->stats.kernel_launches += 2;
+    CK(cudaStreamSynchronize(st));
+    if (h->hscal[S_CERTPEND] && !h->hscal[S_STATUS]) {
+        // a long dirty list (global-path writes): certify it here, appending to the
+        // violations the kinetic kernel already recorded
+        k_certify<<<thread_grid(h, h->hscal[S_DIRTY], 256), 256, 0, st>>>(d, 0, h->viol, h->scal + S_VIOL,
+                                                                          h->viol_cap);
+        h->stats.kernel_launches++;
+        if (sync_scalars(h)) return KDT_ERR_CUDA;
+    }
+    if (timed) {
+        float ms = 0.f;
+        if (h->cfg.timing && cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) {
+            h->stats.kinetic_kernel_ms += ms;
+            h->stats.kinetic_kernel_timed++;
+        }
+        if (cudaEventElapsedTime(&ms, h->ev2, h->ev3) == cudaSuccess) {
+            if (h->cfg.timing) h->stats.step_graph_ms += ms;
+            rc = autotune_after(h, ms);
+            if (rc) return rc;
+        }
+    }
+    int s = h->hscal[S_STATUS];
+    if (s == DEV_ARG || s == DEV_RANGE || s == DEV_DUP_ID) return dev_to_abi(s);  // intake: nothing modified
+    if (s == 0) {
+        int ds = 0;
+        if (repair_step(h, &ds)) return KDT_ERR_CUDA;
+        s = ds;
+    }
+    if (s) {
+        // the step failed while running: finish it by a full rebuild of the final
+        // positions (the certified fallback); if those are invalid, roll back
+        h->stats.fallbacks++;
+        h->stats.last_fallback_reason = s;
+        h->stats.last_fallback_point = h->hscal[S_FAILPT];
+        if (h->cfg.debug & 1) {
+            h->built = true;  // keep the failed state for kdt_export_store
+            return dev_to_abi(s);
+        }
+        bool allow = h->cfg.fallback || s == DEV_DUPLICATE || s == DEV_DEGENERATE;
+        int rc2 = KDT_ERR_RETRY_EXHAUSTED;
+        if (allow) {
+            k_set_positions<<<(mi + 255) / 256, 256, 0, st>>>(h->xy, h->gmoves, mi);
+            h->stats.kernel_launches++;
+            rc2 = rebuild_all(h);
+        }
+        if (rc2) {
+            int rr = roll_back(h, mi);
+            if (rr) return rr;
+            return allow ? rc2 : dev_to_abi(s);
+        }
+    }
+    h->stats.steps++;
+    h->stats.moves += m;
+    if (h->cfg.verify) {
+        int64_t bad = 0;
+        int vr = verify_state(h, &bad);
+        if (vr) return vr;
+        if (bad) return KDT_ERR_INTERNAL;
+    }
+    return KDT_OK;
+}
+
+// canonical export of slots [s0, s0 + nslots) whose point ids are idbase .. idbase + np - 1
+int export_range(kdt *h, int s0, int nslots, int idbase, int np, int32_t *out, int64_t cap, int64_t *n_tri)
+{
+    cudaStream_t st = h->stream;
+    if (grow(h->exp_cnt, (size_t)np * 4) || grow(h->exp_off, (size_t)np * 4) || grow(h->exp_fill, (size_t)np * 4))
+        return KDT_ERR_CUDA;
+    int *cnt = (int *)h->exp_cnt.p, *off = (int *)h->exp_off.p, *fill = (int *)h->exp_fill.p;
+    CK(cudaMemsetAsync(cnt, 0, (size_t)np * 4, st));
+    k_exp_count<<<thread_grid(h, nslots, 256), 256, 0, st>>>(h->tv + s0, nslots, cnt, idbase);
+    h->stats.kernel_launches++;
+    if (scan(h, cnt, off, np, h->scal + S_TOTAL, st)) return KDT_ERR_CUDA;
+    if (sync_scalars(h)) return KDT_ERR_CUDA;
+    int64_t total = h->hscal[S_TOTAL];
+    *n_tri = total;
+    if (total > cap) return KDT_ERR_CAPACITY;
+    bool dev_out = total > 0 && is_device_ptr(out);
+    int3 *dst;
+    if (dev_out) {
+        dst = (int3 *)out;
+    } else {
+        if (grow(h->exp_out, (size_t)std::max<int64_t>(total, 1) * sizeof(int3))) return KDT_ERR_CUDA;
+        dst = (int3 *)h->exp_out.p;
+    }
+    CK(cudaMemsetAsync(fill, 0, (size_t)np * 4, st));
+    k_exp_place<<<thread_grid(h, nslots, 256), 256, 0, st>>>(h->tv + s0, nslots, off, fill, dst, idbase);
+    k_exp_sortseg<<<thread_grid(h, np, 256), 256, 0, st>>>(np, off, cnt, dst);
+    h->stats.kernel_launches += 2;
+    CK(cudaGetLastError());
+    if (!dev_out && total > 0)
+        CK(cudaMemcpyAsync(out, dst, (size_t)total * sizeof(int3), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return KDT_OK;
+}
+
+int build_impl(kdt *h, const int32_t *xy, const int64_t *offs, int n_inst)
+{
+    CK(cudaSetDevice(h->device));
+    free_state(h);
+    int rc = alloc_state(h, offs, n_inst);
+    if (rc) {
+        free_state(h);
+        return rc;
+    }
+    CK(cudaMemcpyAsync(h->xy, xy, (size_t)h->n * sizeof(int2),
+                       is_device_ptr(xy) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    return rebuild_all(h);
 }
 
 }  // namespace
@@ -523,6 +900,9 @@ int kdt_default_config(kdt_config *cfg)
     cfg->timing = 0;
     cfg->warps_per_block = WPB;
     cfg->use_graph = 1;
+    cfg->points_per_partition = 0;
+    cfg->warps_per_partition = 0;
+    cfg->autotune = 0;
     return KDT_OK;
 }
 
@@ -533,7 +913,8 @@ int kdt_create(kdt **out, const kdt_config *cfg, int device, void *cuda_stream)
     kdt_config c;
     if (cfg) c = *cfg;
     else kdt_default_config(&c);
-    if (c.domain_bits <= 0 || c.domain_bits > 28 || c.grid < 0 || c.grid > 4096 || c.retry_cap < 0)
+    if (c.domain_bits <= 0 || c.domain_bits > 28 || c.grid < 0 || c.grid > 4096 || c.retry_cap < 0 ||
+        c.points_per_partition < 0 || c.warps_per_partition < 0 || c.warps_per_partition > 32)
         return KDT_ERR_ARG;
     if (c.retry_cap == 0) c.retry_cap = 4096;
     if (cudaSetDevice(device) != cudaSuccess) return KDT_ERR_CUDA;
@@ -582,18 +963,26 @@ int kdt_destroy(kdt *h)
 
 int64_t kdt_num_points(const kdt *h) { return h && h->built ? h->n : 0; }
 
+int32_t kdt_num_instances(const kdt *h) { return h && h->built ? h->ninst : 0; }
+
 int kdt_build(kdt *h, const int32_t *xy, int64_t n)
 {
     if (!h || !xy || n < 0 || n > (1ll << 28)) return KDT_ERR_ARG;
     if (n < 3) return KDT_ERR_DEGENERATE;
-    CK(cudaSetDevice(h->device));
-    free_state(h);
-    int rc = alloc_state(h, n);
-    if (rc) return rc;
-    CK(cudaMemcpyAsync(h->xy, xy, (size_t)n * sizeof(int2),
-                       is_device_ptr(xy) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
-    rc = rebuild_positions(h);
-    return rc;
+    int64_t offs[2] = {0, n};
+    return build_impl(h, xy, offs, 1);
+}
+
+int kdt_build_batch(kdt *h, const int32_t *xy, const int64_t *offsets, int32_t n_inst)
+{
+    if (!h || !xy || !offsets || n_inst < 1 || n_inst > (1 << 20)) return KDT_ERR_ARG;
+    if (offsets[0] != 0) return KDT_ERR_ARG;
+    for (int i = 0; i < n_inst; ++i) {
+        if (offsets[i + 1] < offsets[i]) return KDT_ERR_ARG;
+        if (offsets[i + 1] - offsets[i] < 3) return KDT_ERR_DEGENERATE;
+    }
+    if (offsets[n_inst] > (1ll << 28)) return KDT_ERR_ARG;
+    return build_impl(h, xy, offsets, n_inst);
 }
 
 int kdt_rebuild(kdt *h)
@@ -601,195 +990,29 @@ int kdt_rebuild(kdt *h)
     if (!h) return KDT_ERR_ARG;
     if (!h->built) return KDT_ERR_STATE;
     CK(cudaSetDevice(h->device));
-    int rc = rebuild_positions(h);
-    return rc;
+    return rebuild_all(h);
 }
 
 int kdt_step(kdt *h, const kdt_move *moves, int64_t m)
 {
     if (!h || m < 0 || (m > 0 && !moves)) return KDT_ERR_ARG;
     if (!h->built) return KDT_ERR_STATE;
-    if (m == 0) return KDT_OK;
-    if (m > h->n) return KDT_ERR_DUPLICATE;  // some id must repeat (or be out of range)
-    CK(cudaSetDevice(h->device));
-    int rc = ensure_moves(h, m);
-    if (rc) return rc;
-    cudaStream_t st = h->stream;
-    const int mi = (int)m;
-    // device moves are read in place; host moves are copied in first
-    const int3 *mp = (const int3 *)moves;
-    if (!is_device_ptr(moves)) {
-        CK(cudaMemcpyAsync(h->moves, moves, (size_t)m * sizeof(int3), cudaMemcpyHostToDevice, st));
-        mp = h->moves;
-    }
-    h->stamp++;
-    Dev d = make_dev(h);
-    bool large = h->cfg.fallback && (double)m > (double)h->cfg.rebuild_ratio * (double)h->n;
-    if (large) {
-        // a step this large is cheaper as a rebuild (Abstract: "if the points move so
-        // far, it's better to rebuild the triangulation")
-        CK(cudaMemsetAsync(h->scal, 0, S_NUM * sizeof(int), st));
-        CK(cudaMemsetAsync(h->cell_cnt, 0, (size_t)h->ncells * sizeof(int), st));
-        k_intake<<<(mi + 255) / 256, 256, 0, st>>>(d, mp, mi, h->grid, h->cfg.domain_bits, h->cell_cnt,
-                                                   h->old_xy, h->move_cell);
-        h->stats.kernel_launches++;
-        if (sync_scalars(h)) return KDT_ERR_CUDA;
-        if (h->hscal[S_STATUS]) return dev_to_abi(h->hscal[S_STATUS]);
-        k_set_positions<<<(mi + 255) / 256, 256, 0, st>>>(h->xy, mp, mi);
-        h->stats.kernel_launches++;
-        rc = rebuild_positions(h);
-        if (rc) {
-            int rr = roll_back(h, mp, mi);
-            return rr ? rr : rc;
-        }
-        h->stats.steps++;
-        h->stats.moves += m;
-        return KDT_OK;
-    }
-    if (h->cfg.use_graph) {
-        // one graph launch per step: the kernels read m and the stamp from ctl
-        if (h->graph_gen != h->gen) {
-            drop_graph(h);
-            // nothing may allocate while capturing: size the scan scratch first
-            if (scan(h, h->cell_cnt, h->cell_off, h->ncells, h->scal + S_TOTAL, st)) return KDT_ERR_CUDA;
-            Dev dg = d;
-            dg.ctl = h->ctl;
-            CK(cudaStreamBeginCapture(h->cstream, cudaStreamCaptureModeThreadLocal));
-            int er = enqueue_step(h, h->cstream, dg, nullptr, 0, true);
-            cudaGraph_t g = nullptr;
-            cudaError_t ce = cudaStreamEndCapture(h->cstream, &g);
-            if (er || ce != cudaSuccess) {
-                if (g) cudaGraphDestroy(g);
-                return KDT_ERR_CUDA;
-            }
-            h->graph = g;
-            CK(cudaGraphInstantiate(&h->gexec, h->graph, 0));
-            h->graph_gen = h->gen;
-        }
-        h->hctl[0] = mi;
-        h->hctl[1] = h->stamp;
-        unsigned long long pa = (unsigned long long)(uintptr_t)mp;
-        h->hctl[2] = (int)(unsigned)(pa & 0xffffffffu);
-        h->hctl[3] = (int)(unsigned)(pa >> 32);
-        if (h->cfg.timing) CK(cudaEventRecord(h->ev2, st));
-        CK(cudaMemcpyAsync(h->ctl, h->hctl, 4 * sizeof(int), cudaMemcpyHostToDevice, st));
-        CK(cudaGraphLaunch(h->gexec, st));
-        if (h->cfg.timing) CK(cudaEventRecord(h->ev3, st));
-        h->stats.kernel_launches += 2;
-        CK(cudaStreamSynchronize(st));
-    } else {
-        if (enqueue_step(h, st, d, mp, mi, false)) return KDT_ERR_CUDA;
-        h->stats.kernel_launches += 2;
-        CK(cudaStreamSynchronize(st));
-    }
-    if (h->hscal[S_CERTPEND] && !h->hscal[S_STATUS]) {
-        // a long dirty list (global-path writes): certify it here, appending to the
-        // violations the kinetic kernel already recorded
-        k_certify<<<thread_grid(h, h->hscal[S_DIRTY], 256), 256, 0, st>>>(d, 0, h->viol, h->scal + S_VIOL,
-                                                                          h->viol_cap);
-        h->stats.kernel_launches++;
-        if (sync_scalars(h)) return KDT_ERR_CUDA;
-    }
-    if (h->cfg.timing) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) {
-            h->stats.kinetic_kernel_ms += ms;
-            h->stats.kinetic_kernel_timed++;
-        }
-        if (h->cfg.use_graph && cudaEventElapsedTime(&ms, h->ev2, h->ev3) == cudaSuccess)
-            h->stats.step_graph_ms += ms;
-    }
-    int s = h->hscal[S_STATUS];
-    if (s == DEV_ARG || s == DEV_RANGE || s == DEV_DUP_ID) {
-        // found at intake: nothing was modified
-        return dev_to_abi(s);
-    }
-    if (s == 0) {
-        int nv = h->hscal[S_VIOL];
-        bool overflow = h->hscal[S_DIRTY] > h->dirty_cap;
-        if (nv > 0 || overflow) {
-            int ds = 0;
-            if (overflow) {
-                if (certify_and_repair(h, true, &ds)) return KDT_ERR_CUDA;
-            } else {
-                // repair the violations already found, then certify what the repair wrote
-                h->stats.violations += nv;
-                if (nv > h->viol_cap) nv = h->viol_cap;
-                int dirty_before = h->hscal[S_DIRTY];
-                k_fixup<<<warp_grid(h, nv, 16), WPB * 32, 0, st>>>(d, h->viol, nv);
-                h->stats.kernel_launches++;
-                CK(cudaGetLastError());
-                if (sync_scalars(h)) return KDT_ERR_CUDA;
-                ds = h->hscal[S_STATUS];
-                if (!ds) {
-                    // certify the slots written by the repair (dirty range after dirty_before)
-                    Dev d2 = make_dev(h);
-                    bool all = h->hscal[S_DIRTY] > h->dirty_cap;
-                    if (all) {
-                        if (certify_and_repair(h, true, &ds)) return KDT_ERR_CUDA;
-                    } else {
-                        for (int round = 0; round < 64; ++round) {
-                            CK(cudaMemsetAsync(h->scal + S_VIOL, 0, sizeof(int), st));
-                            k_certify<<<thread_grid(h, 65536, 256), 256, 0, st>>>(d2, dirty_before, h->viol,
-                                                                                 h->scal + S_VIOL, h->viol_cap);
-                            h->stats.kernel_launches++;
-                            if (sync_scalars(h)) return KDT_ERR_CUDA;
-                            ds = h->hscal[S_STATUS];
-                            int nv2 = h->hscal[S_VIOL];
-                            if (ds || nv2 == 0) break;
-                            h->stats.violations += nv2;
-                            if (nv2 > h->viol_cap) nv2 = h->viol_cap;
-                            dirty_before = h->hscal[S_DIRTY];
-                            k_fixup<<<warp_grid(h, nv2, 16), WPB * 32, 0, st>>>(d2, h->viol, nv2);
-                            h->stats.kernel_launches++;
-                            if (sync_scalars(h)) return KDT_ERR_CUDA;
-                            ds = h->hscal[S_STATUS];
-                            if (ds) break;
-                            if (h->hscal[S_DIRTY] > h->dirty_cap) {
-                                if (certify_and_repair(h, true, &ds)) return KDT_ERR_CUDA;
-                                break;
-                            }
-                        }
-                    }
-                }
-            }
-            s = ds;
-        }
-    }
-    if (s) {
-        // the step failed while running: finish it by a full rebuild of the final
-        // positions (the certified fallback); if those are invalid, roll back
-        h->stats.fallbacks++;
-        h->stats.last_fallback_reason = s;
-        h->stats.last_fallback_point = h->hscal[S_FAILPT];
-        if (h->cfg.debug & 1) {
-            h->built = true;  // keep the failed state for kdt_export_store
-            return dev_to_abi(s);
-        }
-        bool allow = h->cfg.fallback || s == DEV_DUPLICATE || s == DEV_DEGENERATE;
-        int rc2 = KDT_ERR_RETRY_EXHAUSTED;
-        if (allow) {
-            k_set_positions<<<(mi + 255) / 256, 256, 0, st>>>(h->xy, mp, mi);
-            h->stats.kernel_launches++;
-            rc2 = rebuild_positions(h);
-        }
-        if (rc2) {
-            int rr = roll_back(h, mp, mi);
-            if (rr) return rr;
-            return allow ? rc2 : dev_to_abi(s);
-        }
-    }
-    h->stats.steps++;
-    h->stats.moves += m;
-    if (h->cfg.verify) {
-        int64_t bad = 0;
-        int vr = verify_state(h, &bad);
-        if (vr) return vr;
-        if (bad) {
-            return KDT_ERR_INTERNAL;
-        }
-    }
-    return KDT_OK;
+    if (h->ninst != 1) return KDT_ERR_STATE;  // batched handles step with kdt_step_batch
+    int64_t moff[2] = {0, m};
+    return step_impl(h, moves, moff, m);
+}
+
+int kdt_step_batch(kdt *h, const kdt_move *moves, const int64_t *move_offsets, int32_t n_inst)
+{
+    if (!h || !move_offsets || n_inst < 0) return KDT_ERR_ARG;
+    if (!h->built) return KDT_ERR_STATE;
+    if (n_inst != h->ninst) return KDT_ERR_ARG;
+    if (move_offsets[0] != 0) return KDT_ERR_ARG;
+    for (int i = 0; i < n_inst; ++i)
+        if (move_offsets[i + 1] < move_offsets[i]) return KDT_ERR_ARG;
+    int64_t m = move_offsets[n_inst];
+    if (m > 0 && !moves) return KDT_ERR_ARG;
+    return step_impl(h, moves, move_offsets, m);
 }
 
 int kdt_export_triangles(kdt *h, int32_t *out, int64_t cap, int64_t *n_tri)
@@ -797,36 +1020,17 @@ int kdt_export_triangles(kdt *h, int32_t *out, int64_t cap, int64_t *n_tri)
     if (!h || !n_tri || cap < 0 || (cap > 0 && !out)) return KDT_ERR_ARG;
     if (!h->built) return KDT_ERR_STATE;
     CK(cudaSetDevice(h->device));
-    cudaStream_t st = h->stream;
-    const int n = (int)h->n;
-    if (grow(h->exp_cnt, (size_t)n * 4) || grow(h->exp_off, (size_t)n * 4) || grow(h->exp_fill, (size_t)n * 4))
-        return KDT_ERR_CUDA;
-    int *cnt = (int *)h->exp_cnt.p, *off = (int *)h->exp_off.p, *fill = (int *)h->exp_fill.p;
-    CK(cudaMemsetAsync(cnt, 0, (size_t)n * 4, st));
-    k_exp_count<<<thread_grid(h, h->cap, 256), 256, 0, st>>>(h->tv, h->cap, cnt);
-    h->stats.kernel_launches++;
-    if (scan(h, cnt, off, n, h->scal + S_TOTAL, st)) return KDT_ERR_CUDA;
-    if (sync_scalars(h)) return KDT_ERR_CUDA;
-    int64_t total = h->hscal[S_TOTAL];
-    *n_tri = total;
-    if (total > cap) return KDT_ERR_CAPACITY;
-    bool dev_out = is_device_ptr(out);
-    int3 *dst;
-    if (dev_out) {
-        dst = (int3 *)out;
-    } else {
-        if (grow(h->exp_out, (size_t)std::max<int64_t>(total, 1) * sizeof(int3))) return KDT_ERR_CUDA;
-        dst = (int3 *)h->exp_out.p;
-    }
-    CK(cudaMemsetAsync(fill, 0, (size_t)n * 4, st));
-    k_exp_place<<<thread_grid(h, h->cap, 256), 256, 0, st>>>(h->tv, h->cap, off, fill, dst);
-    k_exp_sortseg<<<thread_grid(h, n, 256), 256, 0, st>>>(n, off, cnt, dst);
-    h->stats.kernel_launches += 2;
-    CK(cudaGetLastError());
-    if (!dev_out && total > 0)
-        CK(cudaMemcpyAsync(out, dst, (size_t)total * sizeof(int3), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    return KDT_OK;
+    return export_range(h, 0, h->cap, 0, (int)h->n, out, cap, n_tri);
+}
+
+int kdt_export_triangles_inst(kdt *h, int32_t inst, int32_t *out, int64_t cap, int64_t *n_tri)
+{
+    if (!h || !n_tri || cap < 0 || (cap > 0 && !out)) return KDT_ERR_ARG;
+    if (!h->built) return KDT_ERR_STATE;
+    if (inst < 0 || inst >= h->ninst) return KDT_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    int s0 = h->tofs[inst], p0 = h->pofs[inst];
+    return export_range(h, s0, h->tofs[inst + 1] - s0, p0, h->pofs[inst + 1] - p0, out, cap, n_tri);
 }
 
 int kdt_export_points(kdt *h, int32_t *xy, int64_t cap_points)
@@ -866,7 +1070,10 @@ int kdt_reset_stats(kdt *h)
     cudaSetDevice(h->device);
     cudaStreamSynchronize(h->stream);
     add_counters(h);
+    int64_t tp = h->stats.tuned_points_per_partition, tw = h->stats.tuned_warps_per_partition;
     memset(&h->stats, 0, sizeof h->stats);
+    h->stats.tuned_points_per_partition = tp;
+    h->stats.tuned_warps_per_partition = tw;
     return KDT_OK;
 }
 
@@ -952,7 +1159,7 @@ extern "C" int kdt_export_triangles_noalloc(kdt *h, int32_t *out, int64_t cap, i
     int *total = tiles + 1023;                            // grand total
     const int ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     CK(cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(int), st));
-    k_exp_count<<<thread_grid(h, h->cap, 256), 256, 0, st>>>(h->tv, h->cap, cnt);
+    k_exp_count<<<thread_grid(h, h->cap, 256), 256, 0, st>>>(h->tv, h->cap, cnt, 0);
     k_scan_tile<<<ntiles, SCAN_THREADS, 0, st>>>(cnt, off, n, tiles);
     k_scan_sums<<<1, 1024, 0, st>>>(tiles, ntiles, total);
     k_scan_add<<<ntiles, SCAN_THREADS, 0, st>>>(off, n, tiles);
@@ -963,7 +1170,7 @@ extern "C" int kdt_export_triangles_noalloc(kdt *h, int32_t *out, int64_t cap, i
     *n_tri = tot;
     if (tot > cap) return KDT_ERR_CAPACITY;
     CK(cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(int), st));
-    k_exp_place<<<thread_grid(h, h->cap, 256), 256, 0, st>>>(h->tv, h->cap, off, cnt, (int3 *)out);
+    k_exp_place<<<thread_grid(h, h->cap, 256), 256, 0, st>>>(h->tv, h->cap, off, cnt, (int3 *)out, 0);
     k_exp_sortseg<<<thread_grid(h, n, 256), 256, 0, st>>>(n, off, cnt, (int3 *)out);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));

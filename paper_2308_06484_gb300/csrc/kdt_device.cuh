@@ -74,6 +74,7 @@ struct Dev {
     int *viol;           // edges found not locally Delaunay: (slot << 2) | edge
     int *viol_count;
     int viol_cap;
+    int rlo, rn;         // the points of the instance being worked on (walk restarts)
     unsigned long long *counters;
     int use_filter;
     int retry_cap;
@@ -220,6 +221,18 @@ __device__ int check_edge(const Dev &d, int t, const int4 &v, const int4 &nb, in
     int2 p2 = v.z >= 0 ? __ldcg(d.xy + v.z) : z;
     int2 pd = dd >= 0 ? __ldcg(d.xy + dd) : z;
     return conflict(v.x, v.y, v.z, p0, p1, p2, dd, pd, d.use_filter, ex, ti) ? 1 : 0;
+}
+
+// largest k in [0, cnt) with off[k] <= x (CSR offsets, off[cnt] = total)
+__device__ __forceinline__ int csr_find(const int *off, int cnt, int x)
+{
+    int lo = 0, hi = cnt - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
 // ------------------------------------------------------------------ claims
@@ -635,7 +648,7 @@ __device__ __noinline__ int insert_point(Warp &w, const Dev &d, int p, int2 q, i
             if (attempt & 1) {
                 t = start;
             } else {
-                int r = (int)(xorshift(w.rng) % (unsigned)d.n);
+                int r = d.rlo + (int)(xorshift(w.rng) % (unsigned)d.rn);
                 t = __shfl_sync(FULL, __ldcg(d.pt_tri + r), 0);
                 if (t < 0) t = start;
             }

@@ -17,7 +17,18 @@ constexpr int DEV_DUP_ID = 10;  // a move id repeated within one step (found at 
 enum Slot : int {
     S_STATUS = 0, S_DIRTY = 1, S_VIOL = 2, S_TRIS = 3, S_DEFER = 4, S_THIRD = 5,
     S_MINX = 6, S_MINY = 7, S_MAXX = 8, S_MAXY = 9, S_TOTAL = 10, S_BAD = 11, S_ALIVE = 12,
-    S_WRAPS = 13, S_FAILPT = 14, S_DONE = 15, S_CERTPEND = 16, S_NUM = 20
+    S_WRAPS = 13, S_FAILPT = 14, S_DONE = 15, S_CERTPEND = 16, S_TICKET = 17, S_NUM = 20
+};
+
+// Instance tables (one instance for kdt_build; many for kdt_build_batch).  Every
+// instance is its own triangulation in one shared store: global point ids
+// pofs[i] .. pofs[i+1]-1, partitions cofs[i] .. cofs[i+1]-1 (grid[i] per side).
+struct Inst {
+    const int *pofs;
+    const int *cofs;
+    const int *grid;
+    const int *moff;  // per step: the moves of instance i are moff[i] .. moff[i+1]-1
+    int ninst;
 };
 
 __device__ __forceinline__ Warp make_warp(WarpShared *sh, int token, unsigned seed)
@@ -127,42 +138,6 @@ __global__ void k_scan_add(int *out, int n, const int *tile_sums)
 
 // ------------------------------------------------------------------ step: intake
 
-// Validate the moves (A2), stamp the moved ids, remember old positions, and count
-// the moves of each partition (Section III blocks; cell of the point's position at
-// the start of the step: the block that owns it).
-__global__ void k_intake(Dev d, const int3 *moves, int m, int grid, int bits, int *cell_cnt,
-                         int2 *old_xy, int *move_cell)
-{
-    if (d.ctl) {
-        m = __ldcg(d.ctl);
-        d.stamp = __ldcg(d.ctl + 1);
-    }
-    long long lim = 1ll << bits;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-        int3 mv = moves[i];
-        if (mv.x < 0 || mv.x >= d.n) {
-            atomicCAS(d.status, 0, DEV_ARG);
-            continue;
-        }
-        if (mv.y < 0 || mv.z < 0 || mv.y >= lim || mv.z >= lim) {
-            atomicCAS(d.status, 0, DEV_RANGE);
-            continue;
-        }
-        int prev = atomicExch(d.pt_stamp + mv.x, d.stamp);
-        if (prev == d.stamp) {
-            atomicCAS(d.status, 0, DEV_DUP_ID);
-            continue;
-        }
-        int2 o = d.xy[mv.x];
-        old_xy[i] = o;
-        int cx = (int)(((long long)o.x * grid) >> bits);
-        int cy = (int)(((long long)o.y * grid) >> bits);
-        int c = cy * grid + cx;
-        move_cell[i] = c;
-        atomicAdd(cell_cnt + c, 1);
-    }
-}
-
 // The moves of a step, read from the control block when the step is a graph launch
 // (ctl[2..3] hold the pointer), else from the argument.
 __device__ __forceinline__ const int3 *step_moves(const Dev &d, const int3 *moves)
@@ -176,8 +151,8 @@ __device__ __forceinline__ const int3 *step_moves(const Dev &d, const int3 *move
 // moved id, remember the old position, and push the move onto the list of the
 // partition that owns the point (its cell at the start of the step, Section III
 // blocks): next[i] = previous head of the cell's list.
-__global__ void k_intake_link(Dev d, const int3 *moves, int m, int grid, int bits, int *head, int *next,
-                              int2 *old_xy)
+__global__ void k_intake_link(Dev d, const int3 *moves, int m, Inst I, int bits, int *head, int *next,
+                              int2 *old_xy, int3 *gmoves)
 {
     if (d.ctl) {
         m = __ldcg(d.ctl);
@@ -186,8 +161,10 @@ __global__ void k_intake_link(Dev d, const int3 *moves, int m, int grid, int bit
     moves = step_moves(d, moves);
     long long lim = 1ll << bits;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        int inst = I.ninst > 1 ? csr_find(I.moff, I.ninst + 1, i) : 0;
+        int p0 = I.pofs[inst], ni = I.pofs[inst + 1] - p0;
         int3 mv = moves[i];
-        if (mv.x < 0 || mv.x >= d.n) {
+        if (mv.x < 0 || mv.x >= ni) {
             atomicCAS(d.status, 0, DEV_ARG);
             continue;
         }
@@ -195,16 +172,19 @@ __global__ void k_intake_link(Dev d, const int3 *moves, int m, int grid, int bit
             atomicCAS(d.status, 0, DEV_RANGE);
             continue;
         }
-        int prev = atomicExch(d.pt_stamp + mv.x, d.stamp);
+        int g = p0 + mv.x;
+        int prev = atomicExch(d.pt_stamp + g, d.stamp);
         if (prev == d.stamp) {
             atomicCAS(d.status, 0, DEV_DUP_ID);
             continue;
         }
-        int2 o = d.xy[mv.x];
+        int2 o = d.xy[g];
         old_xy[i] = o;
-        int cx = (int)(((long long)o.x * grid) >> bits);
-        int cy = (int)(((long long)o.y * grid) >> bits);
-        next[i] = atomicExch(head + cy * grid + cx, i);
+        gmoves[i] = make_int3(g, mv.y, mv.z);
+        int G = I.grid[inst];
+        int cx = (int)(((long long)o.x * G) >> bits);
+        int cy = (int)(((long long)o.y * G) >> bits);
+        next[i] = atomicExch(head + I.cofs[inst] + cy * G + cx, i);
     }
 }
 
@@ -218,24 +198,38 @@ __global__ void k_intake_link(Dev d, const int3 *moves, int m, int grid, int bit
 // message.  A point whose target is still occupied by a point that has not moved
 // yet is deferred.  The last warp to finish inserts the deferred points and
 // certifies the triangles written on the global-memory path.
-__device__ void step_tail(Warp &w, const Dev &d, const int4 *deferred, const int *defer_count, int defer_cap,
+__device__ void step_tail(Warp &w, Dev d, Inst I, const int4 *deferred, const int *defer_count, int defer_cap,
                           int *viol, int viol_cap);
 
 __global__ void __launch_bounds__(WPB * 32, 8) k_kinetic(Dev d, const int3 *moves, const int *head, const int *next,
-                                                         int ncells, int4 *deferred, int *defer_count,
-                                                         int defer_cap, int *viol, int viol_cap)
+                                                         Inst I, int ncells, int wpp, int4 *deferred,
+                                                         int *defer_count, int defer_cap, int *viol, int viol_cap)
 {
     if (d.ctl) d.stamp = __ldcg(d.ctl + 1);
-    moves = step_moves(d, moves);
     __shared__ WarpShared shs[WPB];
     int wib = threadIdx.x >> 5;
     int gw = blockIdx.x * (blockDim.x >> 5) + wib;
     int nw = gridDim.x * (blockDim.x >> 5);
     Warp w = make_warp(&shs[wib], gw + 1, gw + 17 * d.stamp);
-    for (int c = gw; c < ncells; c += nw) {
+    const int items = ncells * wpp;
+    while (true) {
+        // persistent warps pull (partition, share) work items from a ticket
+        int t = 0;
+        if (w.lane == 0) t = atomicAdd(d.status + S_TICKET, 1);
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= items) break;
+        int c = t / wpp, sub = t - c * wpp;
+        int inst = I.ninst > 1 ? csr_find(I.cofs, I.ninst + 1, c) : 0;
+        d.rlo = I.pofs[inst];
+        d.rn = I.pofs[inst + 1] - d.rlo;
         int i = __shfl_sync(FULL, __ldcg(head + c), 0);
+        int k = -1;
         while (i >= 0) {
             if (read_status(d)) break;
+            if (++k % wpp != sub) {
+                i = __shfl_sync(FULL, __ldcg(next + i), 0);
+                continue;
+            }
             int3 mv = moves[i];
             int p = mv.x;
             int2 q = make_int2(mv.y, mv.z);
@@ -282,7 +276,7 @@ __global__ void __launch_bounds__(WPB * 32, 8) k_kinetic(Dev d, const int3 *move
     done = __shfl_sync(FULL, done, 0);
     if (done == nw - 1) {
         __threadfence();
-        step_tail(w, d, deferred, defer_count, defer_cap, viol, viol_cap);
+        step_tail(w, d, I, deferred, defer_count, defer_cap, viol, viol_cap);
     }
     flush_counters(w, d);
 }
@@ -351,7 +345,7 @@ __device__ void certify_one(const Dev &d, int t, int *viol, int *viol_count, int
 // Tail of a step (one warp, after every other warp finished): insert the deferred
 // points, then certify the triangles written on the global-memory path (the staged
 // path certified its own).  A long dirty list is left to the host.
-__device__ void step_tail(Warp &w, const Dev &d, const int4 *deferred, const int *defer_count, int defer_cap,
+__device__ void step_tail(Warp &w, Dev d, Inst I, const int4 *deferred, const int *defer_count, int defer_cap,
                           int *viol, int viol_cap)
 {
     if (read_status(d)) return;
@@ -362,6 +356,9 @@ __device__ void step_tail(Warp &w, const Dev &d, const int4 *deferred, const int
         int4 e = deferred[j];
         int2 q = __ldcg(d.xy + e.x);
         q = bcast2(q, 0);
+        int inst = I.ninst > 1 ? csr_find(I.pofs, I.ninst + 1, e.x) : 0;
+        d.rlo = I.pofs[inst];
+        d.rn = I.pofs[inst + 1] - d.rlo;
         int rc = insert_point(w, d, e.x, q, e.w, e.y, e.z, false);
         if (rc) {
             if (rc > 0) set_status(d, rc);
@@ -390,10 +387,10 @@ __global__ void k_certify(Dev d, int lo, int *viol, int *viol_count, int viol_ca
 }
 
 // certify every slot (after a build, or when the dirty list overflowed)
-__global__ void k_certify_all(Dev d, int nslots, int *viol, int *viol_count, int viol_cap, int *wraps)
+__global__ void k_certify_all(Dev d, int s0, int nslots, int *viol, int *viol_count, int viol_cap, int *wraps)
 {
     unsigned ex = 0, ti = 0;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nslots; t += gridDim.x * blockDim.x) {
+    for (int t = s0 + blockIdx.x * blockDim.x + threadIdx.x; t < s0 + nslots; t += gridDim.x * blockDim.x) {
         certify_one(d, t, viol, viol_count, viol_cap, &ex, &ti);
         int4 v = __ldcg(d.tv + t);
         if ((v.w & ALIVE) && (v.x < 0 || v.y < 0 || v.z < 0)) {
@@ -485,12 +482,12 @@ __global__ void k_hilbert(const int2 *xy, int n, const int *bbox, int k, int shi
     atomicAdd(hist + h, 1);
 }
 
-__global__ void k_place_order(int n, const unsigned *key, const int *off, int *fill, int *order)
+__global__ void k_place_order(int n, const unsigned *key, const int *off, int *fill, int *order, int base)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     unsigned h = key[i];
-    order[off[h] + atomicAdd(fill + h, 1)] = i;
+    order[off[h] + atomicAdd(fill + h, 1)] = base + i;
 }
 
 // first j >= 2 with orient(order[0], order[1], order[j]) != 0
@@ -502,7 +499,7 @@ __global__ void k_third(const int2 *xy, int n, const int *order, int *third)
 }
 
 // The first triangle (a, b, c) and its three ghosts (c,b,inf), (a,c,inf), (b,a,inf).
-__global__ void k_init(Dev d, const int *order, const int *third, int *tri_count)
+__global__ void k_init(Dev d, const int *order, const int *third, int *tri_count, int s0)
 {
     int a = order[0], b = order[1], c = order[*third];
     if (orient2d(d.xy[a], d.xy[b], d.xy[c]) < 0) {
@@ -511,24 +508,25 @@ __global__ void k_init(Dev d, const int *order, const int *third, int *tri_count
         c = t;
     }
     const int G = KDT_GHOST;
-    d.tv[0] = make_int4(a, b, c, ALIVE);
-    d.tn[0] = make_int4((1 << 2) | 2, (2 << 2) | 2, (3 << 2) | 2, 0);
-    d.tv[1] = make_int4(c, b, G, ALIVE);
-    d.tn[1] = make_int4((3 << 2) | 1, (2 << 2) | 0, (0 << 2) | 0, 0);
-    d.tv[2] = make_int4(a, c, G, ALIVE);
-    d.tn[2] = make_int4((1 << 2) | 1, (3 << 2) | 0, (0 << 2) | 1, 0);
-    d.tv[3] = make_int4(b, a, G, ALIVE);
-    d.tn[3] = make_int4((2 << 2) | 1, (1 << 2) | 0, (0 << 2) | 2, 0);
-    d.pt_tri[a] = 0;
-    d.pt_tri[b] = 0;
-    d.pt_tri[c] = 0;
-    *tri_count = 4;
+    const int t0 = s0, t1 = s0 + 1, t2 = s0 + 2, t3 = s0 + 3;
+    d.tv[t0] = make_int4(a, b, c, ALIVE);
+    d.tn[t0] = make_int4((t1 << 2) | 2, (t2 << 2) | 2, (t3 << 2) | 2, 0);
+    d.tv[t1] = make_int4(c, b, G, ALIVE);
+    d.tn[t1] = make_int4((t3 << 2) | 1, (t2 << 2) | 0, (t0 << 2) | 0, 0);
+    d.tv[t2] = make_int4(a, c, G, ALIVE);
+    d.tn[t2] = make_int4((t1 << 2) | 1, (t3 << 2) | 0, (t0 << 2) | 1, 0);
+    d.tv[t3] = make_int4(b, a, G, ALIVE);
+    d.tn[t3] = make_int4((t2 << 2) | 1, (t1 << 2) | 0, (t0 << 2) | 2, 0);
+    d.pt_tri[a] = t0;
+    d.pt_tri[b] = t0;
+    d.pt_tri[c] = t0;
+    *tri_count = s0 + 4;
 }
 
 // Insert the points at sorted positions (2j+1) * 2^level, each starting its walk at
 // the triangle of its Hilbert predecessor (2j) * 2^level, already inserted.
 __global__ void __launch_bounds__(WPB * 32) k_insert_level(Dev d, const int *order, int level, int items,
-                                                           int *tri_count)
+                                                           int *tri_count, int nloc, int slot_end)
 {
     __shared__ WarpShared shs[WPB];
     int wib = threadIdx.x >> 5;
@@ -538,7 +536,7 @@ __global__ void __launch_bounds__(WPB * 32) k_insert_level(Dev d, const int *ord
     for (int j = gw; j < items; j += nw) {
         if (read_status(d)) break;
         long long i = ((long long)(2 * j + 1)) << level;
-        if (i >= d.n) continue;
+        if (i >= nloc) continue;
         int v = order[i];
         if (__shfl_sync(FULL, __ldcg(d.pt_tri + v), 0) >= 0) continue;  // one of the first three
         int parent = order[i - (1ll << level)];
@@ -547,7 +545,7 @@ __global__ void __launch_bounds__(WPB * 32) k_insert_level(Dev d, const int *ord
         int s = 0;
         if (w.lane == 0) s = atomicAdd(tri_count, 2);
         s = __shfl_sync(FULL, s, 0);
-        if (s + 1 >= d.cap) {
+        if (s + 1 >= slot_end) {
             set_status(d, DEV_INTERNAL);
             break;
         }
@@ -568,17 +566,17 @@ __device__ __forceinline__ bool finite_alive(const int4 &v)
     return (v.w & ALIVE) && v.x >= 0 && v.y >= 0 && v.z >= 0;
 }
 
-__global__ void k_exp_count(const int4 *tv, int nslots, int *cnt)
+__global__ void k_exp_count(const int4 *tv, int nslots, int *cnt, int idbase)
 {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nslots; t += gridDim.x * blockDim.x) {
         int4 v = tv[t];
         if (!finite_alive(v)) continue;
-        atomicAdd(cnt + min(v.x, min(v.y, v.z)), 1);
+        atomicAdd(cnt + min(v.x, min(v.y, v.z)) - idbase, 1);
     }
 }
 
 // rotate so the smallest id comes first (keeps the counter-clockwise order)
-__global__ void k_exp_place(const int4 *tv, int nslots, const int *off, int *fill, int3 *out)
+__global__ void k_exp_place(const int4 *tv, int nslots, const int *off, int *fill, int3 *out, int idbase)
 {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nslots; t += gridDim.x * blockDim.x) {
         int4 v = tv[t];
@@ -587,6 +585,9 @@ __global__ void k_exp_place(const int4 *tv, int nslots, const int *off, int *fil
         if (v.x < v.y && v.x < v.z) r = make_int3(v.x, v.y, v.z);
         else if (v.y < v.z) r = make_int3(v.y, v.z, v.x);
         else r = make_int3(v.z, v.x, v.y);
+        r.x -= idbase;
+        r.y -= idbase;
+        r.z -= idbase;
         out[off[r.x] + atomicAdd(fill + r.x, 1)] = r;
     }
 }

@@ -39,7 +39,8 @@ class Config(ctypes.Structure):
                 ("verify", ctypes.c_int32), ("timing", ctypes.c_int32),
                 ("warps_per_block", ctypes.c_int32), ("build_warps", ctypes.c_int32),
                 ("kinetic_warps", ctypes.c_int32), ("debug", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("use_graph", ctypes.c_int32), ("points_per_partition", ctypes.c_int32),
+                ("warps_per_partition", ctypes.c_int32), ("autotune", ctypes.c_int32)]
 
 
 _STAT_FIELDS = ["steps", "moves", "rebuilds", "fallbacks", "kernel_launches", "flips", "retries",
@@ -57,7 +58,8 @@ class Stats(ctypes.Structure):
                 + [("kinetic_kernel_ms", ctypes.c_double), ("kinetic_kernel_timed", ctypes.c_int64),
                    ("last_fallback_reason", ctypes.c_int64), ("last_fallback_point", ctypes.c_int64)]
                 + [(f, ctypes.c_int64) for f in _STAT_FIELDS2]
-                + [("step_graph_ms", ctypes.c_double), ("reserved", ctypes.c_int64 * 7)])
+                + [("step_graph_ms", ctypes.c_double), ("tuned_points_per_partition", ctypes.c_int64),
+                   ("tuned_warps_per_partition", ctypes.c_int64), ("reserved", ctypes.c_int64 * 5)])
 
 
 _lib = None
@@ -67,7 +69,8 @@ SYMBOLS = ["kdt_default_config", "kdt_create", "kdt_destroy", "kdt_build", "kdt_
            "kdt_rebuild", "kdt_export_triangles", "kdt_export_points", "kdt_verify",
            "kdt_num_points", "kdt_get_stats", "kdt_reset_stats", "kdt_error_string",
            "kdt_version", "kdt_eval_predicates", "kdt_export_store",
-           "kdt_export_triangles_noalloc"]
+           "kdt_export_triangles_noalloc", "kdt_build_batch", "kdt_step_batch",
+           "kdt_export_triangles_inst", "kdt_num_instances"]
 
 
 def lib_path():
@@ -104,6 +107,11 @@ def load(build_if_stale: bool = True):
     L.kdt_eval_predicates.argtypes = [vp, vp, i64, vp, i32, vp]
     L.kdt_export_store.argtypes = [vp, vp, vp, vp, i64]
     L.kdt_export_triangles_noalloc.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
+    L.kdt_build_batch.argtypes = [vp, vp, vp, ctypes.c_int32]
+    L.kdt_step_batch.argtypes = [vp, vp, vp, ctypes.c_int32]
+    L.kdt_export_triangles_inst.argtypes = [vp, ctypes.c_int32, vp, i64, ctypes.POINTER(i64)]
+    L.kdt_num_instances.argtypes = [vp]
+    L.kdt_num_instances.restype = ctypes.c_int32
     for s in SYMBOLS:
         getattr(L, s)
     _lib = L
@@ -186,6 +194,39 @@ class Triangulation:
         p, m = _ptr(moves)
         _check(self.L.kdt_step(self.h, p, m), "kdt_step")
 
+    def build_batch(self, xys):
+        """Build one triangulation per point set in `xys` (list of (n_i, 2) int32 arrays)."""
+        sizes = [int(np.asarray(x).shape[0]) for x in xys]
+        offs = np.zeros(len(sizes) + 1, dtype=np.int64)
+        offs[1:] = np.cumsum(sizes)
+        allxy = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.int32).reshape(-1, 2) for x in xys]))
+        self._n_hint = int(offs[-1])
+        self._offs = offs
+        _check(self.L.kdt_build_batch(self.h, ctypes.c_void_p(allxy.ctypes.data),
+                                      ctypes.c_void_p(offs.ctypes.data), len(sizes)), "kdt_build_batch")
+
+    def step_batch(self, moves, move_offsets):
+        """One step of every instance: moves (m, 3) int32 with instance-local ids
+        (numpy or torch, host or CUDA) and int64 CSR offsets (n_inst + 1)."""
+        p, _ = _ptr(moves)
+        mo = np.ascontiguousarray(np.asarray(move_offsets, dtype=np.int64))
+        _check(self.L.kdt_step_batch(self.h, p, ctypes.c_void_p(mo.ctypes.data), mo.shape[0] - 1),
+               "kdt_step_batch")
+
+    def export_triangles_inst(self, inst):
+        nt = ctypes.c_int64(0)
+        rc = self.L.kdt_export_triangles_inst(self.h, inst, None, 0, ctypes.byref(nt))
+        if rc not in (KDT_OK, -5):
+            _check(rc, "kdt_export_triangles_inst")
+        out = np.empty((nt.value, 3), dtype=np.int32)
+        _check(self.L.kdt_export_triangles_inst(self.h, inst, ctypes.c_void_p(out.ctypes.data), nt.value,
+                                                ctypes.byref(nt)), "kdt_export_triangles_inst")
+        return out
+
+    @property
+    def n_instances(self):
+        return int(self.L.kdt_num_instances(self.h))
+
     def rebuild(self):
         _check(self.L.kdt_rebuild(self.h), "kdt_rebuild")
 
@@ -249,6 +290,8 @@ class Triangulation:
         for f in _STAT_FIELDS2:
             d[f] = int(getattr(s, f))
         d["step_graph_ms"] = float(s.step_graph_ms)
+        d["tuned_points_per_partition"] = int(s.tuned_points_per_partition)
+        d["tuned_warps_per_partition"] = int(s.tuned_warps_per_partition)
         return d
 
     def reset_stats(self):
