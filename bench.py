@@ -198,6 +198,128 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+C4_WORKLOAD = ("512 instances, sizes log-uniform 1e3-2e5 (seeded), uniform on [0,2^20)^2, "
+               "~256 points per partition, 1-4 moves per partition per step (1-8 units)")
+
+
+def run_c4(args):
+    """Batched workload: every instance advanced by one kdt_step_batch per step
+    (one graph launch), against the same instances stepped one handle at a time and
+    against a full rebuild of every instance."""
+    import torch
+    from paper_2308_06484_gb300 import kdt, workloads as W
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    ws = W.c4()
+    # the autotuner times one step of each of its 9 configurations first
+    warmup = max(args.warmup, 9 + 3) if args.autotune else args.warmup
+    args.warmup = warmup
+    nsteps = args.warmup + args.steps
+    steps = []
+    for _ in range(nsteps):
+        mv = [w.next_moves() for w in ws]
+        offs = np.zeros(len(mv) + 1, dtype=np.int64)
+        offs[1:] = np.cumsum([m.shape[0] for m in mv])
+        steps.append((torch.from_numpy(np.ascontiguousarray(np.concatenate(mv))).to(dev), offs, mv))
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    ws0 = W.c4()  # the same seeded instances from their start positions
+    start = [w.positions for w in ws0]
+    tri = kdt.Triangulation(kdt.default_config(domain_bits=20, timing=1, autotune=args.autotune))
+    tri.build_batch(start)
+    for i in range(args.warmup):
+        tri.step_batch(steps[i][0], steps[i][1])
+    tri.reset_stats()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(0)
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        d, offs, _ = steps[args.warmup + k]
+        ev[k][0].record()
+        tri.step_batch(d, offs)
+        ev[k][1].record()
+        flush.zero_()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    sec = sum(a.elapsed_time(b) for a, b in ev) / 1000.0
+    st = tri.stats()
+    moves = st["moves"]
+    verify_bad = tri.verify()
+    check = None
+    if args.check:
+        import oracle
+        # the generators already stand at the final positions (all steps were drawn)
+        sample = list(range(0, len(ws), max(1, len(ws) // 32))) + [len(ws) - 1]
+        check = all(np.array_equal(tri.export_triangles_inst(i), oracle.delaunay(ws[i].positions))
+                    for i in sample)
+    # comparator 1: the same instances, one handle each, stepped one after another
+    plain_ms = None
+    if args.c4_plain_steps > 0:
+        hs = []
+        for x in start:
+            t1 = kdt.Triangulation(kdt.default_config(domain_bits=20))
+            t1.build(x)
+            hs.append(t1)
+        for i in range(args.warmup):
+            for t1, m1 in zip(hs, steps[i][2]):
+                t1.step(m1)
+        evp = []
+        torch.cuda.synchronize()
+        for k in range(args.c4_plain_steps):
+            _, _, mv = steps[args.warmup + k]
+            dm = [torch.from_numpy(m1).to(dev) for m1 in mv]
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            for t1, m1 in zip(hs, dm):
+                t1.step(m1)
+            b.record()
+            evp.append((a, b, sum(m1.shape[0] for m1 in mv)))
+        torch.cuda.synchronize()
+        plain_ms = sum(a.elapsed_time(b) for a, b, _ in evp) / len(evp)
+        plain_moves = sum(c for _, _, c in evp) / len(evp)
+        for t1 in hs:
+            t1.close()
+    # comparator 2: full rebuild of every instance
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    tri.rebuild()
+    b.record()
+    torch.cuda.synchronize()
+    rebuild_ms = a.elapsed_time(b)
+    m_avg = moves / args.steps
+    peak, peak_kind = measured_peaks()
+    kin_ms = st["kinetic_kernel_ms"] / max(1, st["kinetic_kernel_timed"])
+    achieved = BYTES_PER_UPDATE * m_avg / (kin_ms / 1000.0) / 1e9
+    line = {
+        "metric": METRIC, "value": moves / sec, "unit": "updates/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sec / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64+int128 exact (fp32 filter)", "data": "synthetic",
+        "config": {"workload": C4_WORKLOAD, "instances": len(ws), "points": int(sum(w.n for w in ws)),
+                   "moves_per_step": m_avg, "l2": "flushed between timed steps (256 MB write)",
+                   "autotune": args.autotune, "tuned_points_per_partition": st["tuned_points_per_partition"],
+                   "tuned_warps_per_partition": st["tuned_warps_per_partition"]},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "k_kinetic", "kernel_ms": kin_ms, "peak_kind": peak_kind},
+        "comparators": {
+            "gpu_kinetic_one_handle_per_instance": (None if plain_ms is None else
+                                                    {"value": plain_moves / (plain_ms / 1000.0), "unit": "updates/s",
+                                                     "ms_per_step": plain_ms}),
+            "gpu_full_rebuild_all_instances": {"value": m_avg / (rebuild_ms / 1000.0), "unit": "updates/s",
+                                               "ms_per_rebuild": rebuild_ms},
+        },
+        "gpu_launches": int(st["kernel_launches"]), "fallbacks": int(st["fallbacks"]), "clocks": clk,
+        "verify_violations": int(verify_bad),
+    }
+    if check is not None:
+        line["sampled_instances_match_oracle"] = check
+    print(json.dumps(line), flush=True)
+    tri.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -212,11 +334,17 @@ def main():
     ap.add_argument("--ref-budget-s", type=float, default=90.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--check", action="store_true", help="compare the final state with the oracle")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c4"],
+                    help="c2: the headline single instance; c4: 512 batched instances")
+    ap.add_argument("--autotune", type=int, default=1)
+    ap.add_argument("--c4-plain-steps", type=int, default=3)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "c4":
+        return run_c4(args)
 
     import torch
     import torch.distributed as dist

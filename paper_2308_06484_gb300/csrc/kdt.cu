@@ -36,7 +36,7 @@ struct Buf {
 // the partition sizes and warps per partition the autotuner tries
 constexpr int TUNE_PPP[3] = {128, 256, 512};
 constexpr int TUNE_WPP[3] = {1, 2, 4};
-constexpr int TUNE_STEPS = 2;  // timed steps per configuration
+constexpr int TUNE_STEPS = 1;  // timed steps per configuration
 
 }  // namespace
 
@@ -51,7 +51,7 @@ struct kdt {
     // instances
     int ninst = 0;
     std::vector<int> pofs, tofs, cofs, igrid;  // host copies
-    int *d_pofs = nullptr, *d_cofs = nullptr, *d_grid = nullptr, *d_moff = nullptr;
+    int *d_pofs = nullptr, *d_cofs = nullptr, *d_grid = nullptr, *d_moff = nullptr, *d_tofs = nullptr;
     int *h_moff = nullptr;  // pinned
     int ncells = 0;          // partitions (all instances)
     int ppp = 256;           // points per partition in use
@@ -198,6 +198,7 @@ Inst make_inst(kdt *h)
     I.pofs = h->d_pofs;
     I.cofs = h->d_cofs;
     I.grid = h->d_grid;
+    I.tofs = h->d_tofs;
     I.moff = h->d_moff;
     I.ninst = h->ninst;
     return I;
@@ -463,7 +464,7 @@ void free_state(kdt *h)
     h->gen++;
     void *ps[] = {h->xy, h->pt_tri, h->pt_stamp, h->tv, h->tn, h->viol, h->moves, h->gmoves, h->old_xy,
                   h->next, h->head, h->deferred, h->dirty, h->scan_tmp, h->d_pofs, h->d_cofs, h->d_grid,
-                  h->d_moff};
+                  h->d_moff, h->d_tofs};
     for (void *p : ps)
         if (p) cudaFree(p);
     if (h->h_moff) cudaFreeHost(h->h_moff);
@@ -471,6 +472,7 @@ void free_state(kdt *h)
     h->viol = nullptr; h->moves = nullptr; h->gmoves = nullptr; h->old_xy = nullptr; h->next = nullptr;
     h->head = nullptr; h->deferred = nullptr; h->dirty = nullptr; h->scan_tmp = nullptr;
     h->d_pofs = nullptr; h->d_cofs = nullptr; h->d_grid = nullptr; h->d_moff = nullptr; h->h_moff = nullptr;
+    h->d_tofs = nullptr;
     h->mcap = 0; h->dirty_cap = 0; h->scan_tmp_cap = 0;
     Buf *bs[] = {&h->key, &h->bord, &h->hist, &h->hoff, &h->exp_cnt, &h->exp_off, &h->exp_fill, &h->exp_out};
     for (Buf *b : bs) free_buf(*b);
@@ -496,10 +498,12 @@ int alloc_state(kdt *h, const int64_t *offs, int n_inst)
     h->cap = h->tofs[n_inst];
     h->built = false;
     if (dalloc(&h->xy, h->n) || dalloc(&h->pt_tri, h->n) || dalloc(&h->pt_stamp, h->n) || dalloc(&h->tv, h->cap) ||
-        dalloc(&h->tn, h->cap) || dalloc(&h->d_pofs, n_inst + 1) || dalloc(&h->d_moff, n_inst + 1))
+        dalloc(&h->tn, h->cap) || dalloc(&h->d_pofs, n_inst + 1) || dalloc(&h->d_moff, n_inst + 1) ||
+        dalloc(&h->d_tofs, n_inst + 1))
         return KDT_ERR_CUDA;
     if (cudaMallocHost(&h->h_moff, (n_inst + 1) * sizeof(int)) != cudaSuccess) return KDT_ERR_CUDA;
     CK(cudaMemcpy(h->d_pofs, h->pofs.data(), (n_inst + 1) * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_tofs, h->tofs.data(), (n_inst + 1) * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMemsetAsync(h->pt_stamp, 0, h->n * sizeof(int), h->stream));
     h->viol_cap = std::max(4096, h->cap);
     if (dalloc(&h->viol, (size_t)h->viol_cap)) return KDT_ERR_CUDA;
@@ -554,7 +558,7 @@ int verify_state(kdt *h, int64_t *bad)
     Dev d = make_dev(h);
     CK(cudaMemsetAsync(h->scal + S_BAD, 0, 3 * sizeof(int), h->stream));
     k_verify<<<thread_grid(h, std::max<int64_t>(h->cap, h->n), 256), 256, 0, h->stream>>>(
-        d, h->cap, h->scal + S_BAD, h->scal + S_ALIVE, h->scal + S_WRAPS);
+        d, make_inst(h), h->cap, h->scal + S_BAD, h->scal + S_ALIVE, h->scal + S_WRAPS);
     h->stats.kernel_launches++;
     CK(cudaGetLastError());
     if (sync_scalars(h)) return KDT_ERR_CUDA;
@@ -631,8 +635,8 @@ int repair_step(kdt *h, int *ds)
 }
 
 // Autotuner: the first TUNE_STEPS steps of every (points per partition, warps per
-// partition) pair are timed with events around the step; then the fastest pair is
-// kept.  Results do not depend on the pair.  A single instance with a configured
+// partition) pair are timed with events around the step; then the pair with the
+// least time per move is kept.  Results do not depend on the pair.  A single instance with a configured
 // grid tunes the warps per partition only.
 bool tune_fixed_grid(const kdt *h) { return h->ninst == 1 && h->cfg.grid > 0; }
 
@@ -648,10 +652,10 @@ int autotune_before(kdt *h)
     return 0;
 }
 
-int autotune_after(kdt *h, float ms)
+int autotune_after(kdt *h, float ms, int64_t m)
 {
     if (h->tune_idx < 0 || h->tune_done) return 0;
-    h->tune_ms[h->tune_idx] += ms;
+    h->tune_ms[h->tune_idx] += (double)ms / (double)(m > 0 ? m : 1);
     if (++h->tune_count < TUNE_STEPS) return 0;
     h->tune_count = 0;
     ++h->tune_idx;
@@ -767,7 +771,7 @@ int step_impl(kdt *h, const kdt_move *moves, const int64_t *moff, int64_t m)
         }
         if (cudaEventElapsedTime(&ms, h->ev2, h->ev3) == cudaSuccess) {
             if (h->cfg.timing) h->stats.step_graph_ms += ms;
-            rc = autotune_after(h, ms);
+            rc = autotune_after(h, ms, m);
             if (rc) return rc;
         }
     }

@@ -146,6 +146,12 @@ __device__ __forceinline__ int read_status(const Dev &d) { return __shfl_sync(FU
 // Load tv[t] and tn[t] together (lanes 0 and 1) and broadcast.
 // A slot outside the store (an unclaimed read can see the transient -1 neighbour of
 // a triangle another warp is writing) reads as a dead triangle.
+// Vertex id of the instance whose points are [d.rlo, d.rlo + d.rn) (or the ghost).
+__device__ __forceinline__ bool of_instance(const Dev &d, int id)
+{
+    return id == KDT_GHOST || (unsigned)(id - d.rlo) < (unsigned)d.rn;
+}
+
 __device__ __forceinline__ void load_tri(const Warp &w, const Dev &d, int t, int4 &v, int4 &nb)
 {
     int4 x = make_int4(0, 0, 0, 0);
@@ -302,6 +308,13 @@ __device__ __noinline__ int walk(Warp &w, const Dev &d, int t, int2 q, int &wher
         int4 v, nb;
         load_tri(w, d, t, v, nb);
         if (!(v.w & ALIVE)) return -1;
+        // The walk reads without claims: a triangle being written can pair its new
+        // vertices with old neighbour words (zero in a fresh slot, i.e. slot 0).  In a
+        // batch every instance covers the same coordinate domain, so such a reference
+        // can lead into another instance's triangulation, where the geometry alone
+        // would accept a location.  A triangle with a vertex outside the instance
+        // ends the walk (the caller restarts).
+        if (!of_instance(d, v.x) || !of_instance(d, v.y) || !of_instance(d, v.z)) return -1;
         int2 p0, p1, p2, pz;
         load_xy4(w, d, v.x, v.y, v.z, KDT_GHOST, p0, p1, p2, pz);
         int g = v.x == KDT_GHOST ? 0 : (v.y == KDT_GHOST ? 1 : (v.z == KDT_GHOST ? 2 : -1));

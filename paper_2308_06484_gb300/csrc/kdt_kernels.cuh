@@ -28,6 +28,7 @@ struct Inst {
     const int *cofs;
     const int *grid;
     const int *moff;  // per step: the moves of instance i are moff[i] .. moff[i+1]-1
+    const int *tofs;  // triangle slots of instance i: tofs[i] .. tofs[i+1]-1
     int ninst;
 };
 
@@ -613,7 +614,7 @@ __global__ void k_exp_sortseg(int n, const int *off, const int *cnt, int3 *out)
 
 // ------------------------------------------------------------------ verifier
 
-__global__ void k_verify(Dev d, int nslots, int *bad, int *alive, int *wraps)
+__global__ void k_verify(Dev d, Inst I, int nslots, int *bad, int *alive, int *wraps)
 {
     unsigned ex = 0, ti = 0;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nslots; t += gridDim.x * blockDim.x) {
@@ -625,6 +626,21 @@ __global__ void k_verify(Dev d, int nslots, int *bad, int *alive, int *wraps)
         if (ghosts > 1 || (v.x == v.y || v.y == v.z || v.x == v.z)) {
             atomicAdd(bad, 1);
             continue;
+        }
+        if (I.ninst > 1) {
+            // every vertex and neighbour of a triangle belongs to the instance of its slot
+            int inst = csr_find(I.tofs, I.ninst + 1, t);
+            int plo = I.pofs[inst], phi = I.pofs[inst + 1], slo = I.tofs[inst], shi = I.tofs[inst + 1];
+            bool own = true;
+            for (int e = 0; e < 3; ++e) {
+                int id = e == 0 ? v.x : (e == 1 ? v.y : v.z);
+                int r = (e == 0 ? nb.x : (e == 1 ? nb.y : nb.z)) >> 2;
+                own = own && (id == KDT_GHOST || (id >= plo && id < phi)) && r >= slo && r < shi;
+            }
+            if (!own) {
+                atomicAdd(bad, 1);
+                continue;
+            }
         }
         if (ghosts == 0 && orient2d(d.xy[v.x], d.xy[v.y], d.xy[v.z]) <= 0) atomicAdd(bad, 1);
         if (nb.w != 0) atomicAdd(bad, 1);  // a claim left behind

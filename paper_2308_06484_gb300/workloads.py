@@ -143,21 +143,22 @@ class KineticWorkload:
     def _choose(self):
         G = self.grid
         cells = cell_of(self.pos, G, self.bits)
-        order = np.argsort(cells, kind="stable")
         counts = np.bincount(cells, minlength=G * G)
         starts = np.concatenate([[0], np.cumsum(counts)[:-1]])
         lo, hi = self.mpc
         want = self.rng.integers(lo, hi + 1, size=G * G)
         want = np.minimum(want, counts)
-        chosen = []
         if hi == 1:
+            order = np.argsort(cells, kind="stable")
             cs = np.nonzero(want)[0]
             off = (self.rng.random(cs.shape[0]) * counts[cs]).astype(np.int64)
             chosen = order[starts[cs] + off]
             return chosen
         # several points per cell: random keys, take the first `want` of each segment
+        # (order by cell, then key, then id: two stable sorts)
         rk = self.rng.random(self.n)
-        order2 = np.lexsort((rk, cells))
+        o1 = np.argsort(rk, kind="stable")
+        order2 = o1[np.argsort(cells[o1], kind="stable")]
         rank = np.arange(self.n) - starts[cells[order2]]
         sel = rank < want[cells[order2]]
         return order2[sel]
@@ -210,7 +211,9 @@ class KineticWorkload:
         new = _key(self.pos[ids])
         keep = np.ones(self.skeys.size, dtype=bool)
         keep[np.searchsorted(self.skeys, old)] = False
-        self.skeys = np.sort(np.concatenate([self.skeys[keep], new]))
+        rest = self.skeys[keep]
+        new = np.sort(new)
+        self.skeys = np.insert(rest, np.searchsorted(rest, new), new)
         self.step_index += 1
         return np.ascontiguousarray(moves)
 

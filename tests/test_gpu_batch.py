@@ -86,3 +86,24 @@ def test_batch_errors():
         assert np.array_equal(t.export_triangles_inst(i), before[i])
     with pytest.raises(kdt.KDTError):
         t.build_batch([w.positions[:2] for w in ws])  # an instance with 2 points
+
+
+def test_batch_full_size_sampled():
+    """The 512-instance workload at full size (2.2e7 points): after the build and two
+    steps every triangle belongs to its own instance (kdt_verify) and sampled
+    instances equal the oracle."""
+    from paper_2308_06484_gb300 import kdt
+    ws = W.c4()
+    t = kdt.Triangulation(kdt.default_config(domain_bits=20))
+    t.build_batch([w.positions for w in ws])
+    sample = list(range(0, 512, 32)) + [1, 511]
+    assert t.verify() == 0
+    for i in sample:
+        assert_same(t.export_triangles_inst(i), ws[i].positions, "build instance %d" % i)
+    for s in range(2):
+        mv, offs = _step_moves(ws)
+        t.step_batch(mv, offs)
+    assert t.verify() == 0
+    for i in sample:
+        assert_same(t.export_triangles_inst(i), ws[i].positions, "step instance %d" % i)
+    assert t.stats()["fallbacks"] == 0
