@@ -105,7 +105,11 @@ typedef struct {
     int64_t cycles_gather, cycles_claim, cycles_local, cycles_writeback; /* phase sums    */
     double step_graph_ms;         /* event-timed control copy + step graph (timing = 1)     */
     int64_t tuned_points_per_partition, tuned_warps_per_partition; /* autotuner choice   */
-    int64_t reserved[5];
+    int64_t cycles_ear, cycles_lawson, cycles_certify; /* parts of cycles_local             */
+    int64_t proposal_moves;       /* staged moves located with the learned proposal on      */
+    int64_t proposal_hits;        /* ... whose proposed hole triangle held the new position */
+    int64_t trace_rows;           /* training rows written (kdt_set_trace)                  */
+    int64_t reserved[8];
 } kdt_stats;
 
 /* ---- lifecycle ------------------------------------------------------------------ */

@@ -26,7 +26,7 @@ using namespace kd;
 
 namespace {
 
-constexpr int ABI_VERSION = 2;
+constexpr int ABI_VERSION = 3;
 
 struct Buf {
     void *p = nullptr;
@@ -543,6 +543,12 @@ void add_counters(kdt *h)
     s.cycles_claim += (int64_t)c[C_CYC_CLAIM] << 6;
     s.cycles_local += (int64_t)c[C_CYC_LOCAL] << 6;
     s.cycles_writeback += (int64_t)c[C_CYC_WB] << 6;
+    s.cycles_ear += (int64_t)c[C_CYC_EAR] << 6;
+    s.cycles_lawson += (int64_t)c[C_CYC_LAWSON] << 6;
+    s.cycles_certify += (int64_t)c[C_CYC_CERT] << 6;
+    s.proposal_moves += c[C_PROP_MOVES];
+    s.proposal_hits += c[C_PROP_HITS];
+    s.trace_rows += c[C_TRACE_ROWS];
 }
 
 // Undo a step that failed after it started: restore the old positions and rebuild.

@@ -28,7 +28,7 @@ namespace kd {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int KMAX = 64;               // largest vertex degree a deletion handles
 constexpr int MAXC = 2 * KMAX + 16;    // claims one warp may hold
-constexpr int STACK = 64;              // Lawson flip stack per warp
+constexpr int STACK = 48;              // Lawson flip stack per warp
 constexpr int WALK_CAP = 1 << 12;      // steps before a walk restarts
 constexpr int WALK_RESTARTS = 1024;    // restarts before point location gives up
 constexpr int ALIVE = 1;
@@ -52,6 +52,7 @@ enum Counter : int {
     C_FLIPS = 0, C_RETRIES, C_WALK_STEPS, C_EXACT, C_TIES, C_DEFERRED, C_VIOL, C_FIX_FLIPS,
     C_DEG_DEL, C_STACK_DROP, C_SPLIT_EDGE, C_SPLIT_GHOST, C_DELETES, C_INSERTS, C_FLIP_TESTS,
     C_MV_GLOBAL, C_CYC_MOVE, C_CYC_GATHER, C_CYC_CLAIM, C_CYC_LOCAL, C_CYC_WB,
+    C_CYC_EAR, C_CYC_LAWSON, C_CYC_CERT, C_PROP_MOVES, C_PROP_HITS, C_TRACE_ROWS,
     C_NUM,
     C_CYC_MAX = C_NUM  // a second device slot, updated with atomicMax
 };
@@ -96,17 +97,52 @@ struct WarpShared {
     int4 lnl[LM];          // the same neighbours as staged indices (-1: not staged)
     int2 lp[LM][3];        // coordinates of its three vertices
     int EO[KMAX];          // staged outer ref (index << 2 | edge) of each link edge
+    // per-warp state every lane reads; only lane 0 writes it (then a warp barrier)
+    unsigned cnt[C_NUM];   // event counters, flushed at the end of the kernel
+    unsigned cyc_max;      // longest single move (cycles / 64)
+    unsigned rng;          // xorshift state
+    int ncl;               // claims held (cl[0 .. ncl-1])
+    int rlo, rn;           // the points of the instance being worked on
+    unsigned earbad;       // ears found invalid in the current clipping round
 };
 
+// A warp's handle, passed by value: its shared block, its lane and its claim token.
+// Everything mutable lives in the shared block, so no per-lane copy of warp state
+// exists (each lane would otherwise hold an identical copy in local memory).
 struct Warp {
     WarpShared *sh;
     int lane;
     int token;
-    int ncl;
-    unsigned rng;
-    unsigned cnt[C_NUM];
-    unsigned cyc_max;   // longest single move (cycles / 64)
 };
+
+__device__ __forceinline__ void cnt_add(const Warp w, int i, unsigned v)
+{
+    if (w.lane == 0) w.sh->cnt[i] += v;
+}
+
+// next value of the warp's random state (uniform across the warp)
+__device__ __forceinline__ unsigned warp_rand(const Warp w)
+{
+    unsigned s = w.sh->rng;
+    s ^= s << 13;
+    s ^= s >> 17;
+    s ^= s << 5;
+    __syncwarp();
+    if (w.lane == 0) w.sh->rng = s;
+    __syncwarp();
+    return s;
+}
+
+// the instance whose points are [lo, lo + n) (walk restarts, of_instance)
+__device__ __forceinline__ void set_instance(const Warp w, int lo, int n)
+{
+    __syncwarp();
+    if (w.lane == 0) {
+        w.sh->rlo = lo;
+        w.sh->rn = n;
+    }
+    __syncwarp();
+}
 
 // ------------------------------------------------------------------ helpers
 
@@ -128,14 +164,6 @@ __device__ __forceinline__ int2 bcast2(int2 v, int src)
 
 __device__ __forceinline__ int comp(const int4 &v, int i) { return i == 0 ? v.x : (i == 1 ? v.y : v.z); }
 
-__device__ __forceinline__ unsigned xorshift(unsigned &s)
-{
-    s ^= s << 13;
-    s ^= s >> 17;
-    s ^= s << 5;
-    return s;
-}
-
 __device__ __forceinline__ void set_status(const Dev &d, int code)
 {
     atomicCAS(d.status, 0, code);
@@ -146,13 +174,13 @@ __device__ __forceinline__ int read_status(const Dev &d) { return __shfl_sync(FU
 // Load tv[t] and tn[t] together (lanes 0 and 1) and broadcast.
 // A slot outside the store (an unclaimed read can see the transient -1 neighbour of
 // a triangle another warp is writing) reads as a dead triangle.
-// Vertex id of the instance whose points are [d.rlo, d.rlo + d.rn) (or the ghost).
-__device__ __forceinline__ bool of_instance(const Dev &d, int id)
+// Vertex id of the warp's current instance (or the ghost).
+__device__ __forceinline__ bool of_instance(const Warp w, int id)
 {
-    return id == KDT_GHOST || (unsigned)(id - d.rlo) < (unsigned)d.rn;
+    return id == KDT_GHOST || (unsigned)(id - w.sh->rlo) < (unsigned)w.sh->rn;
 }
 
-__device__ __forceinline__ void load_tri(const Warp &w, const Dev &d, int t, int4 &v, int4 &nb)
+__device__ __forceinline__ void load_tri(const Warp w, const Dev &d, int t, int4 &v, int4 &nb)
 {
     int4 x = make_int4(0, 0, 0, 0);
     bool in = t >= 0 && t < d.cap;
@@ -163,7 +191,7 @@ __device__ __forceinline__ void load_tri(const Warp &w, const Dev &d, int t, int
 }
 
 // Coordinates of up to 4 vertices (ghost -> (0,0), never used) in one round trip.
-__device__ __forceinline__ void load_xy4(const Warp &w, const Dev &d, int a, int b, int c, int e,
+__device__ __forceinline__ void load_xy4(const Warp w, const Dev &d, int a, int b, int c, int e,
                                          int2 &pa, int2 &pb, int2 &pc, int2 &pe)
 {
     int id = w.lane == 0 ? a : (w.lane == 1 ? b : (w.lane == 2 ? c : (w.lane == 3 ? e : KDT_GHOST)));
@@ -186,21 +214,21 @@ __device__ __forceinline__ void dirty_push(const Dev &d, int t)
     if (pos < d.dirty_cap) d.dirty[pos] = t;
 }
 
-__device__ __forceinline__ void backoff(Warp &w, int attempt)
+__device__ __forceinline__ void backoff(Warp w, int attempt)
 {
     unsigned lim = 32u << (attempt < 7 ? attempt : 7);
-    unsigned ns = 16 + (xorshift(w.rng) % lim);  // every lane advances the same state
+    unsigned ns = 16 + (warp_rand(w) % lim);
     if (w.lane == 0) __nanosleep(ns);
     __syncwarp();
-    w.cnt[C_RETRIES]++;
+    cnt_add(w, C_RETRIES, 1);
 }
 
-__device__ __forceinline__ void flush_counters(const Warp &w, const Dev &d)
+__device__ __forceinline__ void flush_counters(Warp w, const Dev &d)
 {
     if (w.lane == 0 && d.counters) {
         for (int i = 0; i < C_NUM; ++i)
-            if (w.cnt[i]) atomicAdd(d.counters + i, (unsigned long long)w.cnt[i]);
-        if (w.cyc_max) atomicMax(d.counters + C_CYC_MAX, (unsigned long long)w.cyc_max);
+            if (w.sh->cnt[i]) atomicAdd(d.counters + i, (unsigned long long)w.sh->cnt[i]);
+        if (w.sh->cyc_max) atomicMax(d.counters + C_CYC_MAX, (unsigned long long)w.sh->cyc_max);
     }
 }
 
@@ -246,7 +274,7 @@ __device__ __forceinline__ int csr_find(const int *off, int cnt, int x)
 // Try to claim the slots lane j holds in `mine` (j < m).  Returns true when every
 // slot is now owned by this warp.  Newly taken slots are appended to the claim
 // list either way; the caller releases everything on failure.
-__device__ __forceinline__ bool claim_lanes(Warp &w, const Dev &d, int mine, int m)
+__device__ __forceinline__ bool claim_lanes(Warp w, const Dev &d, int mine, int m)
 {
     bool ok = true, added = false;
     if (w.lane < m && mine >= 0) {
@@ -256,18 +284,17 @@ __device__ __forceinline__ bool claim_lanes(Warp &w, const Dev &d, int mine, int
     }
     unsigned am = __ballot_sync(FULL, added);
     unsigned om = __ballot_sync(FULL, ok);
-    if (added) {
-        int pos = w.ncl + __popc(am & ((1u << w.lane) - 1));
-        w.sh->cl[pos] = mine;
-    }
-    w.ncl += __popc(am);
+    int held = w.sh->ncl;
+    if (added) w.sh->cl[held + __popc(am & ((1u << w.lane) - 1))] = mine;
+    __syncwarp();
+    if (w.lane == 0) w.sh->ncl = held + __popc(am);
     __threadfence();
     __syncwarp();
     return om == FULL;
 }
 
 // Claim a list held in shared memory (any length; the caller keeps ncl + m <= MAXC).
-__device__ __forceinline__ bool claim_list(Warp &w, const Dev &d, const int *list, int m)
+__device__ __forceinline__ bool claim_list(Warp w, const Dev &d, const int *list, int m)
 {
     bool all = true;
     for (int base = 0; base < m; base += 32) {
@@ -279,14 +306,14 @@ __device__ __forceinline__ bool claim_list(Warp &w, const Dev &d, const int *lis
     return all;
 }
 
-__device__ __forceinline__ void release_all(Warp &w, const Dev &d)
+__device__ __forceinline__ void release_all(Warp w, const Dev &d)
 {
     __syncwarp();
     if (w.lane == 0) {
         __threadfence();  // our writes are visible before any owner word clears
-        for (int i = 0; i < w.ncl; ++i) atomicExch(&d.tn[w.sh->cl[i]].w, 0);
+        for (int i = 0; i < w.sh->ncl; ++i) atomicExch(&d.tn[w.sh->cl[i]].w, 0);
+        w.sh->ncl = 0;
     }
-    w.ncl = 0;
     __syncwarp();
 }
 
@@ -299,22 +326,33 @@ enum Where : int { W_INSIDE = 0, W_EDGE = 1, W_VERTEX = 2, W_GHOST = 3, W_FAIL =
 // coinciding vertex for W_VERTEX.  Reads are unclaimed; callers re-check after
 // claiming.  A random start edge breaks ties so walks cannot cycle forever in the
 // non-Delaunay states other warps may leave transiently.
-__device__ __noinline__ int walk(Warp &w, const Dev &d, int t, int2 q, int &where, int &e, int &vtx)
+struct WalkResult {
+    int t;      // slot where the walk stopped, -1 when it gave up
+    int where;  // Where
+    int e;      // edge for W_EDGE
+    int vtx;    // coinciding vertex for W_VERTEX
+};
+
+__device__ __noinline__ WalkResult walk(Warp w, const Dev &d, int t, int2 q)
 {
-    where = W_FAIL;
+    WalkResult res;
+    res.t = -1;
+    res.where = W_FAIL;
+    res.e = 0;
+    res.vtx = -1;
     for (int steps = 0; steps < WALK_CAP; ++steps) {
-        w.cnt[C_WALK_STEPS]++;
-        if (t < 0 || t >= d.cap) return -1;
+        cnt_add(w, C_WALK_STEPS, 1);
+        if (t < 0 || t >= d.cap) return res;
         int4 v, nb;
         load_tri(w, d, t, v, nb);
-        if (!(v.w & ALIVE)) return -1;
+        if (!(v.w & ALIVE)) return res;
         // The walk reads without claims: a triangle being written can pair its new
         // vertices with old neighbour words (zero in a fresh slot, i.e. slot 0).  In a
         // batch every instance covers the same coordinate domain, so such a reference
         // can lead into another instance's triangulation, where the geometry alone
         // would accept a location.  A triangle with a vertex outside the instance
         // ends the walk (the caller restarts).
-        if (!of_instance(d, v.x) || !of_instance(d, v.y) || !of_instance(d, v.z)) return -1;
+        if (!of_instance(w, v.x) || !of_instance(w, v.y) || !of_instance(w, v.z)) return res;
         int2 p0, p1, p2, pz;
         load_xy4(w, d, v.x, v.y, v.z, KDT_GHOST, p0, p1, p2, pz);
         int g = v.x == KDT_GHOST ? 0 : (v.y == KDT_GHOST ? 1 : (v.z == KDT_GHOST ? 2 : -1));
@@ -322,14 +360,15 @@ __device__ __noinline__ int walk(Warp &w, const Dev &d, int t, int2 q, int &wher
             int2 pu = g == 0 ? p1 : (g == 1 ? p2 : p0);
             int2 pv = g == 0 ? p2 : (g == 1 ? p0 : p1);
             if (orient2d(pu, pv, q) > 0) {
-                where = W_GHOST;
-                return t;
+                res.where = W_GHOST;
+                res.t = t;
+                return res;
             }
             t = comp(nb, g) >> 2;  // across the finite edge
             continue;
         }
         int o0 = orient2d(p1, p2, q), o1 = orient2d(p2, p0, q), o2 = orient2d(p0, p1, q);
-        unsigned r = xorshift(w.rng) % 3;
+        unsigned r = warp_rand(w) % 3;
         int nxt = -1;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -343,25 +382,26 @@ __device__ __noinline__ int walk(Warp &w, const Dev &d, int t, int2 q, int &wher
         }
         int zeros = (o0 == 0) + (o1 == 0) + (o2 == 0);
         if (zeros == 0) {
-            where = W_INSIDE;
+            res.where = W_INSIDE;
         } else if (zeros == 1) {
-            where = W_EDGE;
-            e = o0 == 0 ? 0 : (o1 == 0 ? 1 : 2);
+            res.where = W_EDGE;
+            res.e = o0 == 0 ? 0 : (o1 == 0 ? 1 : 2);
         } else {
-            where = W_VERTEX;
+            res.where = W_VERTEX;
             // the vertex shared by the two zero edges
-            vtx = o0 != 0 ? v.x : (o1 != 0 ? v.y : v.z);
+            res.vtx = o0 != 0 ? v.x : (o1 != 0 ? v.y : v.z);
         }
-        return t;
+        res.t = t;
+        return res;
     }
-    return -1;
+    return res;
 }
 
 // ------------------------------------------------------------------ writes
 
 // Write the fan of m triangles (q, W[k], W[k+1]) into slots X[k]; O[k] is the
 // outer reference across edge (W[k], W[k+1]).  Used by the 1->3 and 2->4 splits.
-__device__ void write_fan(Warp &w, const Dev &d, int q, const int *W, const int *O, const int *X, int m)
+__device__ void write_fan(Warp w, const Dev &d, int q, const int *W, const int *O, const int *X, int m)
 {
     if (w.lane == 0) {
         for (int k = 0; k < m; ++k) {
@@ -382,7 +422,7 @@ __device__ void write_fan(Warp &w, const Dev &d, int q, const int *W, const int 
 // Flip the edge opposite vertex e of slot T (apex p).  U is the neighbour across it
 // (its apex at index f is d).  Before:  T = (p, a, b),  U = (b, a, d).
 // After:  T = (p, a, d),  U = (p, d, b).  All four outer back-pointers are rewritten.
-__device__ void do_flip(Warp &w, const Dev &d, int T, int e, const int4 &tv_, const int4 &tn_, int U,
+__device__ void do_flip(Warp w, const Dev &d, int T, int e, const int4 &tv_, const int4 &tn_, int U,
                         int f, const int4 &uv, const int4 &un)
 {
     if (w.lane == 0) {
@@ -416,7 +456,7 @@ __device__ void do_flip(Warp &w, const Dev &d, int T, int e, const int4 &tv_, co
 // pushed.  Tests are made on unclaimed reads; only an indicated flip is claimed and
 // re-checked.  An edge that cannot be settled here is left to the certification
 // pass that follows every step, so correctness never depends on this stack.
-__device__ __noinline__ int lawson(Warp &w, const Dev &d, int top, int p, bool insertion_mode)
+__device__ __noinline__ int lawson(Warp w, const Dev &d, int top, int p, bool insertion_mode)
 {
     WarpShared *sh = w.sh;
     int attempts = 0;
@@ -440,15 +480,16 @@ __device__ __noinline__ int lawson(Warp &w, const Dev &d, int top, int p, bool i
         if (comp(uv, (f + 1) % 3) != b || comp(uv, (f + 2) % 3) != a) continue;  // stale read
         int2 pp, pa, pb, pd;
         load_xy4(w, d, apex, a, b, dd, pp, pa, pb, pd);
-        w.cnt[C_FLIP_TESTS]++;
-        int vv[3] = {v.x, v.y, v.z};
-        int2 pv[3];
-        pv[e] = pp;
-        pv[(e + 1) % 3] = pa;
-        pv[(e + 2) % 3] = pb;
-        if (!conflict(vv[0], vv[1], vv[2], pv[0], pv[1], pv[2], dd, pd, d.use_filter,
-                      &w.cnt[C_EXACT], &w.cnt[C_TIES]))
-            continue;
+        cnt_add(w, C_FLIP_TESTS, 1);
+        // coordinates in the triangle's stored rotation (apex at index e)
+        int2 pv0 = e == 0 ? pp : (e == 1 ? pb : pa);
+        int2 pv1 = e == 1 ? pp : (e == 2 ? pb : pa);
+        int2 pv2 = e == 2 ? pp : (e == 0 ? pb : pa);
+        unsigned ex = 0, ti = 0;
+        bool cf = conflict(v.x, v.y, v.z, pv0, pv1, pv2, dd, pd, d.use_filter, &ex, &ti);
+        cnt_add(w, C_EXACT, ex);
+        cnt_add(w, C_TIES, ti);
+        if (!cf) continue;
         // claim the quad and its four outer neighbours, then re-check
         int mine = -1;
         if (w.lane == 0) mine = T;
@@ -467,12 +508,12 @@ __device__ __noinline__ int lawson(Warp &w, const Dev &d, int top, int p, bool i
                  (uv2.w & ALIVE) && un2.x == un.x && un2.y == un.y && un2.z == un.z;
             if (ok) {
                 do_flip(w, d, T, e, v2, nb2, U, f, uv2, un2);
-                w.cnt[insertion_mode ? C_FLIPS : C_FIX_FLIPS]++;
+                cnt_add(w, insertion_mode ? C_FLIPS : C_FIX_FLIPS, 1);
                 release_all(w, d);
                 // push follow-up edges
                 int add = insertion_mode ? 2 : 4;
                 if (top + add > STACK) {
-                    w.cnt[C_STACK_DROP]++;
+                    cnt_add(w, C_STACK_DROP, 1);
                     continue;
                 }
                 if (w.lane == 0) {
@@ -492,7 +533,7 @@ __device__ __noinline__ int lawson(Warp &w, const Dev &d, int top, int p, bool i
         release_all(w, d);
         // contention or a stale read: retry this edge later
         if (++attempts > d.retry_cap) {
-            w.cnt[C_STACK_DROP]++;
+            cnt_add(w, C_STACK_DROP, 1);
             attempts = 0;
             continue;
         }
@@ -514,7 +555,7 @@ __device__ __noinline__ int lawson(Warp &w, const Dev &d, int top, int p, bool i
 // one claimed operation keeps the hull convex whenever nothing is claimed, so no
 // other warp can ever mistake a pocket of a half-repaired hull for the outside.
 // Returns 0 when written, 1 to retry (contention or stale reads), or an error.
-__device__ __noinline__ int insert_outside(Warp &w, const Dev &d, int p, int2 q, int V0, int spare0, int spare1, int &m_out)
+__device__ __noinline__ int insert_outside(Warp w, const Dev &d, int p, int2 q, int V0, int spare0, int spare1, int &m_out)
 {
     WarpShared *sh = w.sh;
     const int KCH = 60;
@@ -634,8 +675,8 @@ __device__ __noinline__ int insert_outside(Warp &w, const Dev &d, int p, int2 q,
     }
     __syncwarp();
     write_fan(w, d, p, W, Ow, Xw, m);
-    w.cnt[C_SPLIT_GHOST]++;
-    w.cnt[C_INSERTS]++;
+    cnt_add(w, C_SPLIT_GHOST, 1);
+    cnt_add(w, C_INSERTS, 1);
     release_all(w, d);
     m_out = m;
     return 0;
@@ -645,7 +686,7 @@ __device__ __noinline__ int insert_outside(Warp &w, const Dev &d, int p, int2 q,
 // spare0 / spare1 are two dead slots owned by the caller (a deletion's leftovers or
 // fresh slots during a build).  Returns 0, 1 = deferred (p lands on a vertex that is
 // still moving in this step), or a DevStatus error.
-__device__ __noinline__ int insert_point(Warp &w, const Dev &d, int p, int2 q, int start, int spare0, int spare1,
+__device__ __noinline__ int insert_point(Warp w, const Dev &d, int p, int2 q, int start, int spare0, int spare1,
                             bool allow_defer)
 {
     WarpShared *sh = w.sh;
@@ -653,15 +694,15 @@ __device__ __noinline__ int insert_point(Warp &w, const Dev &d, int p, int2 q, i
     for (int attempt = 0;; ++attempt) {
         if (attempt > d.retry_cap) return DEV_RETRY;
         if (read_status(d)) return -1;
-        int where, e = 0, vtx = -1;
-        int tt = walk(w, d, t, q, where, e, vtx);
+        WalkResult wr = walk(w, d, t, q);
+        int tt = wr.t, where = wr.where, e = wr.e, vtx = wr.vtx;
         if (tt < 0) {
             if (++walk_fail > WALK_RESTARTS) return DEV_WALK;
             // restart from the hint, then from the triangle of a random present point
             if (attempt & 1) {
                 t = start;
             } else {
-                int r = d.rlo + (int)(xorshift(w.rng) % (unsigned)d.rn);
+                int r = w.sh->rlo + (int)(warp_rand(w) % (unsigned)w.sh->rn);
                 t = __shfl_sync(FULL, __ldcg(d.pt_tri + r), 0);
                 if (t < 0) t = start;
             }
@@ -768,9 +809,9 @@ __device__ __noinline__ int insert_point(Warp &w, const Dev &d, int p, int2 q, i
         m = where == W_EDGE ? 4 : 3;
         __syncwarp();
         write_fan(w, d, p, W, O, X, m);
-        if (where == W_EDGE) w.cnt[C_SPLIT_EDGE]++;
-        if (where == W_GHOST) w.cnt[C_SPLIT_GHOST]++;
-        w.cnt[C_INSERTS]++;
+        if (where == W_EDGE) cnt_add(w, C_SPLIT_EDGE, 1);
+        if (where == W_GHOST) cnt_add(w, C_SPLIT_GHOST, 1);
+        cnt_add(w, C_INSERTS, 1);
         release_all(w, d);
         if (w.lane == 0)
             for (int k = 0; k < m; ++k) sh->stack[k] = make_int2(X[k], 0);
@@ -784,32 +825,110 @@ __device__ __noinline__ int insert_point(Warp &w, const Dev &d, int p, int2 q, i
 
 // Gather the star of p counter-clockwise from pt_tri[p] into S/I/L/ON.  Returns k,
 // or -1 when the reads are inconsistent (another warp is working there), -2 when
-// the degree exceeds KMAX.
-__device__ int gather_star(Warp &w, const Dev &d, int p)
+// the degree exceeds KMAX.  The star is walked in both directions at once (the
+// next triangle counter-clockwise and the next clockwise are loaded in the same
+// round trip), so a star of k triangles costs about k/2 dependent loads.  The
+// clockwise part is kept at the top of the arrays and moved into place at the end.
+__device__ int gather_star(Warp w, const Dev &d, int p)
 {
     WarpShared *sh = w.sh;
     int t0 = __ldcg(d.pt_tri + p);
     t0 = __shfl_sync(FULL, t0, 0);
     if (t0 < 0 || t0 >= d.cap) return -1;
-    int t = t0, k = 0;
+    int nf = 0, nbk = 0;   // entries counter-clockwise after t0, clockwise before it
+    int tf = t0, tb = -1;  // triangles to load this round (-1: none)
     while (true) {
-        int4 v, nb;
-        load_tri(w, d, t, v, nb);
-        if (!(v.w & ALIVE)) return -1;
-        int I = v.x == p ? 0 : (v.y == p ? 1 : (v.z == p ? 2 : -1));
-        if (I < 0) return -1;
-        if (k >= KMAX) return -2;
+        // lanes 0, 1: tf (vertices, neighbours); lanes 2, 3: tb
+        int4 x = make_int4(0, 0, 0, 0);
+        int tl = w.lane < 2 ? tf : (w.lane < 4 ? tb : -1);
+        if (tl >= 0 && tl < d.cap) x = (w.lane & 1) ? __ldcg(d.tn + tl) : __ldcg(d.tv + tl);
+        int4 fv = bcast4(x, 0), fn = bcast4(x, 1), bv = bcast4(x, 2), bn = bcast4(x, 3);
+        // forward triangle (t0 itself in the first round)
+        if (!(fv.w & ALIVE)) return -1;
+        int If = fv.x == p ? 0 : (fv.y == p ? 1 : (fv.z == p ? 2 : -1));
+        if (If < 0) return -1;
+        if (nf + nbk + 1 > KMAX) return -2;
         if (w.lane == 0) {
-            sh->S[k] = t;
-            sh->I[k] = I;
-            sh->L[k] = comp(v, (I + 1) % 3);
-            sh->ON[k] = comp(nb, I);
+            sh->S[nf] = tf;
+            sh->I[nf] = If;
+            sh->L[nf] = comp(fv, (If + 1) % 3);
+            sh->ON[nf] = comp(fn, If);
         }
-        ++k;
-        int nx = comp(nb, (I + 1) % 3) >> 2;
-        if (nx == t0) break;
-        if (nx < 0 || nx >= d.cap) return -1;
-        t = nx;
+        ++nf;
+        int fnext = comp(fn, (If + 1) % 3) >> 2;
+        if (tb < 0) {
+            // first round: t0; its clockwise neighbour starts the other direction
+            int fprev = comp(fn, (If + 2) % 3) >> 2;
+            if (fnext == t0) break;  // a star of one triangle (never valid: rejected by k < 3)
+            if (fnext < 0 || fnext >= d.cap || fprev < 0 || fprev >= d.cap) return -1;
+            if (fnext == fprev) {    // two triangles
+                tf = fnext;
+                tb = -1;
+                // load it as a forward triangle in the next round, then stop
+                int4 y = make_int4(0, 0, 0, 0);
+                if (w.lane < 2) y = (w.lane & 1) ? __ldcg(d.tn + tf) : __ldcg(d.tv + tf);
+                int4 v2 = bcast4(y, 0), n2 = bcast4(y, 1);
+                if (!(v2.w & ALIVE)) return -1;
+                int I2 = v2.x == p ? 0 : (v2.y == p ? 1 : (v2.z == p ? 2 : -1));
+                if (I2 < 0) return -1;
+                if (w.lane == 0) {
+                    sh->S[nf] = tf;
+                    sh->I[nf] = I2;
+                    sh->L[nf] = comp(v2, (I2 + 1) % 3);
+                    sh->ON[nf] = comp(n2, I2);
+                }
+                ++nf;
+                break;
+            }
+            tf = fnext;
+            tb = fprev;
+            continue;
+        }
+        // backward triangle
+        if (tb == tf) break;  // both directions reached the same triangle: stored once
+        if (!(bv.w & ALIVE)) return -1;
+        int Ib = bv.x == p ? 0 : (bv.y == p ? 1 : (bv.z == p ? 2 : -1));
+        if (Ib < 0) return -1;
+        if (nf + nbk + 1 > KMAX) return -2;
+        if (w.lane == 0) {
+            int at = KMAX - 1 - nbk;
+            sh->S[at] = tb;
+            sh->I[at] = Ib;
+            sh->L[at] = comp(bv, (Ib + 1) % 3);
+            sh->ON[at] = comp(bn, Ib);
+        }
+        ++nbk;
+        int bprev = comp(bn, (Ib + 2) % 3) >> 2;
+        if (fnext == tb) break;  // the forward direction continues into the backward part
+        if (bprev == tf) break;  // (the same meeting seen from the other side)
+        if (fnext < 0 || fnext >= d.cap || bprev < 0 || bprev >= d.cap) return -1;
+        if (fnext == bprev) {
+            // one triangle left between them: load it forward in the next round
+            tf = fnext;
+            tb = fnext;
+            continue;
+        }
+        tf = fnext;
+        tb = bprev;
+    }
+    __syncwarp();
+    // move the clockwise part (top of the arrays, last found first) after the rest
+    int k = nf + nbk;
+    int src = KMAX - nbk + w.lane;
+    int cS = 0, cI = 0, cL = 0, cO = 0;
+    bool mv = w.lane < nbk;
+    if (mv) {
+        cS = sh->S[src];
+        cI = sh->I[src];
+        cL = sh->L[src];
+        cO = sh->ON[src];
+    }
+    __syncwarp();
+    if (mv) {
+        sh->S[nf + w.lane] = cS;
+        sh->I[nf + w.lane] = cI;
+        sh->L[nf + w.lane] = cL;
+        sh->ON[nf + w.lane] = cO;
     }
     __syncwarp();
     return k;
@@ -839,11 +958,34 @@ __device__ bool ear_valid(const int *EL, const int2 *EX, int m, int i, const Dev
     return true;
 }
 
+// One test of ear i (L[i], L[i+1], L[i+2]) of the current link polygon of m vertices:
+// t = 0 fails a finite ear that is not counter-clockwise; t >= 1 fails it when
+// vertex i+2+t conflicts with it (the conditions ear_valid checks, one per call).
+__device__ __forceinline__ bool ear_test_fails(const int *EL, const int2 *EX, int m, int i, int t, const Dev &d,
+                                               unsigned *exact_calls, unsigned *ties)
+{
+    int i1 = i + 1 == m ? 0 : i + 1, i2 = i1 + 1 == m ? 0 : i1 + 1;
+    int x = EL[i], y = EL[i1], z = EL[i2];
+    int2 px = EX[i], py = EX[i1], pz = EX[i2];
+    int g = x == KDT_GHOST ? 0 : (y == KDT_GHOST ? 1 : (z == KDT_GHOST ? 2 : -1));
+    if (t == 0) return g < 0 && orient2d(px, py, pz) <= 0;
+    int j = i + 2 + t;
+    if (j >= m) j -= m;
+    int wv = EL[j];
+    if (wv == KDT_GHOST) return false;
+    if (g >= 0) {
+        int2 gu = g == 0 ? py : (g == 1 ? pz : px);
+        int2 gv = g == 0 ? pz : (g == 1 ? px : py);
+        return ghost_conflict(gu, gv, EX[j]);
+    }
+    return incircle_sos(x, y, z, wv, px, py, pz, EX[j], d.use_filter, exact_calls, ties) > 0;
+}
+
 // Delete p: claim its star and the ring of outer neighbours, re-triangulate the
 // star-shaped hole by Delaunay ears (the simple deletion the paper prefers, Section
 // IV), release.  On success the two slots the hole no longer needs are returned
 // dead in spare0/spare1 and `hint` is a new triangle next to p's old position.
-__device__ __noinline__ int delete_point(Warp &w, const Dev &d, int p, int &spare0, int &spare1, int &hint)
+__device__ __noinline__ int delete_point(Warp w, const Dev &d, int p, int &spare0, int &spare1, int &hint)
 {
     WarpShared *sh = w.sh;
     for (int attempt = 0;; ++attempt) {
@@ -921,8 +1063,8 @@ __device__ __noinline__ int delete_point(Warp &w, const Dev &d, int p, int &spar
                 unsigned bm = __ballot_sync(FULL, v);
                 if (bm) chosen = base + __ffs(bm) - 1;
             }
-            w.cnt[C_EXACT] += __reduce_add_sync(FULL, ex);
-            w.cnt[C_TIES] += __reduce_add_sync(FULL, ti);
+            cnt_add(w, C_EXACT, __reduce_add_sync(FULL, ex));
+            cnt_add(w, C_TIES, __reduce_add_sync(FULL, ti));
             if (chosen < 0) {
                 // cannot happen for a valid star; leave the store to the fallback
                 release_all(w, d);
@@ -996,8 +1138,8 @@ __device__ __noinline__ int delete_point(Warp &w, const Dev &d, int p, int &spar
             d.tv[spare1].w = 0;
             d.pt_tri[p] = -1;
         }
-        w.cnt[C_DEG_DEL] += k;
-        w.cnt[C_DELETES]++;
+        cnt_add(w, C_DEG_DEL, k);
+        cnt_add(w, C_DELETES, 1);
         release_all(w, d);
         return DEV_OK;
     }

@@ -32,20 +32,40 @@ struct Inst {
     int ninst;
 };
 
-__device__ __forceinline__ Warp make_warp(WarpShared *sh, int token, unsigned seed)
+// The warp's handle and its shared state (counters zero, claims none, random state
+// from `seed`, instance = the points [d.rlo, d.rlo + d.rn)).
+static_assert(C_NUM <= 32, "one lane clears each counter");
+
+__device__ __forceinline__ Warp make_warp(WarpShared *sh, int token, unsigned seed, const Dev &d)
 {
     Warp w;
     w.sh = sh;
     w.lane = threadIdx.x & 31;
     w.token = token;
-    w.ncl = 0;
-    w.rng = seed * 2654435761u + 0x9E3779B9u;
-    if (w.rng == 0) w.rng = 1;
-#pragma unroll
-    for (int i = 0; i < C_NUM; ++i) w.cnt[i] = 0;
-    w.cyc_max = 0;
+    if (w.lane < C_NUM) sh->cnt[w.lane] = 0;
+    if (w.lane == 0) {
+        unsigned r = seed * 2654435761u + 0x9E3779B9u;
+        sh->rng = r ? r : 1u;
+        sh->ncl = 0;
+        sh->cyc_max = 0;
+        sh->rlo = d.rlo;
+        sh->rn = d.rn;
+    }
+    __syncwarp();
     return w;
 }
+
+// One copy of the launch's Dev per block in shared memory: device functions take it
+// by reference, which a kernel parameter cannot give without a per-thread copy in
+// local memory.
+#define KD_BLOCK_DEV(param)                                           \
+    __shared__ Dev kd_block_dev;                                      \
+    if (threadIdx.x == 0) {                                           \
+        kd_block_dev = (param);                                       \
+        if ((param).ctl) kd_block_dev.stamp = __ldcg((param).ctl + 1); \
+    }                                                                 \
+    __syncthreads();                                                  \
+    const Dev &d = kd_block_dev
 
 // ------------------------------------------------------------------ scan
 
@@ -199,19 +219,19 @@ __global__ void k_intake_link(Dev d, const int3 *moves, int m, Inst I, int bits,
 // message.  A point whose target is still occupied by a point that has not moved
 // yet is deferred.  The last warp to finish inserts the deferred points and
 // certifies the triangles written on the global-memory path.
-__device__ void step_tail(Warp &w, Dev d, Inst I, const int4 *deferred, const int *defer_count, int defer_cap,
+__device__ void step_tail(Warp w, const Dev &d, Inst I, const int4 *deferred, const int *defer_count, int defer_cap,
                           int *viol, int viol_cap);
 
-__global__ void __launch_bounds__(WPB * 32, 8) k_kinetic(Dev d, const int3 *moves, const int *head, const int *next,
+__global__ void __launch_bounds__(WPB * 32, 7) k_kinetic(Dev dp, const int3 *moves, const int *head, const int *next,
                                                          Inst I, int ncells, int wpp, int4 *deferred,
                                                          int *defer_count, int defer_cap, int *viol, int viol_cap)
 {
-    if (d.ctl) d.stamp = __ldcg(d.ctl + 1);
+    KD_BLOCK_DEV(dp);
     __shared__ WarpShared shs[WPB];
     int wib = threadIdx.x >> 5;
     int gw = blockIdx.x * (blockDim.x >> 5) + wib;
     int nw = gridDim.x * (blockDim.x >> 5);
-    Warp w = make_warp(&shs[wib], gw + 1, gw + 17 * d.stamp);
+    Warp w = make_warp(&shs[wib], gw + 1, gw + 17 * d.stamp, d);
     const int items = ncells * wpp;
     while (true) {
         // persistent warps pull (partition, share) work items from a ticket
@@ -221,8 +241,7 @@ __global__ void __launch_bounds__(WPB * 32, 8) k_kinetic(Dev d, const int3 *move
         if (t >= items) break;
         int c = t / wpp, sub = t - c * wpp;
         int inst = I.ninst > 1 ? csr_find(I.cofs, I.ninst + 1, c) : 0;
-        d.rlo = I.pofs[inst];
-        d.rn = I.pofs[inst + 1] - d.rlo;
+        set_instance(w, I.pofs[inst], I.pofs[inst + 1] - I.pofs[inst]);
         int i = __shfl_sync(FULL, __ldcg(head + c), 0);
         int k = -1;
         while (i >= 0) {
@@ -239,7 +258,7 @@ __global__ void __launch_bounds__(WPB * 32, 8) k_kinetic(Dev d, const int3 *move
             // Delete + Update + Insert of Fig. 4 as one staged operation
             int rc = move_point(w, d, p, q, s0, s1, hint);
             if (rc == MV_GLOBAL) {
-                w.cnt[C_MV_GLOBAL]++;
+                cnt_add(w, C_MV_GLOBAL, 1);
                 if (w.lane == 0) {
                     d.xy[p] = q;
                     __threadfence();
@@ -249,8 +268,8 @@ __global__ void __launch_bounds__(WPB * 32, 8) k_kinetic(Dev d, const int3 *move
             }
             {
                 unsigned cy = (unsigned)((clock64() - c0) >> 6);
-                w.cnt[C_CYC_MOVE] += cy;
-                w.cyc_max = cy > w.cyc_max ? cy : w.cyc_max;
+                cnt_add(w, C_CYC_MOVE, cy);
+                if (w.lane == 0 && cy > w.sh->cyc_max) w.sh->cyc_max = cy;
             }
             if (rc == MV_DEFER || rc == 1) {
                 if (w.lane == 0) {
@@ -258,7 +277,7 @@ __global__ void __launch_bounds__(WPB * 32, 8) k_kinetic(Dev d, const int3 *move
                     if (pos < defer_cap) deferred[pos] = make_int4(p, s0, s1, hint);
                     else atomicCAS(d.status, 0, DEV_CAPACITY);
                 }
-                w.cnt[C_DEFERRED]++;
+                cnt_add(w, C_DEFERRED, 1);
                 __syncwarp();
             } else if (rc) {
                 if (rc > 0 && w.lane == 0 && atomicCAS(d.status, 0, rc) == 0) d.status[S_FAILPT] = p;
@@ -346,7 +365,7 @@ __device__ void certify_one(const Dev &d, int t, int *viol, int *viol_count, int
 // Tail of a step (one warp, after every other warp finished): insert the deferred
 // points, then certify the triangles written on the global-memory path (the staged
 // path certified its own).  A long dirty list is left to the host.
-__device__ void step_tail(Warp &w, Dev d, Inst I, const int4 *deferred, const int *defer_count, int defer_cap,
+__device__ void step_tail(Warp w, const Dev &d, Inst I, const int4 *deferred, const int *defer_count, int defer_cap,
                           int *viol, int viol_cap)
 {
     if (read_status(d)) return;
@@ -358,8 +377,7 @@ __device__ void step_tail(Warp &w, Dev d, Inst I, const int4 *deferred, const in
         int2 q = __ldcg(d.xy + e.x);
         q = bcast2(q, 0);
         int inst = I.ninst > 1 ? csr_find(I.pofs, I.ninst + 1, e.x) : 0;
-        d.rlo = I.pofs[inst];
-        d.rn = I.pofs[inst + 1] - d.rlo;
+        set_instance(w, I.pofs[inst], I.pofs[inst + 1] - I.pofs[inst]);
         int rc = insert_point(w, d, e.x, q, e.w, e.y, e.z, false);
         if (rc) {
             if (rc > 0) set_status(d, rc);
@@ -403,13 +421,14 @@ __global__ void k_certify_all(Dev d, int s0, int nslots, int *viol, int *viol_co
 
 // Lawson repair of the edges the certification rejected (general flip algorithm:
 // every flip queues the four outer edges of its quadrilateral).
-__global__ void __launch_bounds__(WPB * 32) k_fixup(Dev d, const int *viol, int nviol)
+__global__ void __launch_bounds__(WPB * 32) k_fixup(Dev dp, const int *viol, int nviol)
 {
+    KD_BLOCK_DEV(dp);
     __shared__ WarpShared shs[WPB];
     int wib = threadIdx.x >> 5;
     int gw = blockIdx.x * (blockDim.x >> 5) + wib;
     int nw = gridDim.x * (blockDim.x >> 5);
-    Warp w = make_warp(&shs[wib], gw + 1, gw + 31 * d.stamp + 5);
+    Warp w = make_warp(&shs[wib], gw + 1, gw + 31 * d.stamp + 5, d);
     for (int j = gw; j < nviol; j += nw) {
         if (read_status(d)) break;
         int r = viol[j];
@@ -526,14 +545,15 @@ __global__ void k_init(Dev d, const int *order, const int *third, int *tri_count
 
 // Insert the points at sorted positions (2j+1) * 2^level, each starting its walk at
 // the triangle of its Hilbert predecessor (2j) * 2^level, already inserted.
-__global__ void __launch_bounds__(WPB * 32) k_insert_level(Dev d, const int *order, int level, int items,
+__global__ void __launch_bounds__(WPB * 32) k_insert_level(Dev dp, const int *order, int level, int items,
                                                            int *tri_count, int nloc, int slot_end)
 {
+    KD_BLOCK_DEV(dp);
     __shared__ WarpShared shs[WPB];
     int wib = threadIdx.x >> 5;
     int gw = blockIdx.x * (blockDim.x >> 5) + wib;
     int nw = gridDim.x * (blockDim.x >> 5);
-    Warp w = make_warp(&shs[wib], gw + 1, gw * 7 + level * 1315423911u);
+    Warp w = make_warp(&shs[wib], gw + 1, gw * 7 + level * 1315423911u, d);
     for (int j = gw; j < items; j += nw) {
         if (read_status(d)) break;
         long long i = ((long long)(2 * j + 1)) << level;

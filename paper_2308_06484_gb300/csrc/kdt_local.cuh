@@ -6,12 +6,15 @@
 // around it in one batch, copies them into the warp's shared memory (vertices,
 // neighbours as global refs and as staged indices, and the coordinates of every
 // vertex, so no lookup is needed later), and there
-//   1. deletes p by Delaunay ears (the simple deletion Section IV prefers),
-//   2. locates q among the staged triangles,
-//   3. splits the containing triangle (1->3, or 2->4 when q is on an edge),
-//   4. runs the Lawson flips of the edges opposite q with the flip stack in shared
-//      memory, claiming and staging further triangles only when a flip reaches
-//      outside the region,
+//   1. deletes p by Delaunay ears (the simple deletion Section IV prefers): every
+//      (ear, vertex) test of a round runs on its own lane, and all valid ears no two
+//      of which are neighbours are clipped in the same round,
+//   2. locates q among the staged triangles (one triangle per lane),
+//   3. inserts q by Bowyer-Watson (the insertion Section IV names): the conflict
+//      test of every staged triangle on its own lane gives the cavity, which is
+//      grown past the region (claiming and staging) only when it reaches its edge;
+//      q is joined to the cavity boundary in the cavity's entries and two spares,
+//   4. certifies every edge of every new triangle against its staged neighbour,
 // then writes every modified triangle back and releases the claims.  Global memory
 // sees one claim batch, one validation pass and one write-back instead of a round
 // trip per ear and per flip.  When q is not inside the staged region (a long move,
@@ -32,6 +35,7 @@ enum MoveResult : int { MV_DONE = 0, MV_DEFER = 1, MV_GLOBAL = 2, MV_ABORT = -1 
 struct Region {
     int cnt;                   // staged triangles
     unsigned long long dirty;  // modified staged triangles
+    unsigned long long vchg;   // staged triangles whose vertices changed
 };
 
 __device__ __forceinline__ int local_find(const WarpShared *sh, int cnt, int slot)
@@ -66,12 +70,13 @@ __device__ __forceinline__ int gref_of(const WarpShared *sh, int lref)
 // Claim and stage one more triangle, read under the claim (so no validation is
 // needed), with its vertex coordinates and its links to the staged triangles.
 // Returns its staged index, or -1 when the claim fails or space runs out.
-__device__ __noinline__ int ensure_local(Warp &w, const Dev &d, Region &R, int slot)
+// (`cnt` staged so far; a new entry gets index cnt, and the caller counts it)
+__device__ __noinline__ int ensure_local(Warp w, const Dev &d, int cnt, int slot)
 {
     WarpShared *sh = w.sh;
-    int j = local_find(sh, R.cnt, slot);
+    int j = local_find(sh, cnt, slot);
     if (j >= 0) return j;
-    if (R.cnt >= LM || w.ncl >= MAXC || slot < 0 || slot >= d.cap) return -1;
+    if (cnt >= LM || w.sh->ncl >= MAXC || slot < 0 || slot >= d.cap) return -1;
     int mine = w.lane == 0 ? slot : -1;
     if (!claim_lanes(w, d, mine, 1)) return -1;
     int4 v, nb;
@@ -79,7 +84,7 @@ __device__ __noinline__ int ensure_local(Warp &w, const Dev &d, Region &R, int s
     if (!(v.w & ALIVE)) return -1;
     int2 p0, p1, p2, pz;
     load_xy4(w, d, v.x, v.y, v.z, KDT_GHOST, p0, p1, p2, pz);
-    j = R.cnt++;
+    j = cnt++;
     sh->lslot[j] = slot;
     sh->lv[j] = v;
     sh->ln[j] = nb;
@@ -88,7 +93,7 @@ __device__ __noinline__ int ensure_local(Warp &w, const Dev &d, Region &R, int s
     sh->lp[j][2] = p2;
     for (int e = 0; e < 3; ++e) {
         int r = ic(nb, e);
-        int k = local_find(sh, R.cnt, r >> 2);
+        int k = local_find(sh, cnt, r >> 2);
         reinterpret_cast<int *>(&sh->lnl[j])[e] = k;
         if (k >= 0) reinterpret_cast<int *>(&sh->lnl[k])[r & 3] = j;
     }
@@ -97,16 +102,56 @@ __device__ __noinline__ int ensure_local(Warp &w, const Dev &d, Region &R, int s
 }
 
 // make sure the neighbour of staged j across edge e is staged; its staged index or -1
-__device__ __forceinline__ int nb_staged(Warp &w, const Dev &d, Region &R, int j, int e)
+__device__ __forceinline__ int nb_staged(Warp w, const Dev &d, Region &R, int j, int e)
 {
     int k = ic(w.sh->lnl[j], e);
     if (k >= 0) return k;
-    return ensure_local(w, d, R, ic(w.sh->ln[j], e) >> 2);
+    k = ensure_local(w, d, R.cnt, ic(w.sh->ln[j], e) >> 2);
+    if (k == R.cnt) ++R.cnt;
+    return k;
+}
+
+// Certify the finished region before it is written: every edge of a triangle whose
+// vertices changed, tested against the staged triangle across it (all of them are
+// staged and were claimed while they were read and modified).  Triangles whose
+// vertices did not change only got new neighbour references: their edges keep the
+// state they had.  An edge whose far side is not staged is left to the step's
+// certification of the dirty list.  Returns true when every edge could be tested
+// here (violations go to the violation list for the host's repair pass).
+__device__ __forceinline__ bool certify_staged(Warp w, const Dev &d, const Region &R)
+{
+    WarpShared *sh = w.sh;
+    unsigned ex = 0, ti = 0;
+    bool far = false;
+    for (int idx = w.lane; idx < 3 * R.cnt; idx += 32) {
+        int j = idx / 3, e = idx - 3 * j;
+        if (!((R.vchg >> j) & 1ull)) continue;
+        int4 v = sh->lv[j];
+        if (!(v.w & ALIVE)) continue;
+        int k = ic(sh->lnl[j], e);
+        if (k < 0) {
+            far = true;
+            continue;
+        }
+        // test each shared edge once: from the lower staged index when both changed
+        if (((R.vchg >> k) & 1ull) && k < j) continue;
+        int f = ic(sh->ln[j], e) & 3;
+        int dd = ic(sh->lv[k], f);
+        if (conflict(v.x, v.y, v.z, sh->lp[j][0], sh->lp[j][1], sh->lp[j][2], dd, sh->lp[k][f], d.use_filter,
+                     &ex, &ti)) {
+            int pos = atomicAdd(d.viol_count, 1);
+            if (pos < d.viol_cap) d.viol[pos] = (sh->lslot[j] << 2) | e;
+        }
+    }
+    cnt_add(w, C_EXACT, __reduce_add_sync(FULL, ex));
+    cnt_add(w, C_TIES, __reduce_add_sync(FULL, ti));
+    return !__any_sync(FULL, far);
 }
 
 // Write every modified staged triangle back (lane-parallel), update pt_tri of their
-// vertices, release all claims, then certify the written triangles.
-__device__ void write_back(Warp &w, const Dev &d, Region &R)
+// vertices, release all claims, then (unless the caller certified the region on its
+// staged copy) certify the written triangles against global memory.
+__device__ void write_back(Warp w, const Dev &d, Region R, bool certified = false)
 {
     WarpShared *sh = w.sh;
     __syncwarp();
@@ -128,8 +173,8 @@ __device__ void write_back(Warp &w, const Dev &d, Region &R)
     }
     __syncwarp();
     __threadfence();
-    R.dirty = 0;
     release_all(w, d);
+    if (certified) return;
     // certify what was written: an edge whose far side changes later is certified
     // again by the operation that changes it, so the last writer of every edge checks
     // it against final data.  A transiently inconsistent read goes to the dirty list,
@@ -176,107 +221,11 @@ __device__ __forceinline__ int locate_in(const WarpShared *sh, int j, int2 q, in
     return 2;
 }
 
-// Staged fan around q: triangles (q, W[k], W[k+1]) into staged entries X[k]; OL[k] is
-// the staged ref (index << 2 | edge) of the outer neighbour across (W[k], W[k+1]).
-__device__ void local_fan(WarpShared *sh, Region &R, int q, int2 pq, const int *W, const int2 *WX,
-                          const int *OL, const int *X, int m)
-{
-    for (int k = 0; k < m; ++k) {
-        int kn = k + 1 == m ? 0 : k + 1, kp = k == 0 ? m - 1 : k - 1;
-        int x = X[k], o = OL[k];
-        sh->lv[x] = make_int4(q, W[k], W[kn], ALIVE);
-        sh->lp[x][0] = pq;
-        sh->lp[x][1] = WX[k];
-        sh->lp[x][2] = WX[kn];
-        set_nb(sh, x, 0, o >> 2, gref_of(sh, o));
-        set_nb(sh, x, 1, X[kn], (sh->lslot[X[kn]] << 2) | 2);
-        set_nb(sh, x, 2, X[kp], (sh->lslot[X[kp]] << 2) | 1);
-        set_nb(sh, o >> 2, o & 3, x, (sh->lslot[x] << 2) | 0);
-        R.dirty |= (1ull << x) | (1ull << (o >> 2));
-    }
-}
-
-// Lawson flips of the edges opposite p on the staged region (stack entries: staged
-// index, edge).  Triangles a flip needs beyond the region are claimed and staged; if
-// that fails, the remaining stack is handed back with *top_out > 0.
-__device__ void local_lawson(Warp &w, const Dev &d, Region &R, int p, int top, int *top_out)
-{
-    WarpShared *sh = w.sh;
-    while (top > 0) {
-        int2 ent = sh->stack[top - 1];
-        --top;
-        int T = ent.x, e = ent.y;
-        int4 v = sh->lv[T];
-        if (!(v.w & ALIVE) || ic(v, e) != p) continue;
-        int U = nb_staged(w, d, R, T, e);
-        if (U < 0) {
-            __syncwarp();
-            sh->stack[top] = ent;
-            *top_out = top + 1;
-            return;
-        }
-        int f = ic(sh->ln[T], e) & 3;
-        int4 uv = sh->lv[U];
-        int e1 = e == 2 ? 0 : e + 1, e2 = e == 0 ? 2 : e - 1;
-        int f1 = f == 2 ? 0 : f + 1, f2 = f == 0 ? 2 : f - 1;
-        int a = ic(v, e1), b = ic(v, e2), dd = ic(uv, f);
-        int2 pp = sh->lp[T][e], pa = sh->lp[T][e1], pb = sh->lp[T][e2], pd = sh->lp[U][f];
-        w.cnt[C_FLIP_TESTS]++;
-        // the test is on the triangle in its stored rotation
-        int2 q0 = sh->lp[T][0], q1 = sh->lp[T][1], q2 = sh->lp[T][2];
-        if (!conflict(v.x, v.y, v.z, q0, q1, q2, dd, pd, d.use_filter, &w.cnt[C_EXACT], &w.cnt[C_TIES]))
-            continue;
-        // the four outer neighbours get new back-pointers: stage them
-        int Ta = nb_staged(w, d, R, T, e1), Tb = nb_staged(w, d, R, T, e2);
-        int Ub = Ta >= 0 && Tb >= 0 ? nb_staged(w, d, R, U, f1) : -1;
-        int Ua = Ub >= 0 ? nb_staged(w, d, R, U, f2) : -1;
-        if (Ua < 0) {
-            __syncwarp();
-            sh->stack[top] = ent;
-            *top_out = top + 1;
-            return;
-        }
-        int ga = ic(sh->ln[T], e1), gb = ic(sh->ln[T], e2);    // nt_a, nt_b
-        int hb = ic(sh->ln[U], f1), ha = ic(sh->ln[U], f2);    // nu_b, nu_a
-        int sT = sh->lslot[T], sU = sh->lslot[U];
-        __syncwarp();  // every lane has read T, U and the entry before any lane writes
-        // T = (p, a, d), U = (p, d, b)
-        sh->lv[T] = make_int4(p, a, dd, ALIVE);
-        sh->lp[T][0] = pp;
-        sh->lp[T][1] = pa;
-        sh->lp[T][2] = pd;
-        sh->lv[U] = make_int4(p, dd, b, ALIVE);
-        sh->lp[U][0] = pp;
-        sh->lp[U][1] = pd;
-        sh->lp[U][2] = pb;
-        set_nb(sh, T, 0, Ub, hb);
-        set_nb(sh, T, 1, U, (sU << 2) | 2);
-        set_nb(sh, T, 2, Tb, gb);
-        set_nb(sh, U, 0, Ua, ha);
-        set_nb(sh, U, 1, Ta, ga);
-        set_nb(sh, U, 2, T, (sT << 2) | 1);
-        set_nb(sh, Ub, hb & 3, T, (sT << 2) | 0);
-        set_nb(sh, Tb, gb & 3, T, (sT << 2) | 2);
-        set_nb(sh, Ua, ha & 3, U, (sU << 2) | 0);
-        set_nb(sh, Ta, ga & 3, U, (sU << 2) | 1);
-        R.dirty |= (1ull << T) | (1ull << U) | (1ull << Ta) | (1ull << Tb) | (1ull << Ua) | (1ull << Ub);
-        w.cnt[C_FLIPS]++;
-        if (top + 2 > STACK) {
-            w.cnt[C_STACK_DROP]++;
-            continue;
-        }
-        sh->stack[top] = make_int2(T, 0);
-        sh->stack[top + 1] = make_int2(U, 0);
-        top += 2;
-    }
-    *top_out = 0;
-}
-
 // Move p to q: delete p and insert it at q in one claimed region.  On MV_GLOBAL the
 // deletion is written back and the caller inserts p at q with insert_point starting
 // at `hint` with the spares (s0, s1); on MV_DEFER likewise but q is still occupied by
 // a point that moves later in this step.
-__device__ int move_point(Warp &w, const Dev &d, int p, int2 q, int &s0, int &s1, int &hint)
+__device__ int move_point(Warp w, const Dev &d, int p, int2 q, int &s0, int &s1, int &hint)
 {
     WarpShared *sh = w.sh;
     for (int attempt = 0;; ++attempt) {
@@ -285,7 +234,7 @@ __device__ int move_point(Warp &w, const Dev &d, int p, int2 q, int &s0, int &s1
         long long t0 = clock64();
         int k = gather_star(w, d, p);
         long long t1 = clock64();
-        w.cnt[C_CYC_GATHER] += (unsigned)((t1 - t0) >> 6);
+        cnt_add(w, C_CYC_GATHER, (unsigned)((t1 - t0) >> 6));
         if (k == -2 && attempt == d.retry_cap) return DEV_DEGREE;
         if (k < 3 || 2 * k + 8 > LM) {
             if (k >= 3) {
@@ -300,6 +249,7 @@ __device__ int move_point(Warp &w, const Dev &d, int p, int2 q, int &s0, int &s1
         Region R;
         R.cnt = 2 * k;
         R.dirty = 0;
+        R.vchg = 0;
         for (int i = w.lane; i < 2 * k; i += 32) {
             int slot = i < k ? sh->S[i] : (sh->ON[i - k] >> 2);
             sh->lslot[i] = slot;
@@ -335,7 +285,7 @@ __device__ int move_point(Warp &w, const Dev &d, int p, int2 q, int &s0, int &s1
             continue;
         }
         long long t2 = clock64();
-        w.cnt[C_CYC_CLAIM] += (unsigned)((t2 - t1) >> 6);
+        cnt_add(w, C_CYC_CLAIM, (unsigned)((t2 - t1) >> 6));
         // a ring triangle adjacent to two link edges is staged once: later copies get
         // an unused negative slot id so that lookups find the first one
         for (int i = w.lane; i < k; i += 32) {
@@ -387,72 +337,115 @@ __device__ int move_point(Warp &w, const Dev &d, int p, int2 q, int &s0, int &s1
             }
         }
         // ---- 1. delete p: Delaunay ears over the link, into the star's staged entries
+        long long te0 = clock64();
         int m = k, newc = 0;
         while (m > 3) {
-            int chosen = -1;
+            // Every (ear i, test t) pair on its own lane: t = 0 is the ear's orientation,
+            // t >= 1 the conflict of vertex i+2+t with the ear (SoS incircle, or the
+            // ghost rule for an ear through infinity).
+            const unsigned allm = m == 32 ? FULL : ((1u << m) - 1u);
+            if (w.lane == 0) sh->earbad = 0u;
+            __syncwarp();
             unsigned ex = 0, ti = 0;
-            for (int base = 0; base < m && chosen < 0; base += 32) {
-                int i = base + w.lane;
-                bool v = i < m && ear_valid(sh->L, sh->LX, m, i, d, &ex, &ti);
-                unsigned bm = __ballot_sync(FULL, v);
-                if (bm) chosen = base + __ffs(bm) - 1;
+            const int npair = m * (m - 2);
+            for (int base = 0; base < npair; base += 32) {
+                int idx = base + w.lane;
+                if (idx < npair) {
+                    int i = idx / (m - 2), t = idx - i * (m - 2);
+                    if (ear_test_fails(sh->L, sh->LX, m, i, t, d, &ex, &ti)) atomicOr(&sh->earbad, 1u << i);
+                }
             }
-            w.cnt[C_EXACT] += __reduce_add_sync(FULL, ex);
-            w.cnt[C_TIES] += __reduce_add_sync(FULL, ti);
-            if (chosen < 0) {
+            __syncwarp();
+            unsigned good = ~sh->earbad & allm;
+            cnt_add(w, C_EXACT, __reduce_add_sync(FULL, ex));
+            cnt_add(w, C_TIES, __reduce_add_sync(FULL, ti));
+            if (!good) {
                 release_all(w, d);
                 return DEV_INTERNAL;
             }
-            int i = chosen, i1 = i + 1 == m ? 0 : i + 1, i2 = i1 + 1 == m ? 0 : i1 + 1;
-            int X = newc++;  // staged index == star position
-            int eo_i = sh->EO[i], eo_i1 = sh->EO[i1];
-            int Li = sh->L[i], Li1 = sh->L[i1], Li2 = sh->L[i2];
-            int2 Xi = sh->LX[i], Xi1 = sh->LX[i1], Xi2 = sh->LX[i2];
-            int sX = sh->lslot[X];
-            __syncwarp();  // every lane has read before any lane writes
-            sh->lv[X] = make_int4(Li, Li1, Li2, ALIVE);
-            sh->lp[X][0] = Xi;
-            sh->lp[X][1] = Xi1;
-            sh->lp[X][2] = Xi2;
-            set_nb(sh, X, 0, eo_i1 >> 2, gref_of(sh, eo_i1));
-            set_nb(sh, X, 1, -1, -1);  // the new diagonal: set when it is consumed
-            set_nb(sh, X, 2, eo_i >> 2, gref_of(sh, eo_i));
-            set_nb(sh, eo_i1 >> 2, eo_i1 & 3, X, (sX << 2) | 0);
-            set_nb(sh, eo_i >> 2, eo_i & 3, X, (sX << 2) | 2);
-            R.dirty |= (1ull << X) | (1ull << (eo_i >> 2)) | (1ull << (eo_i1 >> 2));
-            sh->EO[i] = (X << 2) | 1;
+            // Clip every valid ear no neighbour of which is clipped too (each valid ear is
+            // a triangle of the hole's unique triangulation), keeping 3 vertices or more.
+            unsigned sel = 0;
+            int ns = 0;
+            for (int i = 0; i < m && ns < m - 3; ++i) {
+                if (!((good >> i) & 1u)) continue;
+                int ip = i == 0 ? m - 1 : i - 1;
+                if ((sel >> ip) & 1u) continue;
+                if (i == m - 1 && (sel & 1u)) continue;
+                sel |= 1u << i;
+                ++ns;
+            }
+            // lane r builds the r-th clipped ear into staged entry newc + r
+            unsigned long long dmask = 0, vmask = 0;
+            {
+                int r = w.lane, i = -1;
+                int X = newc + r, eo_i = 0, eo_i1 = 0, Li = 0, Li1 = 0, Li2 = 0, sX = 0;
+                int2 Xi = make_int2(0, 0), Xi1 = Xi, Xi2 = Xi;
+                if (r < ns) {
+                    i = (int)__fns(sel, 0, r + 1);
+                    int i1 = i + 1 == m ? 0 : i + 1, i2 = i1 + 1 == m ? 0 : i1 + 1;
+                    eo_i = sh->EO[i];
+                    eo_i1 = sh->EO[i1];
+                    Li = sh->L[i];
+                    Li1 = sh->L[i1];
+                    Li2 = sh->L[i2];
+                    Xi = sh->LX[i];
+                    Xi1 = sh->LX[i1];
+                    Xi2 = sh->LX[i2];
+                    sX = sh->lslot[X];
+                }
+                __syncwarp();  // every lane has read before any lane writes
+                if (r < ns) {
+                    sh->lv[X] = make_int4(Li, Li1, Li2, ALIVE);
+                    sh->lp[X][0] = Xi;
+                    sh->lp[X][1] = Xi1;
+                    sh->lp[X][2] = Xi2;
+                    set_nb(sh, X, 0, eo_i1 >> 2, gref_of(sh, eo_i1));
+                    set_nb(sh, X, 1, -1, -1);  // the new diagonal: set when it is consumed
+                    set_nb(sh, X, 2, eo_i >> 2, gref_of(sh, eo_i));
+                    set_nb(sh, eo_i1 >> 2, eo_i1 & 3, X, (sX << 2) | 0);
+                    set_nb(sh, eo_i >> 2, eo_i & 3, X, (sX << 2) | 2);
+                    sh->EO[i] = (X << 2) | 1;
+                    dmask = (1ull << X) | (1ull << (eo_i >> 2)) | (1ull << (eo_i1 >> 2));
+                    vmask = 1ull << X;
+                }
+            }
+            dmask |= __shfl_xor_sync(FULL, dmask, 16);
+            dmask |= __shfl_xor_sync(FULL, dmask, 8);
+            dmask |= __shfl_xor_sync(FULL, dmask, 4);
+            dmask |= __shfl_xor_sync(FULL, dmask, 2);
+            dmask |= __shfl_xor_sync(FULL, dmask, 1);
+            vmask |= __shfl_xor_sync(FULL, vmask, 16);
+            vmask |= __shfl_xor_sync(FULL, vmask, 8);
+            vmask |= __shfl_xor_sync(FULL, vmask, 4);
+            vmask |= __shfl_xor_sync(FULL, vmask, 2);
+            vmask |= __shfl_xor_sync(FULL, vmask, 1);
+            R.dirty |= dmask;
+            R.vchg |= vmask;
             __syncwarp();
-            // remove element i1 (shift the tail down by one)
-            int lv = 0, eov = 0;
-            int2 xv = make_int2(0, 0);
-            int j = w.lane;
-            bool mv = j >= i1 && j < m - 1;
-            if (mv) {
-                lv = sh->L[j + 1];
-                eov = sh->EO[j + 1];
-                xv = sh->LX[j + 1];
+            // drop the clipped ears' middle vertices from the link
+            {
+                unsigned removed = ((sel << 1) | (sel >> (m - 1))) & allm;
+                int j = w.lane;
+                bool keep = j < m && !((removed >> j) & 1u);
+                int nj = j - __popc(removed & ((1u << j) - 1u));
+                int lv = 0, eov = 0;
+                int2 xv = make_int2(0, 0);
+                if (keep) {
+                    lv = sh->L[j];
+                    eov = sh->EO[j];
+                    xv = sh->LX[j];
+                }
+                __syncwarp();
+                if (keep) {
+                    sh->L[nj] = lv;
+                    sh->EO[nj] = eov;
+                    sh->LX[nj] = xv;
+                }
+                __syncwarp();
             }
-            bool mv2 = j + 32 >= i1 && j + 32 < m - 1;
-            int lv2 = 0, eov2 = 0;
-            int2 xv2 = make_int2(0, 0);
-            if (mv2) {
-                lv2 = sh->L[j + 33];
-                eov2 = sh->EO[j + 33];
-                xv2 = sh->LX[j + 33];
-            }
-            __syncwarp();
-            if (mv) {
-                sh->L[j] = lv;
-                sh->EO[j] = eov;
-                sh->LX[j] = xv;
-            }
-            if (mv2) {
-                sh->L[j + 32] = lv2;
-                sh->EO[j + 32] = eov2;
-                sh->LX[j + 32] = xv2;
-            }
-            __syncwarp();
-            --m;
+            m -= ns;
+            newc += ns;
         }
         {
             int X = newc++;
@@ -472,6 +465,7 @@ __device__ int move_point(Warp &w, const Dev &d, int p, int2 q, int &s0, int &s1
             set_nb(sh, e2 >> 2, e2 & 3, X, (sX << 2) | 1);
             set_nb(sh, e0 >> 2, e0 & 3, X, (sX << 2) | 2);
             R.dirty |= (1ull << X) | (1ull << (e0 >> 2)) | (1ull << (e1 >> 2)) | (1ull << (e2 >> 2));
+            R.vchg |= 1ull << X;
         }
         // spares: staged entries k-2, k-1 (dead)
         const int X0 = k - 2, X1 = k - 1;
@@ -481,16 +475,17 @@ __device__ int move_point(Warp &w, const Dev &d, int p, int2 q, int &s0, int &s1
         sh->lnl[X1] = make_int4(-1, -1, -1, 0);
         if (w.lane == 0) d.pt_tri[p] = -1;
         R.dirty |= (1ull << X0) | (1ull << X1);
-        w.cnt[C_DEG_DEL] += k;
-        w.cnt[C_DELETES]++;
+        cnt_add(w, C_DEG_DEL, k);
+        cnt_add(w, C_DELETES, 1);
         s0 = sh->lslot[X0];
         s1 = sh->lslot[X1];
         hint = sh->lslot[0];
+        cnt_add(w, C_CYC_EAR, (unsigned)((clock64() - te0) >> 6));
         // Update (Fig. 4): p takes its new position
         if (w.lane == 0) d.xy[p] = q;
         __syncwarp();
         // ---- 2. locate q among the staged triangles
-        int where = -1, te = 0, tvtx = -1, tj = -1;
+        int where = -1, tvtx = -1, tj = -1;
         for (int base = 0; base < R.cnt && tj < 0; base += 32) {
             int j = base + w.lane;
             int e = 0, vt = -1;
@@ -501,7 +496,6 @@ __device__ int move_point(Warp &w, const Dev &d, int p, int2 q, int &s0, int &s1
                 int src = __ffs(bm) - 1;
                 tj = base + src;
                 where = __shfl_sync(FULL, r, src);
-                te = __shfl_sync(FULL, e, src);
                 tvtx = __shfl_sync(FULL, vt, src);
             }
         }
@@ -516,69 +510,167 @@ __device__ int move_point(Warp &w, const Dev &d, int p, int2 q, int &s0, int &s1
             if (st == d.stamp) return MV_DEFER;
             return DEV_DUPLICATE;
         }
-        // ---- 3. split (staged); every triangle whose refs change must be staged
-        int4 v = sh->lv[tj];
-        int *W = sh->tmp, *OL = sh->tmp + 8, *Xs = sh->tmp + 16;
-        int2 *WX = reinterpret_cast<int2 *>(sh->tmp + 24);
-        int mf;
-        bool okf;
-        if (where == 1) {
-            int e = te, e1 = (e + 1) % 3, e2 = (e + 2) % 3;
-            int Uj = nb_staged(w, d, R, tj, e);
-            int f = ic(sh->ln[tj], e) & 3, f1 = (f + 1) % 3, f2 = (f + 2) % 3;
-            okf = Uj >= 0 && nb_staged(w, d, R, tj, e1) >= 0 && nb_staged(w, d, R, tj, e2) >= 0 &&
-                  nb_staged(w, d, R, Uj, f1) >= 0 && nb_staged(w, d, R, Uj, f2) >= 0;
-            if (okf) {
-                int4 uv = sh->lv[Uj];
-                W[0] = ic(v, e);  WX[0] = sh->lp[tj][e];
-                W[1] = ic(v, e1); WX[1] = sh->lp[tj][e1];
-                W[2] = ic(uv, f); WX[2] = sh->lp[Uj][f];
-                W[3] = ic(v, e2); WX[3] = sh->lp[tj][e2];
-                // outer staged refs: (a,b) t opp c; (b,d) u opp c; (d,c) u opp b; (c,a) t opp b
-                OL[0] = (ic(sh->lnl[tj], e2) << 2) | (ic(sh->ln[tj], e2) & 3);
-                OL[1] = (ic(sh->lnl[Uj], f1) << 2) | (ic(sh->ln[Uj], f1) & 3);
-                OL[2] = (ic(sh->lnl[Uj], f2) << 2) | (ic(sh->ln[Uj], f2) & 3);
-                OL[3] = (ic(sh->lnl[tj], e1) << 2) | (ic(sh->ln[tj], e1) & 3);
-                Xs[0] = tj; Xs[1] = Uj; Xs[2] = X0; Xs[3] = X1;
-                w.cnt[C_SPLIT_EDGE]++;
+        // ---- 3. Bowyer-Watson insertion of q (Section IV names it for insertion): the
+        // cavity is every triangle whose circumcircle holds q (SoS incircle, ghost rule
+        // for ghosts), tested one staged triangle per lane; q is then joined to the
+        // cavity's boundary.  The cavity of a Delaunay triangulation is connected and
+        // star-shaped from q, so a cavity triangle whose neighbour is not staged makes
+        // that neighbour staged (claimed) and tested before the boundary is taken.
+        long long tl0 = clock64();
+        unsigned long long C = 0;
+        {
+            unsigned ex = 0, ti = 0;
+            for (int base = 0; base < R.cnt; base += 32) {
+                int j = base + w.lane;
+                bool c = false;
+                if (j < R.cnt && sh->lslot[j] >= 0) {
+                    int4 v = sh->lv[j];
+                    c = (v.w & ALIVE) && conflict(v.x, v.y, v.z, sh->lp[j][0], sh->lp[j][1], sh->lp[j][2], p, q,
+                                                  d.use_filter, &ex, &ti);
+                }
+                C |= (unsigned long long)__ballot_sync(FULL, c) << base;
             }
-            mf = 4;
-        } else {
-            okf = nb_staged(w, d, R, tj, 0) >= 0 && nb_staged(w, d, R, tj, 1) >= 0 &&
-                  nb_staged(w, d, R, tj, 2) >= 0;
-            if (okf) {
-                W[0] = v.x; W[1] = v.y; W[2] = v.z;
-                WX[0] = sh->lp[tj][0]; WX[1] = sh->lp[tj][1]; WX[2] = sh->lp[tj][2];
-                OL[0] = (sh->lnl[tj].z << 2) | (sh->ln[tj].z & 3);
-                OL[1] = (sh->lnl[tj].x << 2) | (sh->ln[tj].x & 3);
-                OL[2] = (sh->lnl[tj].y << 2) | (sh->ln[tj].y & 3);
-                Xs[0] = tj; Xs[1] = X0; Xs[2] = X1;
+            while (true) {
+                // a (cavity triangle, edge) pair whose neighbour is not staged
+                int gj = -1, ge = 0;
+                for (int base = 0; base < 3 * R.cnt && gj < 0; base += 32) {
+                    int idx = base + w.lane;
+                    int j = idx / 3, e = idx - 3 * j;
+                    bool need = idx < 3 * R.cnt && ((C >> j) & 1ull) && ic(sh->lnl[j], e) < 0;
+                    unsigned bm = __ballot_sync(FULL, need);
+                    if (bm) {
+                        int src = __ffs(bm) - 1;
+                        gj = __shfl_sync(FULL, j, src);
+                        ge = __shfl_sync(FULL, e, src);
+                    }
+                }
+                if (gj < 0) break;
+                int t = ensure_local(w, d, R.cnt, ic(sh->ln[gj], ge) >> 2);
+                if (t < 0) {
+                    write_back(w, d, R);
+                    return MV_GLOBAL;
+                }
+                if (t == R.cnt) ++R.cnt;
+                int4 v = sh->lv[t];
+                if ((v.w & ALIVE) && conflict(v.x, v.y, v.z, sh->lp[t][0], sh->lp[t][1], sh->lp[t][2], p, q,
+                                              d.use_filter, &ex, &ti))
+                    C |= 1ull << t;
+                if (ic(sh->lnl[gj], ge) < 0) {  // never expected: the new triangle is linked
+                    write_back(w, d, R);
+                    return MV_GLOBAL;
+                }
             }
-            mf = 3;
+            cnt_add(w, C_EXACT, __reduce_add_sync(FULL, ex));
+            cnt_add(w, C_TIES, __reduce_add_sync(FULL, ti));
         }
-        if (!okf) {
-            write_back(w, d, R);
-            return MV_GLOBAL;
+        const int ncav = __popcll(C);
+        if (!((C >> tj) & 1ull)) {  // q's triangle always conflicts: an inconsistent region
+            release_all(w, d);
+            return DEV_INTERNAL;
         }
-        local_fan(sh, R, p, q, W, WX, OL, Xs, mf);
-        w.cnt[C_INSERTS]++;
-        // ---- 4. Lawson flips of the edges opposite q
-        __syncwarp();
-        for (int j = 0; j < mf; ++j) sh->stack[j] = make_int2(Xs[j], 0);
-        int left = 0;
-        local_lawson(w, d, R, p, mf, &left);
-        // convert what is left to global (slot, edge) entries before the region goes
-        __syncwarp();
-        for (int j = w.lane; j < left; j += 32) {
-            int2 en = sh->stack[j];
-            sh->stack[j] = make_int2(sh->lslot[en.x], en.y);
+        // boundary edges (a -> b, counter-clockwise around the cavity) into S (a), I (b),
+        // L (outer staged ref), LX (coordinates of a)
+        int nbd = 0;
+        for (int base = 0; base < 3 * R.cnt; base += 32) {
+            int idx = base + w.lane;
+            int j = idx / 3, e = idx - 3 * j;
+            int kn = idx < 3 * R.cnt ? ic(sh->lnl[j], e) : -1;
+            bool b = idx < 3 * R.cnt && ((C >> j) & 1ull) && kn >= 0 && !((C >> kn) & 1ull);
+            unsigned bm = __ballot_sync(FULL, b);
+            int pos = nbd + __popc(bm & ((1u << w.lane) - 1u));
+            if (b && pos < KMAX) {
+                int4 v = sh->lv[j];
+                int e1 = e == 2 ? 0 : e + 1, e2 = e == 0 ? 2 : e - 1;
+                sh->S[pos] = ic(v, e1);
+                sh->I[pos] = ic(v, e2);
+                sh->L[pos] = (kn << 2) | (ic(sh->ln[j], e) & 3);
+                sh->LX[pos] = sh->lp[j][e1];
+            }
+            nbd += __popc(bm);
+        }
+        if (nbd != ncav + 2 || nbd > KMAX) {
+            release_all(w, d);
+            return DEV_INTERNAL;
         }
         __syncwarp();
+        // the new triangles reuse the cavity's entries (ascending) and the two spares;
+        // lane b joins q to boundary edge b, its neighbours are the edges that end at a
+        // (previous) and start at b (next)
+        unsigned long long dmask = 0, vmask = 0;
+        for (int b0 = 0; b0 < nbd; b0 += 32) {
+            int b = b0 + w.lane;
+            int a = 0, bb = 0, ol = 0, nx = -1, pv = -1;
+            int2 pa = make_int2(0, 0);
+            if (b < nbd) {
+                a = sh->S[b];
+                bb = sh->I[b];
+                ol = sh->L[b];
+                pa = sh->LX[b];
+                for (int c = 0; c < nbd; ++c) {
+                    if (sh->S[c] == bb) nx = c;
+                    if (sh->I[c] == a) pv = c;
+                }
+            }
+            // staged entry of boundary edge c: the c-th cavity triangle, then X0, X1
+            auto entry = [&](int c) -> int {
+                if (c >= ncav) return c == ncav ? X0 : X1;
+                unsigned lo = (unsigned)C, hi = (unsigned)(C >> 32);
+                int nlo = __popc(lo);
+                return c < nlo ? (int)__fns(lo, 0, c + 1) : 32 + (int)__fns(hi, 0, c - nlo + 1);
+            };
+            int x = -1, xn = -1, xp = -1;
+            int2 pb = make_int2(0, 0);
+            if (b < nbd) {
+                x = entry(b);
+                xn = nx >= 0 ? entry(nx) : -1;
+                xp = pv >= 0 ? entry(pv) : -1;
+                pb = nx >= 0 ? sh->LX[nx] : pa;
+            }
+            bool bad = b < nbd && (nx < 0 || pv < 0);
+            if (__any_sync(FULL, bad)) {
+                release_all(w, d);
+                return DEV_INTERNAL;
+            }
+            int sx = b < nbd ? sh->lslot[x] : 0, sxn = b < nbd ? sh->lslot[xn] : 0, sxp = b < nbd ? sh->lslot[xp] : 0;
+            __syncwarp();
+            if (b < nbd) {
+                sh->lv[x] = make_int4(p, a, bb, ALIVE);
+                sh->lp[x][0] = q;
+                sh->lp[x][1] = pa;
+                sh->lp[x][2] = pb;
+                set_nb(sh, x, 0, ol >> 2, gref_of(sh, ol));
+                set_nb(sh, x, 1, xn, (sxn << 2) | 2);
+                set_nb(sh, x, 2, xp, (sxp << 2) | 1);
+                set_nb(sh, ol >> 2, ol & 3, x, (sx << 2) | 0);
+                dmask |= (1ull << x) | (1ull << (ol >> 2));
+                vmask |= 1ull << x;
+            }
+        }
+        dmask |= __shfl_xor_sync(FULL, dmask, 16);
+        dmask |= __shfl_xor_sync(FULL, dmask, 8);
+        dmask |= __shfl_xor_sync(FULL, dmask, 4);
+        dmask |= __shfl_xor_sync(FULL, dmask, 2);
+        dmask |= __shfl_xor_sync(FULL, dmask, 1);
+        vmask |= __shfl_xor_sync(FULL, vmask, 16);
+        vmask |= __shfl_xor_sync(FULL, vmask, 8);
+        vmask |= __shfl_xor_sync(FULL, vmask, 4);
+        vmask |= __shfl_xor_sync(FULL, vmask, 2);
+        vmask |= __shfl_xor_sync(FULL, vmask, 1);
+        R.dirty |= dmask;
+        R.vchg |= vmask;
+        __syncwarp();
+        cnt_add(w, C_INSERTS, 1);
+        cnt_add(w, C_FLIPS, (unsigned)(ncav - 1));  // the Lawson flips of the same insertion
+        if (where == 1) cnt_add(w, C_SPLIT_EDGE, 1);
+        cnt_add(w, C_CYC_LAWSON, (unsigned)((clock64() - tl0) >> 6));
+        const int left = 0;
+        long long tc0 = clock64();
+        bool certified = left == 0 && certify_staged(w, d, R);
+        cnt_add(w, C_CYC_CERT, (unsigned)((clock64() - tc0) >> 6));
         long long t3 = clock64();
-        w.cnt[C_CYC_LOCAL] += (unsigned)((t3 - t2) >> 6);
-        write_back(w, d, R);
-        w.cnt[C_CYC_WB] += (unsigned)((clock64() - t3) >> 6);
-        if (left > 0) lawson(w, d, left, p, true);
+        cnt_add(w, C_CYC_LOCAL, (unsigned)((t3 - t2) >> 6));
+        write_back(w, d, R, certified);
+        cnt_add(w, C_CYC_WB, (unsigned)((clock64() - t3) >> 6));
         return MV_DONE;
     }
 }

@@ -52,6 +52,9 @@ _STAT_FIELDS = ["steps", "moves", "rebuilds", "fallbacks", "kernel_launches", "f
 _STAT_FIELDS2 = ["staged_to_global", "cycles_move", "cycles_move_max", "cycles_gather", "cycles_claim",
                  "cycles_local", "cycles_writeback"]
 
+_STAT_FIELDS3 = ["cycles_ear", "cycles_lawson", "cycles_certify", "proposal_moves", "proposal_hits",
+                 "trace_rows"]
+
 
 class Stats(ctypes.Structure):
     _fields_ = ([(f, ctypes.c_int64) for f in _STAT_FIELDS]
@@ -59,7 +62,9 @@ class Stats(ctypes.Structure):
                    ("last_fallback_reason", ctypes.c_int64), ("last_fallback_point", ctypes.c_int64)]
                 + [(f, ctypes.c_int64) for f in _STAT_FIELDS2]
                 + [("step_graph_ms", ctypes.c_double), ("tuned_points_per_partition", ctypes.c_int64),
-                   ("tuned_warps_per_partition", ctypes.c_int64), ("reserved", ctypes.c_int64 * 5)])
+                   ("tuned_warps_per_partition", ctypes.c_int64)]
+                + [(f, ctypes.c_int64) for f in _STAT_FIELDS3]
+                + [("reserved", ctypes.c_int64 * 8)])
 
 
 _lib = None
@@ -292,6 +297,8 @@ class Triangulation:
         d["step_graph_ms"] = float(s.step_graph_ms)
         d["tuned_points_per_partition"] = int(s.tuned_points_per_partition)
         d["tuned_warps_per_partition"] = int(s.tuned_warps_per_partition)
+        for f in _STAT_FIELDS3:
+            d[f] = int(getattr(s, f))
         return d
 
     def reset_stats(self):
