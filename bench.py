@@ -320,6 +320,137 @@ def run_c4(args):
     tri.close()
 
 
+def _timed_steps(tri, moves, warmup, flush):
+    """Per-step CUDA-event times (ms) of tri.step over moves[warmup:], L2 flushed between."""
+    import torch
+    for i in range(warmup):
+        tri.step(moves[i])
+    tri.reset_stats()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(len(moves) - warmup)]
+    torch.cuda.synchronize()
+    for k, (a, b) in enumerate(ev):
+        a.record()
+        tri.step(moves[warmup + k])
+        b.record()
+        flush.zero_()
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+MLP_FLOPS_PER_ROW = 2 * 7424 * 3 + 2 * 18 * 64 + 2 * 64 * 64  # forward, backward to inputs of layers 2-3, grads
+
+
+def run_c5(args):
+    """The learned locate proposal: train on traces of c2 and of the c3 distribution
+    (training seeds), evaluate on the headline c2 workload (its own seed): offline
+    top-1 accuracy, in-step hit rate, and updates/s with the proposal on and off."""
+    import time
+    import torch
+    from paper_2308_06484_gb300 import kdt, proposal, workloads as W
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    cfg = lambda g, b: kdt.default_config(grid=g, domain_bits=b, timing=1)
+    # ---- training rows
+    t0 = time.time()
+    traces = []
+    for (wl, steps, g) in ((W.c2(seed=102), args.c5_train_steps, 64),
+                           (W.c3(n=args.c5_c3_n, grid=args.c5_c3_grid, seed=103), args.c5_c3_steps, args.c5_c3_grid)):
+        tri = kdt.Triangulation(cfg(g, 24))
+        tri.build(torch.from_numpy(wl.positions).to(dev))
+        tr = proposal.Trace(args.c5_trace_cap)
+        tr.attach(tri)
+        for _ in range(steps):
+            tri.step(torch.from_numpy(wl.next_moves()).to(dev))
+        tr.detach(tri)
+        traces.append(tr.view())
+        tri.close()
+    x = torch.cat([a for a, _ in traces])
+    y = torch.cat([b for _, b in traces])
+    gen_s = time.time() - t0
+    # ---- training (and the gradient kernel's rate on one large batch)
+    holder = kdt.Triangulation(kdt.default_config())
+    tn = proposal.Trainer(holder, seed=0, lr=args.c5_lr)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    loss = tn.fit(x, y, epochs=args.c5_epochs, batch=args.c5_batch, seed=0)
+    train_s = time.time() - t1
+    rows_big = min(x.shape[0], 1 << 18)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        holder.mlp_loss_grad(tn.params, x[:rows_big], y[:rows_big], tn.grad, tn.loss)
+    a.record()
+    reps = 10
+    for _ in range(reps):
+        holder.mlp_loss_grad(tn.params, x[:rows_big], y[:rows_big], tn.grad, tn.loss)
+    b.record()
+    torch.cuda.synchronize()
+    grad_ms = a.elapsed_time(b) / reps
+    train_acc, train_mae = tn.evaluate(x, y)
+    # ---- evaluation on the headline workload
+    nsteps = args.warmup + args.steps
+    w_eval = W.c2()
+    moves = [torch.from_numpy(w_eval.next_moves()).to(dev) for _ in range(nsteps)]
+    xy0 = torch.from_numpy(W.c2().positions).to(dev)
+    res = {}
+    for mode in ("off", "on"):
+        tri = kdt.Triangulation(cfg(64, 24))
+        tri.build(xy0)
+        if mode == "on":
+            tri.set_proposal(tn.params)
+        tr = proposal.Trace(4096 * nsteps)
+        tr.attach(tri)
+        ms = _timed_steps(tri, moves, args.warmup, flush)
+        st = tri.stats()
+        tr.detach(tri)
+        res[mode] = {"ms": ms, "st": st, "trace": tr.view(), "check": None}
+        if args.check:
+            import oracle
+            res[mode]["check"] = bool(np.array_equal(tri.export_triangles(), oracle.delaunay(w_eval.positions)))
+        tri.close()
+    ex, ey = res["off"]["trace"]
+    eval_acc, eval_mae = tn.evaluate(ex, ey)
+    counts = torch.bincount(ey[:, 0].long(), minlength=17).float()
+    eval_majority = float((counts.max() / counts.sum()).item()) if ey.shape[0] else 0.0
+    m_avg = res["on"]["st"]["moves"] / args.steps
+    on_s = sum(res["on"]["ms"]) / 1000.0
+    off_s = sum(res["off"]["ms"]) / 1000.0
+    ston = res["on"]["st"]
+    peak_fp32 = 152 * 128 * 2 * 2.07e9 / 1e12
+    achieved = MLP_FLOPS_PER_ROW * rows_big / (grad_ms / 1000.0) / 1e12
+    line = {
+        "metric": METRIC, "value": res["on"]["st"]["moves"] / on_s, "unit": "updates/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * on_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64+int128 exact (fp32 filter); proposal net bf16 weights, fp32 accumulate",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD + ", learned locate proposal on", "moves_per_step": m_avg,
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "train": {"c2_seed": 102, "c2_steps": args.c5_train_steps, "c3_n": args.c5_c3_n,
+                             "c3_grid": args.c5_c3_grid, "c3_seed": 103, "c3_steps": args.c5_c3_steps,
+                             "rows": int(x.shape[0]), "epochs": args.c5_epochs, "batch": args.c5_batch,
+                             "lr": args.c5_lr}},
+        "proposal": {"in_step_hit_rate": ston["proposal_hits"] / max(1, ston["proposal_moves"]),
+                     "in_step_proposals": ston["proposal_moves"] / args.steps,
+                     "eval_top1": eval_acc, "eval_majority_class": eval_majority,
+                     "eval_log2_cavity_mae": eval_mae, "eval_rows": int(ex.shape[0]),
+                     "train_top1": train_acc, "train_loss": loss, "trace_s": gen_s, "train_s": train_s,
+                     "gain": (res["on"]["st"]["moves"] / on_s) / (res["off"]["st"]["moves"] / off_s) - 1.0},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
+                     "frac": achieved / peak_fp32, "traffic": None, "kernel": "k_mlp_grad",
+                     "kernel_ms": grad_ms, "rows": rows_big,
+                     "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
+        "comparators": {"gpu_kinetic_plain": {"value": res["off"]["st"]["moves"] / off_s, "unit": "updates/s",
+                                              "ms_per_step": 1000.0 * off_s / args.steps}},
+        "gpu_launches": int(ston["kernel_launches"]), "fallbacks": int(ston["fallbacks"]),
+    }
+    if args.check:
+        line["final_state_matches_oracle"] = {"on": res["on"]["check"], "off": res["off"]["check"]}
+    print(json.dumps(line), flush=True)
+    holder.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -334,10 +465,18 @@ def main():
     ap.add_argument("--ref-budget-s", type=float, default=90.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--check", action="store_true", help="compare the final state with the oracle")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c4"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5"],
                     help="c2: the headline single instance; c4: 512 batched instances")
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--c4-plain-steps", type=int, default=3)
+    ap.add_argument("--c5-train-steps", type=int, default=100)
+    ap.add_argument("--c5-c3-n", type=int, default=2_000_000)
+    ap.add_argument("--c5-c3-grid", type=int, default=90)
+    ap.add_argument("--c5-c3-steps", type=int, default=4)
+    ap.add_argument("--c5-trace-cap", type=int, default=1_000_000)
+    ap.add_argument("--c5-epochs", type=int, default=4)
+    ap.add_argument("--c5-batch", type=int, default=8192)
+    ap.add_argument("--c5-lr", type=float, default=2e-3)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -345,6 +484,8 @@ def main():
         return run_reference(args)
     if args.workload == "c4":
         return run_c4(args)
+    if args.workload == "c5":
+        return run_c5(args)
 
     import torch
     import torch.distributed as dist

@@ -238,6 +238,70 @@ int kdt_export_store(kdt *h, int32_t *tv, int32_t *tn, int32_t *pt_tri, int64_t 
 int kdt_eval_predicates(const int32_t *xy, const int32_t *quads, int64_t m, int32_t *out,
                         int use_filter, void *cuda_stream);
 
+/* ---- learned locate proposal (this library's extension; the paper has none) ------
+ *
+ * The paper locates the new position of a moved point by a walk (Section IV,
+ * insertion).  Here the staged kinetic move first tests the hole triangle a small
+ * network proposes, then (on a miss) every staged triangle; the exact tests decide,
+ * so the triangulation never depends on the network.  A training row describes one
+ * move of an interior point p to q on the triangulation in force when the move starts:
+ *
+ *   link    v_0..v_{k-1}: the neighbours of p, counter-clockwise;
+ *   j0      the one j whose half-open wedge [dir(v_j - p), dir(v_{j+1} - p)) holds
+ *           d = q - p; rotated index r(v_j) = (j - j0) mod k;
+ *   hole    the k - 2 triangles that replace p's star when p is deleted; each is named
+ *           by its rotated vertex indices sorted ascending, and the names sorted
+ *           lexicographically give the ranks;
+ *   slot    the lowest rank of a hole triangle whose closed region holds q, or 16
+ *           ("beyond") when none does or that rank is 16 or more;
+ *   cavity  the number of triangles the insertion of q destroys (Bowyer-Watson);
+ *   features (32 FP32, every operation correctly rounded): f0 = |d| / R, f1 = k / 16,
+ *           f[2+2r] = <v_{j0+r} - p, u> / R and f[3+2r] = <v_{j0+r} - p, n> / R for
+ *           r = 0..14 (0 for r >= k), u = d / |d|, n = u turned a quarter
+ *           counter-clockwise, R = mean |v_j - p| summed in rotated order.
+ *
+ * Network: 32 -> 64 (ReLU) -> 64 (ReLU) -> 18; outputs 0..16 are slot logits, output
+ * 17 predicts log2(cavity).  Parameters: KDT_MLP_PARAMS BF16 values in the order
+ * W1 [64][32] (row = output unit), b1 [64], W2 [64][64], b2 [64], W3 [18][64], b3 [18];
+ * products and sums in FP32.  Loss of a batch: mean over rows of
+ * cross-entropy(logits, slot) + lam * (out17 - log2(cavity))^2. */
+#define KDT_MLP_IN 32
+#define KDT_MLP_HIDDEN 64
+#define KDT_MLP_OUT 18
+#define KDT_MLP_SLOTS 17
+#define KDT_MLP_PARAMS 7442
+
+/* Record a training row for every staged move of an interior point in the following
+ * steps: features (device, cap x 32 FP32) and labels (device, cap x 2 int32: slot,
+ * cavity).  The caller owns both buffers and keeps them alive while recording; rows
+ * past cap are dropped.  Resets the row count.  cap = 0 (NULL buffers) stops. */
+int kdt_set_trace(kdt *h, float *features, int32_t *labels, int64_t cap);
+
+/* Rows recorded since kdt_set_trace (at most cap).  Synchronizes the handle's stream. */
+int kdt_trace_count(kdt *h, int64_t *rows);
+
+/* Use the network with these parameters (KDT_MLP_PARAMS BF16 values, host or device;
+ * copied) as the locate proposal of later steps; NULL turns the proposal off. */
+int kdt_set_proposal(kdt *h, const uint16_t *params_bf16);
+
+/* Network outputs for rows inputs: x (device, rows x 32) -> out (device, rows x 18).
+ * params_bf16: device, 4-byte aligned.  Asynchronous on the handle's stream (a handle
+ * needs no triangulation for the kdt_mlp_* calls). */
+int kdt_mlp_forward(kdt *h, const uint16_t *params_bf16, const float *x, int64_t rows, float *out);
+
+/* Mean loss (device scalar, may be NULL) and its gradient with respect to the BF16
+ * parameters' values (device, KDT_MLP_PARAMS FP32) over a batch: batch row r is input
+ * row index[r] (device int64) or r when index is NULL; labels as kdt_set_trace writes
+ * them.  Summation order is fixed, so results repeat exactly.  Asynchronous. */
+int kdt_mlp_loss_grad(kdt *h, const uint16_t *params_bf16, const float *x, const int32_t *labels,
+                      const int64_t *index, int64_t rows, float lam, float *grad, float *loss);
+
+/* One Adam step t >= 1 (Kingma and Ba, 2015) on FP32 master parameters with moments m
+ * and v (device, KDT_MLP_PARAMS each, updated in place); params_bf16 (device, may be
+ * NULL) receives the masters rounded to BF16 (nearest, ties to even).  Asynchronous. */
+int kdt_mlp_adam(kdt *h, float *master, const float *grad, float *m, float *v, int64_t t, float lr,
+                 float beta1, float beta2, float eps, uint16_t *params_bf16);
+
 #ifdef __cplusplus
 }
 #endif

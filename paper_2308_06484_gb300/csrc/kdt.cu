@@ -97,6 +97,15 @@ struct kdt {
     int *hscal = nullptr;  // pinned copy of the scalars
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
     kdt_stats stats{};
+    // learned locate proposal and its training rows (kdt_mlp.cuh)
+    unsigned short *mlp_w = nullptr;  // library copy of the proposal's BF16 parameters
+    bool prop_on = false;
+    float *trace_x = nullptr;         // caller's buffers
+    int *trace_y = nullptr;
+    int trace_cap = 0;
+    int *trace_count = nullptr;       // device counter
+    float *mlp_part = nullptr;        // per-block partial gradients of k_mlp_grad
+    int mlp_part_blocks = 0;
 };
 
 namespace {
@@ -189,6 +198,11 @@ Dev make_dev(kdt *h)
     d.viol_cap = h->viol_cap;
     d.rlo = 0;
     d.rn = (int)std::max<int64_t>(h->n, 1);
+    d.mlp = h->prop_on ? h->mlp_w : nullptr;
+    d.trace_x = h->trace_x;
+    d.trace_y = h->trace_y;
+    d.trace_count = h->trace_count;
+    d.trace_cap = h->trace_cap;
     return d;
 }
 
@@ -584,6 +598,10 @@ int enqueue_step(kdt *h, cudaStream_t st, const Dev &d, const int3 *mp, int mi, 
 {
     int cap = from_ctl ? h->mcap : mi;
     Inst I = make_inst(h);
+    // the step's control words and move offsets, from pinned host memory (a captured
+    // copy reads them when the graph runs)
+    if (from_ctl) CK(cudaMemcpyAsync(h->ctl, h->hctl, 4 * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(h->d_moff, h->h_moff, (h->ninst + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(h->scal, 0, S_NUM * sizeof(int), st));
     CK(cudaMemsetAsync(h->head, 0xff, (size_t)h->ncells * sizeof(int), st));  // empty lists
     k_intake_link<<<thread_grid(h, cap, 256), 256, 0, st>>>(d, mp, mi, I, h->cfg.domain_bits, h->head, h->next,
@@ -699,13 +717,13 @@ int step_impl(kdt *h, const kdt_move *moves, const int64_t *moff, int64_t m)
         mp = h->moves;
     }
     for (int i = 0; i <= h->ninst; ++i) h->h_moff[i] = (int)moff[i];
-    CK(cudaMemcpyAsync(h->d_moff, h->h_moff, (h->ninst + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
     h->stamp++;
     Dev d = make_dev(h);
     bool large = h->cfg.fallback && (double)m > (double)h->cfg.rebuild_ratio * (double)h->n;
     if (large) {
         // a step this large is cheaper as a rebuild (Abstract: "if the points move so
         // far, it's better to rebuild the triangulation")
+        CK(cudaMemcpyAsync(h->d_moff, h->h_moff, (h->ninst + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
         CK(cudaMemsetAsync(h->scal, 0, S_NUM * sizeof(int), st));
         CK(cudaMemsetAsync(h->head, 0xff, (size_t)h->ncells * sizeof(int), st));
         k_intake_link<<<thread_grid(h, mi, 256), 256, 0, st>>>(d, mp, mi, make_inst(h), h->cfg.domain_bits, h->head,
@@ -751,7 +769,6 @@ int step_impl(kdt *h, const kdt_move *moves, const int64_t *moff, int64_t m)
         h->hctl[2] = (int)(unsigned)(pa & 0xffffffffu);
         h->hctl[3] = (int)(unsigned)(pa >> 32);
         if (timed) CK(cudaEventRecord(h->ev2, st));
-        CK(cudaMemcpyAsync(h->ctl, h->hctl, 4 * sizeof(int), cudaMemcpyHostToDevice, st));
         CK(cudaGraphLaunch(h->gexec, st));
         if (timed) CK(cudaEventRecord(h->ev3, st));
     } else {
@@ -959,6 +976,9 @@ int kdt_destroy(kdt *h)
     free_state(h);
     if (h->scal) cudaFree(h->scal);
     if (h->counters) cudaFree(h->counters);
+    if (h->mlp_w) cudaFree(h->mlp_w);
+    if (h->trace_count) cudaFree(h->trace_count);
+    if (h->mlp_part) cudaFree(h->mlp_part);
     if (h->hscal) cudaFreeHost(h->hscal);
     if (h->ctl) cudaFree(h->ctl);
     if (h->hctl) cudaFreeHost(h->hctl);
@@ -1187,3 +1207,118 @@ extern "C" int kdt_export_triangles_noalloc(kdt *h, int32_t *out, int64_t cap, i
     return KDT_OK;
 }
 
+
+// ------------------------------------------------------------------ learned proposal
+
+extern "C" {
+
+int kdt_set_trace(kdt *h, float *features, int32_t *labels, int64_t cap)
+{
+    if (!h || cap < 0 || (cap > 0 && (!features || !labels)) || cap > INT_MAX) return KDT_ERR_ARG;
+    if (cap > 0 && (!is_device_ptr(features) || !is_device_ptr(labels))) return KDT_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    if (!h->trace_count && cudaMalloc(&h->trace_count, sizeof(int)) != cudaSuccess) return KDT_ERR_CUDA;
+    CK(cudaMemsetAsync(h->trace_count, 0, sizeof(int), h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->trace_x = cap > 0 ? features : nullptr;
+    h->trace_y = cap > 0 ? labels : nullptr;
+    h->trace_cap = (int)cap;
+    h->gen++;  // a captured step graph holds the old Dev
+    return KDT_OK;
+}
+
+int kdt_trace_count(kdt *h, int64_t *rows)
+{
+    if (!h || !rows) return KDT_ERR_ARG;
+    *rows = 0;
+    if (!h->trace_count) return KDT_OK;
+    CK(cudaSetDevice(h->device));
+    int c = 0;
+    CK(cudaMemcpyAsync(&c, h->trace_count, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *rows = std::min<int64_t>(c, h->trace_cap);
+    return KDT_OK;
+}
+
+int kdt_set_proposal(kdt *h, const uint16_t *params_bf16)
+{
+    if (!h) return KDT_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    if (!params_bf16) {
+        h->prop_on = false;
+        h->gen++;
+        return KDT_OK;
+    }
+    if (!h->mlp_w && cudaMalloc(&h->mlp_w, MLP_PARAMS * sizeof(uint16_t)) != cudaSuccess) return KDT_ERR_CUDA;
+    CK(cudaMemcpyAsync(h->mlp_w, params_bf16, MLP_PARAMS * sizeof(uint16_t),
+                       is_device_ptr(params_bf16) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->prop_on = true;
+    h->gen++;
+    return KDT_OK;
+}
+
+int kdt_mlp_forward(kdt *h, const uint16_t *params_bf16, const float *x, int64_t rows, float *out)
+{
+    if (!h || rows < 0 || (rows > 0 && (!params_bf16 || !x || !out))) return KDT_ERR_ARG;
+    if (rows == 0) return KDT_OK;
+    if (!is_device_ptr(params_bf16) || !is_device_ptr(x) || !is_device_ptr(out)) return KDT_ERR_ARG;
+    if (((uintptr_t)params_bf16 & 3) != 0) return KDT_ERR_ARG;  // read as BF16 pairs
+    CK(cudaSetDevice(h->device));
+    long long warps = rows < (1ll << 22) ? rows : (1ll << 22);
+    int blocks = (int)((warps * 32 + 255) / 256);
+    k_mlp_forward<<<blocks, 256, 0, h->stream>>>((const unsigned short *)params_bf16, x, rows, out);
+    h->stats.kernel_launches++;
+    CK(cudaGetLastError());
+    return KDT_OK;
+}
+
+int kdt_mlp_loss_grad(kdt *h, const uint16_t *params_bf16, const float *x, const int32_t *labels,
+                      const int64_t *index, int64_t rows, float lam, float *grad, float *loss)
+{
+    if (!h || rows <= 0 || !params_bf16 || !x || !labels || !grad) return KDT_ERR_ARG;
+    if (!is_device_ptr(params_bf16) || !is_device_ptr(x) || !is_device_ptr(labels) || !is_device_ptr(grad) ||
+        (loss && !is_device_ptr(loss)) || (index && !is_device_ptr(index)))
+        return KDT_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    long long tiles = (rows + GT - 1) / GT;
+    int blocks = (int)std::min<long long>(tiles, 2ll * sms);
+    if (blocks > h->mlp_part_blocks) {
+        if (h->mlp_part) cudaFree(h->mlp_part);
+        h->mlp_part = nullptr;
+        h->mlp_part_blocks = 0;
+        if (cudaMalloc(&h->mlp_part, (size_t)blocks * (MLP_PARAMS + 1) * sizeof(float)) != cudaSuccess)
+            return KDT_ERR_CUDA;
+        h->mlp_part_blocks = blocks;
+    }
+    const size_t smem = sizeof(MlpSmem);
+    CK(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    float *part_loss = h->mlp_part + (size_t)h->mlp_part_blocks * MLP_PARAMS;
+    k_mlp_grad<<<blocks, GTHREADS, smem, h->stream>>>((const unsigned short *)params_bf16, x, (const int *)labels,
+                                                     (const long long *)index, rows, lam, h->mlp_part, part_loss);
+    k_mlp_reduce<<<(MLP_PARAMS + 255) / 256, 256, 0, h->stream>>>(h->mlp_part, part_loss, blocks, rows, grad, loss);
+    h->stats.kernel_launches += 2;
+    CK(cudaGetLastError());
+    return KDT_OK;
+}
+
+int kdt_mlp_adam(kdt *h, float *master, const float *grad, float *m, float *v, int64_t t, float lr, float beta1,
+                 float beta2, float eps, uint16_t *params_bf16)
+{
+    if (!h || !master || !grad || !m || !v || t < 1) return KDT_ERR_ARG;
+    if (!is_device_ptr(master) || !is_device_ptr(grad) || !is_device_ptr(m) || !is_device_ptr(v) ||
+        (params_bf16 && !is_device_ptr(params_bf16)))
+        return KDT_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    double bc1 = 1.0 - std::pow((double)beta1, (double)t), bc2 = 1.0 - std::pow((double)beta2, (double)t);
+    k_mlp_adam<<<(MLP_PARAMS + 255) / 256, 256, 0, h->stream>>>(master, grad, m, v, MLP_PARAMS, lr, beta1, beta2, eps,
+                                                                (float)bc1, (float)bc2,
+                                                                (unsigned short *)params_bf16);
+    h->stats.kernel_launches++;
+    CK(cudaGetLastError());
+    return KDT_OK;
+}
+
+}  // extern "C"

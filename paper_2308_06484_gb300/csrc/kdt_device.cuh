@@ -79,6 +79,12 @@ struct Dev {
     unsigned long long *counters;
     int use_filter;
     int retry_cap;
+    // learned locate proposal (kdt_mlp.cuh) and its training rows; null = off
+    const unsigned short *mlp;  // network parameters, BF16
+    float *trace_x;             // features, trace_cap x 32
+    int *trace_y;               // (slot, cavity size) per row
+    int *trace_count;           // rows written (may exceed trace_cap: later rows dropped)
+    int trace_cap;
 };
 
 struct WarpShared {

@@ -26,6 +26,7 @@
 // warp barrier.
 #pragma once
 #include "kdt_device.cuh"
+#include "kdt_mlp.cuh"
 
 namespace kd {
 
@@ -221,6 +222,81 @@ __device__ __forceinline__ int locate_in(const WarpShared *sh, int j, int2 q, in
     return 2;
 }
 
+// ---- features of a move for the learned proposal and its training rows
+//
+// For an interior p with link v_0..v_{k-1} (counter-clockwise, in L / LX):
+//   j0: the one j whose half-open wedge [dir(v_j - p), dir(v_{j+1} - p)) holds the
+//       move direction d = q - p (exact integer cross products); -1 if none is found;
+//   feature (lane l): f0 = |d| / R, f1 = k / 16, and for r = 0..14 the link vertex
+//       v_{j0+r} relative to p in the frame (u, n) of the move (u = d / |d|, n = u
+//       turned a quarter counter-clockwise), divided by R = mean |v_j - p| summed in
+//       the order r = 0..k-1: f[2+2r] = <v - p, u> / R, f[3+2r] = <v - p, n> / R,
+//       0 for r >= k.  Every operation is a correctly rounded FP32 operation.
+__device__ __forceinline__ int move_wedge(const WarpShared *sh, int k, int2 po, int2 q, int lane)
+{
+    long long dx = (long long)q.x - po.x, dy = (long long)q.y - po.y;
+    bool hit = false;
+    if (lane < k) {
+        int2 a = sh->LX[lane], b = sh->LX[lane + 1 == k ? 0 : lane + 1];
+        long long ax = (long long)a.x - po.x, ay = (long long)a.y - po.y;
+        long long bx = (long long)b.x - po.x, by = (long long)b.y - po.y;
+        hit = ax * dy - ay * dx >= 0 && dx * by - dy * bx > 0;
+    }
+    unsigned bm = __ballot_sync(FULL, hit);
+    return __popc(bm) == 1 ? __ffs(bm) - 1 : -1;
+}
+
+__device__ __forceinline__ float move_feature(const WarpShared *sh, int k, int j0, int2 po, int2 q, int lane)
+{
+    float dx = __int2float_rn(q.x - po.x), dy = __int2float_rn(q.y - po.y);
+    float s = __fsqrt_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)));
+    float ux = __fdiv_rn(dx, s), uy = __fdiv_rn(dy, s);
+    float R = 0.f;
+    for (int r = 0; r < k; ++r) {
+        int j = j0 + r >= k ? j0 + r - k : j0 + r;
+        int2 v = sh->LX[j];
+        float rx = __int2float_rn(v.x - po.x), ry = __int2float_rn(v.y - po.y);
+        R = __fadd_rn(R, __fsqrt_rn(__fadd_rn(__fmul_rn(rx, rx), __fmul_rn(ry, ry))));
+    }
+    R = __fdiv_rn(R, __int2float_rn(k));
+    if (lane == 0) return __fdiv_rn(s, R);
+    if (lane == 1) return __fdiv_rn(__int2float_rn(k), 16.0f);
+    int r = (lane - 2) >> 1;
+    if (r >= k) return 0.f;
+    int j = j0 + r >= k ? j0 + r - k : j0 + r;
+    int2 v = sh->LX[j];
+    float rx = __int2float_rn(v.x - po.x), ry = __int2float_rn(v.y - po.y);
+    float num = (lane & 1) == 0 ? __fadd_rn(__fmul_rn(rx, ux), __fmul_rn(ry, uy))
+                                : __fsub_rn(__fmul_rn(ry, ux), __fmul_rn(rx, uy));
+    return __fdiv_rn(num, R);
+}
+
+// Rank of hole triangle `lane` (< k - 2; the others get a large value): its vertices'
+// rotated link indices (link position - j0 mod k, link order saved in L0) sorted
+// ascending name it, and the names sorted lexicographically give the ranks.
+__device__ __forceinline__ int hole_rank(const WarpShared *sh, const int *L0, int k, int j0, int lane)
+{
+    int key = 1 << 30;
+    if (lane < k - 2) {
+        int4 v = sh->lv[lane];
+        int ra = 0, rb = 0, rc = 0;
+        for (int i = 0; i < k; ++i) {
+            int r = i - j0 < 0 ? i - j0 + k : i - j0;
+            if (L0[i] == v.x) ra = r;
+            if (L0[i] == v.y) rb = r;
+            if (L0[i] == v.z) rc = r;
+        }
+        int lo = min(ra, min(rb, rc)), hi = max(ra, max(rb, rc)), mid = ra + rb + rc - lo - hi;
+        key = (lo << 12) | (mid << 6) | hi;
+    }
+    int rank = 0;
+    for (int t = 0; t < k - 2; ++t) {
+        int kt = __shfl_sync(FULL, key, t);
+        rank += kt < key;
+    }
+    return lane < k - 2 ? rank : 1 << 30;
+}
+
 // Move p to q: delete p and insert it at q in one claimed region.  On MV_GLOBAL the
 // deletion is written back and the caller inserts p at q with insert_point starting
 // at `hint` with the spares (s0, s1); on MV_DEFER likewise but q is still occupied by
@@ -335,6 +411,19 @@ __device__ int move_point(Warp w, const Dev &d, int p, int2 q, int &s0, int &s1,
                     return DEV_DEGENERATE;
                 }
             }
+        }
+        // ---- learned proposal / training rows: the move's features (interior p only);
+        // the link order is kept in I for the hole ranks (I is not needed any more)
+        const bool learn = (d.mlp != nullptr || d.trace_x != nullptr) && gpos < 0;
+        float feat = 0.f;
+        int j0 = -1;
+        if (learn) {
+            int2 po = sh->lp[0][sh->I[0]];  // p's position before the move
+            j0 = move_wedge(sh, k, po, q, w.lane);
+            if (j0 >= 0) feat = move_feature(sh, k, j0, po, q, w.lane);
+            __syncwarp();
+            for (int i = w.lane; i < k; i += 32) sh->I[i] = sh->L[i];
+            __syncwarp();
         }
         // ---- 1. delete p: Delaunay ears over the link, into the star's staged entries
         long long te0 = clock64();
@@ -484,8 +573,30 @@ __device__ int move_point(Warp w, const Dev &d, int p, int2 q, int &s0, int &s1,
         // Update (Fig. 4): p takes its new position
         if (w.lane == 0) d.xy[p] = q;
         __syncwarp();
-        // ---- 2. locate q among the staged triangles
+        // ---- 2. locate q among the staged triangles (first the proposed one)
         int where = -1, tvtx = -1, tj = -1;
+        int rank = 1 << 30, slot = MLP_BEYOND;
+        if (learn && j0 >= 0) {
+            rank = hole_rank(sh, sh->I, k, j0, w.lane);
+            int e = 0, vt = -1;
+            int r = w.lane < k - 2 ? locate_in(sh, w.lane, q, &e, &vt) : -1;
+            // training label: the lowest-ranked hole triangle holding q (closed)
+            int lab = (r == 0 || r == 1) ? rank : 1 << 30;
+#pragma unroll
+            for (int off = 16; off; off >>= 1) lab = min(lab, __shfl_xor_sync(FULL, lab, off));
+            slot = lab < MLP_BEYOND ? lab : MLP_BEYOND;
+            if (d.mlp) {
+                int guess = mlp_argmax_slot(mlp_warp_forward(d.mlp, feat, w.lane), w.lane);
+                cnt_add(w, C_PROP_MOVES, 1);
+                unsigned bm = __ballot_sync(FULL, guess < MLP_BEYOND && rank == guess && (r == 0 || r == 1));
+                if (bm) {
+                    int src = __ffs(bm) - 1;
+                    tj = src;
+                    where = __shfl_sync(FULL, r, src);
+                    cnt_add(w, C_PROP_HITS, 1);
+                }
+            }
+        }
         for (int base = 0; base < R.cnt && tj < 0; base += 32) {
             int j = base + w.lane;
             int e = 0, vt = -1;
@@ -661,6 +772,19 @@ __device__ int move_point(Warp w, const Dev &d, int p, int2 q, int &s0, int &s1,
         __syncwarp();
         cnt_add(w, C_INSERTS, 1);
         cnt_add(w, C_FLIPS, (unsigned)(ncav - 1));  // the Lawson flips of the same insertion
+        if (learn && j0 >= 0 && d.trace_x) {
+            int row = 0;
+            if (w.lane == 0) row = atomicAdd(d.trace_count, 1);
+            row = __shfl_sync(FULL, row, 0);
+            if (row < d.trace_cap) {
+                d.trace_x[(long long)row * MLP_IN + w.lane] = feat;
+                if (w.lane == 0) {
+                    d.trace_y[2ll * row] = slot;
+                    d.trace_y[2ll * row + 1] = ncav;
+                }
+                cnt_add(w, C_TRACE_ROWS, 1);
+            }
+        }
         if (where == 1) cnt_add(w, C_SPLIT_EDGE, 1);
         cnt_add(w, C_CYC_LAWSON, (unsigned)((clock64() - tl0) >> 6));
         const int left = 0;

@@ -75,7 +75,10 @@ SYMBOLS = ["kdt_default_config", "kdt_create", "kdt_destroy", "kdt_build", "kdt_
            "kdt_num_points", "kdt_get_stats", "kdt_reset_stats", "kdt_error_string",
            "kdt_version", "kdt_eval_predicates", "kdt_export_store",
            "kdt_export_triangles_noalloc", "kdt_build_batch", "kdt_step_batch",
-           "kdt_export_triangles_inst", "kdt_num_instances"]
+           "kdt_export_triangles_inst", "kdt_num_instances", "kdt_set_trace", "kdt_trace_count",
+           "kdt_set_proposal", "kdt_mlp_forward", "kdt_mlp_loss_grad", "kdt_mlp_adam"]
+
+MLP_IN, MLP_OUT, MLP_SLOTS, MLP_PARAMS = 32, 18, 17, 7442
 
 
 def lib_path():
@@ -117,6 +120,13 @@ def load(build_if_stale: bool = True):
     L.kdt_export_triangles_inst.argtypes = [vp, ctypes.c_int32, vp, i64, ctypes.POINTER(i64)]
     L.kdt_num_instances.argtypes = [vp]
     L.kdt_num_instances.restype = ctypes.c_int32
+    f32 = ctypes.c_float
+    L.kdt_set_trace.argtypes = [vp, vp, vp, i64]
+    L.kdt_trace_count.argtypes = [vp, ctypes.POINTER(i64)]
+    L.kdt_set_proposal.argtypes = [vp, vp]
+    L.kdt_mlp_forward.argtypes = [vp, vp, vp, i64, vp]
+    L.kdt_mlp_loss_grad.argtypes = [vp, vp, vp, vp, vp, i64, f32, vp, vp]
+    L.kdt_mlp_adam.argtypes = [vp, vp, vp, vp, vp, i64, f32, f32, f32, f32, vp]
     for s in SYMBOLS:
         getattr(L, s)
     _lib = L
@@ -135,6 +145,19 @@ def _ptr(a, nd_last=None):
     if not isinstance(a, np.ndarray) or a.dtype != np.int32 or not a.flags["C_CONTIGUOUS"]:
         raise ValueError("expected a C-contiguous int32 numpy array")
     return ctypes.c_void_p(a.ctypes.data), a.shape[0] if a.ndim else 0
+
+
+def _dptr(t, dtype_name, n_last=None):
+    """Device pointer of a contiguous CUDA torch tensor of the given dtype (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    want = getattr(torch, dtype_name)
+    if not hasattr(t, "data_ptr") or t.dtype != want or not t.is_contiguous() or not t.is_cuda:
+        raise ValueError("expected a contiguous CUDA %s tensor" % dtype_name)
+    if n_last is not None and (t.dim() < 1 or t.shape[-1] != n_last):
+        raise ValueError("expected last dimension %d" % n_last)
+    return ctypes.c_void_p(t.data_ptr())
 
 
 def _check(rc, where):
@@ -303,6 +326,55 @@ class Triangulation:
 
     def reset_stats(self):
         _check(self.L.kdt_reset_stats(self.h), "kdt_reset_stats")
+
+    # learned locate proposal (library extension)
+    def set_trace(self, features=None, labels=None):
+        """Record training rows into CUDA tensors features (cap, 32) float32 and labels
+        (cap, 2) int32; no arguments stop recording."""
+        if features is None:
+            _check(self.L.kdt_set_trace(self.h, None, None, 0), "kdt_set_trace")
+            return
+        cap = features.shape[0]
+        if labels.shape != (cap, 2):
+            raise ValueError("labels must be (cap, 2)")
+        _check(self.L.kdt_set_trace(self.h, _dptr(features, "float32", MLP_IN), _dptr(labels, "int32", 2), cap),
+               "kdt_set_trace")
+
+    def trace_count(self) -> int:
+        n = ctypes.c_int64(0)
+        _check(self.L.kdt_trace_count(self.h, ctypes.byref(n)), "kdt_trace_count")
+        return int(n.value)
+
+    def set_proposal(self, params_bf16=None):
+        """Use the network with these BF16 parameters (CUDA int16 tensor or numpy uint16
+        array of 7442 bit patterns) as the locate proposal; None turns it off."""
+        if params_bf16 is None:
+            _check(self.L.kdt_set_proposal(self.h, None), "kdt_set_proposal")
+            return
+        if isinstance(params_bf16, np.ndarray):
+            a = np.ascontiguousarray(params_bf16, dtype=np.uint16)
+            if a.size != MLP_PARAMS:
+                raise ValueError("expected %d parameters" % MLP_PARAMS)
+            _check(self.L.kdt_set_proposal(self.h, ctypes.c_void_p(a.ctypes.data)), "kdt_set_proposal")
+            return
+        if params_bf16.numel() != MLP_PARAMS:
+            raise ValueError("expected %d parameters" % MLP_PARAMS)
+        _check(self.L.kdt_set_proposal(self.h, _dptr(params_bf16, "int16")), "kdt_set_proposal")
+
+    def mlp_forward(self, params_bf16, x, out):
+        _check(self.L.kdt_mlp_forward(self.h, _dptr(params_bf16, "int16"), _dptr(x, "float32", MLP_IN),
+                                      x.shape[0], _dptr(out, "float32", MLP_OUT)), "kdt_mlp_forward")
+
+    def mlp_loss_grad(self, params_bf16, x, labels, grad, loss=None, index=None, rows=None, lam=0.25):
+        rows = (index.shape[0] if index is not None else x.shape[0]) if rows is None else rows
+        _check(self.L.kdt_mlp_loss_grad(self.h, _dptr(params_bf16, "int16"), _dptr(x, "float32", MLP_IN),
+                                        _dptr(labels, "int32", 2), _dptr(index, "int64"), rows, lam,
+                                        _dptr(grad, "float32"), _dptr(loss, "float32")), "kdt_mlp_loss_grad")
+
+    def mlp_adam(self, master, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, params_bf16=None):
+        _check(self.L.kdt_mlp_adam(self.h, _dptr(master, "float32"), _dptr(grad, "float32"), _dptr(m, "float32"),
+                                   _dptr(v, "float32"), t, lr, beta1, beta2, eps, _dptr(params_bf16, "int16")),
+               "kdt_mlp_adam")
 
 
 def eval_predicates(xy_dev, quads_dev, out_dev, use_filter: bool = True, stream=None):
