@@ -374,7 +374,13 @@ __device__ __noinline__ WalkResult walk(Warp w, const Dev &d, int t, int2 q)
             continue;
         }
         int o0 = orient2d(p1, p2, q), o1 = orient2d(p2, p0, q), o2 = orient2d(p0, p1, q);
-        unsigned r = warp_rand(w) % 3;
+        // the edge tried first varies with the slot, the step count and the warp (a
+        // hash, uniform across the warp), so walks cannot cycle
+        unsigned h = (unsigned)t * 0x9E3779B1u ^ (unsigned)(steps + 1) * 0x85EBCA77u ^ (unsigned)w.token * 0xC2B2AE3Du;
+        h ^= h >> 15;
+        h *= 0x2C1B3C6Du;
+        h ^= h >> 12;
+        unsigned r = h % 3;
         int nxt = -1;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
