@@ -334,7 +334,7 @@ int rebuild_instance(kdt *h, int i)
     cudaStream_t st = h->stream;
     Dev d = make_dev(h);
     d.dirty_cap = 0;  // the build certifies every slot of the instance instead
-    if (d.retry_cap < 4096) d.retry_cap = 4096;  // the step's cap does not apply to builds
+    if (d.retry_cap < 32768) d.retry_cap = 32768;  // the step's cap does not apply to builds
     d.rlo = p0;
     d.rn = n;
     CK(cudaMemsetAsync(h->scal, 0, S_NUM * sizeof(int), st));
@@ -379,8 +379,10 @@ int rebuild_instance(kdt *h, int i)
     for (int lev = K; lev >= 0; --lev) {
         long long items = ((long long)n - 1 + (1ll << lev)) >> (lev + 1);  // odd multiples of 2^lev below n
         if (items <= 0) continue;
+        // about 16 triangles of room per concurrent insertion: more warps than that only
+        // collide on the same cavities (claims fail, back off, retry)
         long long conc = inserted / 8;
-        if (conc < 64) conc = 64;
+        if (conc < 8) conc = 8;
         if (h->cfg.build_warps > 0) conc = h->cfg.build_warps;
         long long warps = items < conc ? items : conc;
         int blocks = warp_grid(h, warps, 64), threads = WPB * 32;

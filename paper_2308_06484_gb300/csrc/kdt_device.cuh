@@ -222,7 +222,7 @@ __device__ __forceinline__ void dirty_push(const Dev &d, int t)
 
 __device__ __forceinline__ void backoff(Warp w, int attempt)
 {
-    unsigned lim = 32u << (attempt < 7 ? attempt : 7);
+    unsigned lim = 32u << (attempt < 10 ? attempt : 10);  // up to ~33 us
     unsigned ns = 16 + (warp_rand(w) % lim);
     if (w.lane == 0) __nanosleep(ns);
     __syncwarp();

@@ -264,7 +264,8 @@ __global__ void __launch_bounds__(WPB * 32, 7) k_kinetic(Dev dp, const int3 *mov
                     __threadfence();
                 }
                 __syncwarp();
-                rc = insert_point(w, d, p, q, hint, s0, s1, true);
+                rc = insert_staged(w, d, p, q, hint, s0, s1, true);
+                if (rc == 2) rc = insert_point(w, d, p, q, hint, s0, s1, true);
             }
             {
                 unsigned cy = (unsigned)((clock64() - c0) >> 6);
@@ -378,7 +379,8 @@ __device__ void step_tail(Warp w, const Dev &d, Inst I, const int4 *deferred, co
         q = bcast2(q, 0);
         int inst = I.ninst > 1 ? csr_find(I.pofs, I.ninst + 1, e.x) : 0;
         set_instance(w, I.pofs[inst], I.pofs[inst + 1] - I.pofs[inst]);
-        int rc = insert_point(w, d, e.x, q, e.w, e.y, e.z, false);
+        int rc = insert_staged(w, d, e.x, q, e.w, e.y, e.z, false);
+        if (rc == 2) rc = insert_point(w, d, e.x, q, e.w, e.y, e.z, false);
         if (rc) {
             if (rc > 0) set_status(d, rc);
             return;
@@ -554,7 +556,11 @@ __global__ void __launch_bounds__(WPB * 32) k_insert_level(Dev dp, const int *or
     int gw = blockIdx.x * (blockDim.x >> 5) + wib;
     int nw = gridDim.x * (blockDim.x >> 5);
     Warp w = make_warp(&shs[wib], gw + 1, gw * 7 + level * 1315423911u, d);
-    for (int j = gw; j < items; j += nw) {
+    // each warp takes a contiguous run of the level's points: runs are far apart along
+    // the Hilbert curve, so the insertions in flight at any moment rarely share a cavity
+    const int per = (items + nw - 1) / nw;
+    const int jend = min(items, (gw + 1) * per);
+    for (int j = gw * per; j < jend; ++j) {
         if (read_status(d)) break;
         long long i = ((long long)(2 * j + 1)) << level;
         if (i >= nloc) continue;
@@ -571,7 +577,8 @@ __global__ void __launch_bounds__(WPB * 32) k_insert_level(Dev dp, const int *or
             break;
         }
         int2 q = d.xy[v];
-        int rc = insert_point(w, d, v, q, start, s, s + 1, false);
+        int rc = insert_staged(w, d, v, q, start, s, s + 1, false);
+        if (rc == 2) rc = insert_point(w, d, v, q, start, s, s + 1, false);
         if (rc) {
             if (rc > 0) set_status(d, rc);
             break;

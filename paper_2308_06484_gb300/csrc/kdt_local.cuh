@@ -222,6 +222,240 @@ __device__ __forceinline__ int locate_in(const WarpShared *sh, int j, int2 q, in
     return 2;
 }
 
+// ---- Bowyer-Watson insertion on a staged region
+
+enum BwResult : int { BW_OK = 0, BW_CLAIM = 1, BW_FULL = 2, BW_BAD = 3 };
+
+// Stage every not-yet-staged neighbour of the cavity triangles (C) at once: claim them
+// together, read them under the claims, link them to the staged triangles both ways, and
+// add those in conflict with q to C.  Repeats until the cavity's boundary is staged.
+__device__ __forceinline__ int bw_grow(Warp w, const Dev &d, Region &R, int p, int2 q, unsigned long long &C)
+{
+    WarpShared *sh = w.sh;
+    int *need = sh->tmp;  // the slots to stage this round
+    while (true) {
+        int nneed = 0;
+        for (int base = 0; base < 3 * R.cnt; base += 32) {
+            int idx = base + w.lane;
+            int j = idx / 3, e = idx - 3 * j;
+            bool nd = idx < 3 * R.cnt && ((C >> j) & 1ull) && ic(sh->lnl[j], e) < 0;
+            unsigned bm = __ballot_sync(FULL, nd);
+            int pos = nneed + __popc(bm & ((1u << w.lane) - 1u));
+            if (nd && pos < 64) need[pos] = ic(sh->ln[j], e) >> 2;
+            nneed += __popc(bm);
+        }
+        if (nneed == 0) return BW_OK;
+        if (nneed > 64) return BW_FULL;
+        __syncwarp();
+        // distinct slots, in first-seen order
+        int mine = w.lane < nneed ? need[w.lane] : -1;
+        int mine2 = w.lane + 32 < nneed ? need[w.lane + 32] : -1;
+        bool keep = mine >= 0, keep2 = mine2 >= 0;
+        for (int t = 0; t < nneed; ++t) {
+            int o = need[t];
+            if (t < w.lane && o == mine) keep = false;
+            if (t < w.lane + 32 && o == mine2) keep2 = false;
+        }
+        if (mine < 0 || mine >= d.cap) keep = false;
+        if (mine2 < 0 || mine2 >= d.cap) keep2 = false;
+        unsigned k1 = __ballot_sync(FULL, keep), k2 = __ballot_sync(FULL, keep2);
+        const int nu = __popc(k1) + __popc(k2);
+        if (R.cnt + nu > LM || w.sh->ncl + nu > MAXC) return BW_FULL;
+        __syncwarp();
+        if (keep) need[__popc(k1 & ((1u << w.lane) - 1u))] = mine;
+        if (keep2) need[__popc(k1) + __popc(k2 & ((1u << w.lane) - 1u))] = mine2;
+        __syncwarp();
+        if (!claim_list(w, d, need, nu)) return BW_CLAIM;
+        // read the new triangles under their claims, then their vertices' coordinates
+        const int base0 = R.cnt, cnt1 = R.cnt + nu;
+        for (int i = w.lane; i < nu; i += 32) {
+            int j = base0 + i, slot = need[i];
+            int4 v = __ldcg(d.tv + slot), nb = __ldcg(d.tn + slot);
+            sh->lslot[j] = slot;
+            sh->lv[j] = v;
+            sh->ln[j] = nb;
+            int2 z = make_int2(0, 0);
+            sh->lp[j][0] = v.x >= 0 ? __ldcg(d.xy + v.x) : z;
+            sh->lp[j][1] = v.y >= 0 ? __ldcg(d.xy + v.y) : z;
+            sh->lp[j][2] = v.z >= 0 ? __ldcg(d.xy + v.z) : z;
+        }
+        __syncwarp();
+        bool bad = false;
+        for (int i = w.lane; i < nu; i += 32) {
+            int j = base0 + i;
+            int4 nb = sh->ln[j];
+            bad = bad || !(sh->lv[j].w & ALIVE);
+            int lk[3] = {-1, -1, -1};
+            for (int t = 0; t < cnt1; ++t) {
+                int sl = sh->lslot[t];
+                if (lk[0] < 0 && sl == (nb.x >> 2)) lk[0] = t;
+                if (lk[1] < 0 && sl == (nb.y >> 2)) lk[1] = t;
+                if (lk[2] < 0 && sl == (nb.z >> 2)) lk[2] = t;
+            }
+            sh->lnl[j] = make_int4(lk[0], lk[1], lk[2], 0);
+            if (lk[0] >= 0) reinterpret_cast<int *>(&sh->lnl[lk[0]])[nb.x & 3] = j;
+            if (lk[1] >= 0) reinterpret_cast<int *>(&sh->lnl[lk[1]])[nb.y & 3] = j;
+            if (lk[2] >= 0) reinterpret_cast<int *>(&sh->lnl[lk[2]])[nb.z & 3] = j;
+        }
+        if (__any_sync(FULL, bad)) return BW_BAD;
+        __syncwarp();
+        // conflicts of the new triangles
+        unsigned ex = 0, ti = 0;
+        for (int base = base0; base < cnt1; base += 32) {
+            int j = base + w.lane;
+            bool c = false;
+            if (j < cnt1) {
+                int4 v = sh->lv[j];
+                c = conflict(v.x, v.y, v.z, sh->lp[j][0], sh->lp[j][1], sh->lp[j][2], p, q, d.use_filter, &ex, &ti);
+            }
+            C |= (unsigned long long)__ballot_sync(FULL, c) << base;
+        }
+        cnt_add(w, C_EXACT, __reduce_add_sync(FULL, ex));
+        cnt_add(w, C_TIES, __reduce_add_sync(FULL, ti));
+        R.cnt = cnt1;
+    }
+}
+
+// Insert p at q into the staged region by Bowyer-Watson (the insertion Section IV
+// names): the cavity is every triangle whose circumcircle holds q (SoS incircle, the
+// ghost rule for ghosts), tested one staged triangle per lane; it is connected and
+// star-shaped from q, so staging the cavity's neighbours until none is missing gives
+// its whole boundary.  q is joined to every boundary edge; the new triangles reuse the
+// cavity's entries and the two dead entries X0, X1.  tj: a staged triangle holding q.
+__device__ __forceinline__ int bw_insert(Warp w, const Dev &d, Region &R, int p, int2 q, int tj, int X0, int X1,
+                                         int &ncav_out)
+{
+    WarpShared *sh = w.sh;
+    unsigned long long C = 0;
+    {
+        unsigned ex = 0, ti = 0;
+        for (int base = 0; base < R.cnt; base += 32) {
+            int j = base + w.lane;
+            bool c = false;
+            if (j < R.cnt && sh->lslot[j] >= 0) {
+                int4 v = sh->lv[j];
+                c = (v.w & ALIVE) && conflict(v.x, v.y, v.z, sh->lp[j][0], sh->lp[j][1], sh->lp[j][2], p, q,
+                                              d.use_filter, &ex, &ti);
+            }
+            C |= (unsigned long long)__ballot_sync(FULL, c) << base;
+        }
+        cnt_add(w, C_EXACT, __reduce_add_sync(FULL, ex));
+        cnt_add(w, C_TIES, __reduce_add_sync(FULL, ti));
+    }
+    if (!((C >> tj) & 1ull)) return BW_BAD;  // q's triangle always conflicts
+    int g = bw_grow(w, d, R, p, q, C);
+    if (g != BW_OK) return g;
+    const int ncav = __popcll(C);
+    // boundary edges (a -> b, counter-clockwise around the cavity) into S (a), I (b),
+    // L (outer staged ref), LX (coordinates of a)
+    int nbd = 0;
+    for (int base = 0; base < 3 * R.cnt; base += 32) {
+        int idx = base + w.lane;
+        int j = idx / 3, e = idx - 3 * j;
+        int kn = idx < 3 * R.cnt ? ic(sh->lnl[j], e) : -1;
+        bool b = idx < 3 * R.cnt && ((C >> j) & 1ull) && kn >= 0 && !((C >> kn) & 1ull);
+        unsigned bm = __ballot_sync(FULL, b);
+        int pos = nbd + __popc(bm & ((1u << w.lane) - 1u));
+        if (b && pos < KMAX) {
+            int4 v = sh->lv[j];
+            int e1 = e == 2 ? 0 : e + 1, e2 = e == 0 ? 2 : e - 1;
+            sh->S[pos] = ic(v, e1);
+            sh->I[pos] = ic(v, e2);
+            sh->L[pos] = (kn << 2) | (ic(sh->ln[j], e) & 3);
+            sh->LX[pos] = sh->lp[j][e1];
+        }
+        nbd += __popc(bm);
+    }
+    if (nbd != ncav + 2 || nbd > KMAX) return BW_BAD;
+    __syncwarp();
+    // The cavity must be a disk seen from q: each boundary vertex starts and ends one
+    // edge, and every finite boundary edge has q on its inner side.  Only a region that
+    // is not Delaunay (concurrent work not yet certified) can fail this; the caller then
+    // inserts by split and Lawson flips, which need no such property.  Checked for every
+    // edge before anything is written.
+    for (int b0 = 0; b0 < nbd; b0 += 32) {
+        int b = b0 + w.lane;
+        bool bad = false;
+        if (b < nbd) {
+            int a = sh->S[b], bb = sh->I[b], nx = -1, nnx = 0, npv = 0;
+            for (int c = 0; c < nbd; ++c) {
+                if (sh->S[c] == bb) {
+                    nx = c;
+                    ++nnx;
+                }
+                if (sh->I[c] == a) ++npv;
+            }
+            bad = nnx != 1 || npv != 1;
+            if (!bad && a != KDT_GHOST && bb != KDT_GHOST) bad = orient2d(q, sh->LX[b], sh->LX[nx]) <= 0;
+        }
+        if (__any_sync(FULL, bad)) return BW_BAD;
+    }
+    // lane b joins q to boundary edge b; its neighbours are the edges that end at a
+    // (previous) and start at b (next)
+    unsigned long long dmask = 0, vmask = 0;
+    for (int b0 = 0; b0 < nbd; b0 += 32) {
+        int b = b0 + w.lane;
+        int a = 0, bb = 0, ol = 0, nx = -1, pv = -1;
+        int2 pa = make_int2(0, 0);
+        if (b < nbd) {
+            a = sh->S[b];
+            bb = sh->I[b];
+            ol = sh->L[b];
+            pa = sh->LX[b];
+            for (int c = 0; c < nbd; ++c) {
+                if (sh->S[c] == bb) nx = c;
+                if (sh->I[c] == a) pv = c;
+            }
+        }
+        // staged entry of boundary edge c: the c-th cavity triangle, then X0, X1
+        auto entry = [&](int c) -> int {
+            if (c >= ncav) return c == ncav ? X0 : X1;
+            unsigned lo = (unsigned)C, hi = (unsigned)(C >> 32);
+            int nlo = __popc(lo);
+            return c < nlo ? (int)__fns(lo, 0, c + 1) : 32 + (int)__fns(hi, 0, c - nlo + 1);
+        };
+        int x = -1, xn = -1, xp = -1;
+        int2 pb = make_int2(0, 0);
+        if (b < nbd) {
+            x = entry(b);
+            xn = entry(nx);
+            xp = entry(pv);
+            pb = sh->LX[nx];
+        }
+        int sx = b < nbd ? sh->lslot[x] : 0, sxn = b < nbd ? sh->lslot[xn] : 0, sxp = b < nbd ? sh->lslot[xp] : 0;
+        __syncwarp();
+        if (b < nbd) {
+            sh->lv[x] = make_int4(p, a, bb, ALIVE);
+            sh->lp[x][0] = q;
+            sh->lp[x][1] = pa;
+            sh->lp[x][2] = pb;
+            set_nb(sh, x, 0, ol >> 2, gref_of(sh, ol));
+            set_nb(sh, x, 1, xn, (sxn << 2) | 2);
+            set_nb(sh, x, 2, xp, (sxp << 2) | 1);
+            set_nb(sh, ol >> 2, ol & 3, x, (sx << 2) | 0);
+            dmask |= (1ull << x) | (1ull << (ol >> 2));
+            vmask |= 1ull << x;
+        }
+    }
+    dmask |= __shfl_xor_sync(FULL, dmask, 16);
+    dmask |= __shfl_xor_sync(FULL, dmask, 8);
+    dmask |= __shfl_xor_sync(FULL, dmask, 4);
+    dmask |= __shfl_xor_sync(FULL, dmask, 2);
+    dmask |= __shfl_xor_sync(FULL, dmask, 1);
+    vmask |= __shfl_xor_sync(FULL, vmask, 16);
+    vmask |= __shfl_xor_sync(FULL, vmask, 8);
+    vmask |= __shfl_xor_sync(FULL, vmask, 4);
+    vmask |= __shfl_xor_sync(FULL, vmask, 2);
+    vmask |= __shfl_xor_sync(FULL, vmask, 1);
+    R.dirty |= dmask;
+    R.vchg |= vmask;
+    __syncwarp();
+    cnt_add(w, C_INSERTS, 1);
+    cnt_add(w, C_FLIPS, (unsigned)(ncav - 1));  // the Lawson flips of the same insertion
+    ncav_out = ncav;
+    return BW_OK;
+}
+
 // ---- features of a move for the learned proposal and its training rows
 //
 // For an interior p with link v_0..v_{k-1} (counter-clockwise, in L / LX):
@@ -621,157 +855,15 @@ __device__ int move_point(Warp w, const Dev &d, int p, int2 q, int &s0, int &s1,
             if (st == d.stamp) return MV_DEFER;
             return DEV_DUPLICATE;
         }
-        // ---- 3. Bowyer-Watson insertion of q (Section IV names it for insertion): the
-        // cavity is every triangle whose circumcircle holds q (SoS incircle, ghost rule
-        // for ghosts), tested one staged triangle per lane; q is then joined to the
-        // cavity's boundary.  The cavity of a Delaunay triangulation is connected and
-        // star-shaped from q, so a cavity triangle whose neighbour is not staged makes
-        // that neighbour staged (claimed) and tested before the boundary is taken.
+        // ---- 3. Bowyer-Watson insertion of q (Section IV names it for insertion)
         long long tl0 = clock64();
-        unsigned long long C = 0;
-        {
-            unsigned ex = 0, ti = 0;
-            for (int base = 0; base < R.cnt; base += 32) {
-                int j = base + w.lane;
-                bool c = false;
-                if (j < R.cnt && sh->lslot[j] >= 0) {
-                    int4 v = sh->lv[j];
-                    c = (v.w & ALIVE) && conflict(v.x, v.y, v.z, sh->lp[j][0], sh->lp[j][1], sh->lp[j][2], p, q,
-                                                  d.use_filter, &ex, &ti);
-                }
-                C |= (unsigned long long)__ballot_sync(FULL, c) << base;
-            }
-            while (true) {
-                // a (cavity triangle, edge) pair whose neighbour is not staged
-                int gj = -1, ge = 0;
-                for (int base = 0; base < 3 * R.cnt && gj < 0; base += 32) {
-                    int idx = base + w.lane;
-                    int j = idx / 3, e = idx - 3 * j;
-                    bool need = idx < 3 * R.cnt && ((C >> j) & 1ull) && ic(sh->lnl[j], e) < 0;
-                    unsigned bm = __ballot_sync(FULL, need);
-                    if (bm) {
-                        int src = __ffs(bm) - 1;
-                        gj = __shfl_sync(FULL, j, src);
-                        ge = __shfl_sync(FULL, e, src);
-                    }
-                }
-                if (gj < 0) break;
-                int t = ensure_local(w, d, R.cnt, ic(sh->ln[gj], ge) >> 2);
-                if (t < 0) {
-                    write_back(w, d, R);
-                    return MV_GLOBAL;
-                }
-                if (t == R.cnt) ++R.cnt;
-                int4 v = sh->lv[t];
-                if ((v.w & ALIVE) && conflict(v.x, v.y, v.z, sh->lp[t][0], sh->lp[t][1], sh->lp[t][2], p, q,
-                                              d.use_filter, &ex, &ti))
-                    C |= 1ull << t;
-                if (ic(sh->lnl[gj], ge) < 0) {  // never expected: the new triangle is linked
-                    write_back(w, d, R);
-                    return MV_GLOBAL;
-                }
-            }
-            cnt_add(w, C_EXACT, __reduce_add_sync(FULL, ex));
-            cnt_add(w, C_TIES, __reduce_add_sync(FULL, ti));
+        int ncav = 0;
+        int bw = bw_insert(w, d, R, p, q, tj, X0, X1, ncav);
+        if (bw != BW_OK) {
+            // the deletion is written; the insertion continues on the global path
+            write_back(w, d, R);
+            return MV_GLOBAL;
         }
-        const int ncav = __popcll(C);
-        if (!((C >> tj) & 1ull)) {  // q's triangle always conflicts: an inconsistent region
-            release_all(w, d);
-            return DEV_INTERNAL;
-        }
-        // boundary edges (a -> b, counter-clockwise around the cavity) into S (a), I (b),
-        // L (outer staged ref), LX (coordinates of a)
-        int nbd = 0;
-        for (int base = 0; base < 3 * R.cnt; base += 32) {
-            int idx = base + w.lane;
-            int j = idx / 3, e = idx - 3 * j;
-            int kn = idx < 3 * R.cnt ? ic(sh->lnl[j], e) : -1;
-            bool b = idx < 3 * R.cnt && ((C >> j) & 1ull) && kn >= 0 && !((C >> kn) & 1ull);
-            unsigned bm = __ballot_sync(FULL, b);
-            int pos = nbd + __popc(bm & ((1u << w.lane) - 1u));
-            if (b && pos < KMAX) {
-                int4 v = sh->lv[j];
-                int e1 = e == 2 ? 0 : e + 1, e2 = e == 0 ? 2 : e - 1;
-                sh->S[pos] = ic(v, e1);
-                sh->I[pos] = ic(v, e2);
-                sh->L[pos] = (kn << 2) | (ic(sh->ln[j], e) & 3);
-                sh->LX[pos] = sh->lp[j][e1];
-            }
-            nbd += __popc(bm);
-        }
-        if (nbd != ncav + 2 || nbd > KMAX) {
-            release_all(w, d);
-            return DEV_INTERNAL;
-        }
-        __syncwarp();
-        // the new triangles reuse the cavity's entries (ascending) and the two spares;
-        // lane b joins q to boundary edge b, its neighbours are the edges that end at a
-        // (previous) and start at b (next)
-        unsigned long long dmask = 0, vmask = 0;
-        for (int b0 = 0; b0 < nbd; b0 += 32) {
-            int b = b0 + w.lane;
-            int a = 0, bb = 0, ol = 0, nx = -1, pv = -1;
-            int2 pa = make_int2(0, 0);
-            if (b < nbd) {
-                a = sh->S[b];
-                bb = sh->I[b];
-                ol = sh->L[b];
-                pa = sh->LX[b];
-                for (int c = 0; c < nbd; ++c) {
-                    if (sh->S[c] == bb) nx = c;
-                    if (sh->I[c] == a) pv = c;
-                }
-            }
-            // staged entry of boundary edge c: the c-th cavity triangle, then X0, X1
-            auto entry = [&](int c) -> int {
-                if (c >= ncav) return c == ncav ? X0 : X1;
-                unsigned lo = (unsigned)C, hi = (unsigned)(C >> 32);
-                int nlo = __popc(lo);
-                return c < nlo ? (int)__fns(lo, 0, c + 1) : 32 + (int)__fns(hi, 0, c - nlo + 1);
-            };
-            int x = -1, xn = -1, xp = -1;
-            int2 pb = make_int2(0, 0);
-            if (b < nbd) {
-                x = entry(b);
-                xn = nx >= 0 ? entry(nx) : -1;
-                xp = pv >= 0 ? entry(pv) : -1;
-                pb = nx >= 0 ? sh->LX[nx] : pa;
-            }
-            bool bad = b < nbd && (nx < 0 || pv < 0);
-            if (__any_sync(FULL, bad)) {
-                release_all(w, d);
-                return DEV_INTERNAL;
-            }
-            int sx = b < nbd ? sh->lslot[x] : 0, sxn = b < nbd ? sh->lslot[xn] : 0, sxp = b < nbd ? sh->lslot[xp] : 0;
-            __syncwarp();
-            if (b < nbd) {
-                sh->lv[x] = make_int4(p, a, bb, ALIVE);
-                sh->lp[x][0] = q;
-                sh->lp[x][1] = pa;
-                sh->lp[x][2] = pb;
-                set_nb(sh, x, 0, ol >> 2, gref_of(sh, ol));
-                set_nb(sh, x, 1, xn, (sxn << 2) | 2);
-                set_nb(sh, x, 2, xp, (sxp << 2) | 1);
-                set_nb(sh, ol >> 2, ol & 3, x, (sx << 2) | 0);
-                dmask |= (1ull << x) | (1ull << (ol >> 2));
-                vmask |= 1ull << x;
-            }
-        }
-        dmask |= __shfl_xor_sync(FULL, dmask, 16);
-        dmask |= __shfl_xor_sync(FULL, dmask, 8);
-        dmask |= __shfl_xor_sync(FULL, dmask, 4);
-        dmask |= __shfl_xor_sync(FULL, dmask, 2);
-        dmask |= __shfl_xor_sync(FULL, dmask, 1);
-        vmask |= __shfl_xor_sync(FULL, vmask, 16);
-        vmask |= __shfl_xor_sync(FULL, vmask, 8);
-        vmask |= __shfl_xor_sync(FULL, vmask, 4);
-        vmask |= __shfl_xor_sync(FULL, vmask, 2);
-        vmask |= __shfl_xor_sync(FULL, vmask, 1);
-        R.dirty |= dmask;
-        R.vchg |= vmask;
-        __syncwarp();
-        cnt_add(w, C_INSERTS, 1);
-        cnt_add(w, C_FLIPS, (unsigned)(ncav - 1));  // the Lawson flips of the same insertion
         if (learn && j0 >= 0 && d.trace_x) {
             int row = 0;
             if (w.lane == 0) row = atomicAdd(d.trace_count, 1);
@@ -796,6 +888,108 @@ __device__ int move_point(Warp w, const Dev &d, int p, int2 q, int &s0, int &s1,
         write_back(w, d, R, certified);
         cnt_add(w, C_CYC_WB, (unsigned)((clock64() - t3) >> 6));
         return MV_DONE;
+    }
+}
+
+}  // namespace kd
+
+namespace kd {
+
+// Insert p (xy[p] already holds q) by Bowyer-Watson on a staged region: a walk finds
+// a triangle holding q; it and the two spare slots are claimed and staged, the cavity
+// is grown and replaced as in the staged move, certified on the staged copy and
+// written back.  spare0 / spare1: two dead slots the caller owns (a deletion's
+// leftovers, or fresh slots during a build).  Returns 0, 1 = deferred (q lies on a
+// vertex that is still moving in this step), 2 = the cavity outgrew a staged region
+// (the caller uses the global-memory insertion), or an error.
+__device__ __noinline__ int insert_staged(Warp w, const Dev &d, int p, int2 q, int start, int spare0, int spare1,
+                                          bool allow_defer)
+{
+    WarpShared *sh = w.sh;
+    int t = start, walk_fail = 0;
+    for (int attempt = 0;; ++attempt) {
+        if (attempt > d.retry_cap) return DEV_RETRY;
+        if (read_status(d)) return -1;
+        WalkResult wr = walk(w, d, t, q);
+        if (wr.t < 0) {
+            if (++walk_fail > WALK_RESTARTS) return DEV_WALK;
+            // restart from the hint, then from the triangle of a random present point
+            if (attempt & 1) {
+                t = start;
+            } else {
+                int r = w.sh->rlo + (int)(warp_rand(w) % (unsigned)w.sh->rn);
+                t = __shfl_sync(FULL, __ldcg(d.pt_tri + r), 0);
+                if (t < 0) t = start;
+            }
+            backoff(w, attempt);
+            continue;
+        }
+        if (wr.where == W_VERTEX) {
+            int st = __shfl_sync(FULL, __ldcg(d.pt_stamp + wr.vtx), 0);
+            if (allow_defer && st == d.stamp) return 1;
+            return DEV_DUPLICATE;
+        }
+        // claim the triangle and the spares; read the triangle under its claim
+        if (w.lane == 0) {
+            sh->tmp[0] = wr.t;
+            sh->tmp[1] = spare0;
+            sh->tmp[2] = spare1;
+        }
+        __syncwarp();
+        bool ok = claim_list(w, d, sh->tmp, 3);
+        Region R;
+        R.cnt = 3;
+        R.dirty = (1ull << 1) | (1ull << 2);
+        R.vchg = 0;
+        if (ok) {
+            if (w.lane < 3) {
+                int slot = sh->tmp[w.lane];
+                int4 v = make_int4(0, 0, 0, 0), nb = make_int4(-1, -1, -1, 0);
+                int2 z = make_int2(0, 0), p0 = z, p1 = z, p2 = z;
+                if (w.lane == 0) {
+                    v = __ldcg(d.tv + slot);
+                    nb = __ldcg(d.tn + slot);
+                    p0 = v.x >= 0 ? __ldcg(d.xy + v.x) : z;
+                    p1 = v.y >= 0 ? __ldcg(d.xy + v.y) : z;
+                    p2 = v.z >= 0 ? __ldcg(d.xy + v.z) : z;
+                }
+                sh->lslot[w.lane] = slot;
+                sh->lv[w.lane] = v;
+                sh->ln[w.lane] = nb;
+                sh->lnl[w.lane] = make_int4(-1, -1, -1, 0);
+                sh->lp[w.lane][0] = p0;
+                sh->lp[w.lane][1] = p1;
+                sh->lp[w.lane][2] = p2;
+            }
+            __syncwarp();
+            // it must still hold q (a finite triangle) or see q outside its hull edge
+            int e = 0, vt = -1;
+            int r = locate_in(sh, 0, q, &e, &vt);
+            ok = r == 0 || r == 1 || r == 3;
+        }
+        if (!ok) {
+            release_all(w, d);
+            backoff(w, attempt);
+            t = wr.t;
+            continue;
+        }
+        int ncav = 0;
+        int bw = bw_insert(w, d, R, p, q, 0, 1, 2, ncav);
+        if (bw == BW_FULL || bw == BW_BAD) {
+            release_all(w, d);
+            return 2;
+        }
+        if (bw != BW_OK) {
+            release_all(w, d);
+            backoff(w, attempt);
+            t = wr.t;
+            continue;
+        }
+        if (wr.where == W_EDGE) cnt_add(w, C_SPLIT_EDGE, 1);
+        if (wr.where == W_GHOST) cnt_add(w, C_SPLIT_GHOST, 1);
+        bool certified = certify_staged(w, d, R);
+        write_back(w, d, R, certified);
+        return 0;
     }
 }
 
