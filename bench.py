@@ -36,6 +36,27 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 BYTES_PER_UPDATE = 688  # star triangles 32*(k_old+k_new) + back-pointers 16*(k_old+k_new) + coords 8*(k_old+k_new+2), k = 6
+
+# DRAM bytes (read + write) of one k_kinetic launch of the 1e6-point, 4096-move step,
+# from `ncu --set full` (profiles/k_kinetic_c2_1e6.md), valid only for the kernel
+# sources it was taken on (their SHA-256 prefix); reported as null otherwise.
+KINETIC_TRAFFIC = {"sources": "fe9ea2c11b7a0d06", "bytes": 14624000 + 26880, "moves": 4096}
+
+
+def kernel_sources_hash():
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2308_06484_gb300", "csrc", "*.cu*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def kinetic_traffic(moves_per_launch):
+    if kernel_sources_hash() != KINETIC_TRAFFIC["sources"] or moves_per_launch != KINETIC_TRAFFIC["moves"]:
+        return None
+    return KINETIC_TRAFFIC["bytes"]
 METRIC = "moved-point updates/sec (1 GB300, bit-exact) vs plain GPU update and full rebuild"
 WORKLOAD = ("1e6 uniform points on [0,2^24)^2, 64x64 partitions, 4096 moves/step "
             "(1 per partition, 1-8 units R/L/U/D)")
@@ -594,7 +615,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": 12 * m,
                     "d2h_bytes_per_step": 64},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": kinetic_traffic(m),
                          "kernel": "k_kinetic", "kernel_ms": kin_ms, "bytes_per_update": BYTES_PER_UPDATE,
                          "peak_kind": peak_kind},
             "comparators": {
