@@ -106,6 +106,9 @@ struct kdt {
     int *trace_count = nullptr;       // device counter
     float *mlp_part = nullptr;        // per-block partial gradients of k_mlp_grad
     int mlp_part_blocks = 0;
+    // per-warp global scratch of the kinetic launch for deletions of degree > KMAX
+    int *big = nullptr;
+    long long big_warps = 0;
 };
 
 namespace {
@@ -203,6 +206,7 @@ Dev make_dev(kdt *h)
     d.trace_y = h->trace_y;
     d.trace_count = h->trace_count;
     d.trace_cap = h->trace_cap;
+    d.big = h->big;
     return d;
 }
 
@@ -596,6 +600,35 @@ int verify_state(kdt *h, int64_t *bad)
 // copy of the status scalars to the host.  With from_ctl the kernels read m, the
 // stamp and the moves' address from h->ctl, so the sequence can be captured once
 // into a CUDA graph.
+// warps of the kinetic launch
+void kinetic_shape(kdt *h, int *blocks, int *threads)
+{
+    int kblocks = kinetic_blocks(h), kthreads = WPB * 32;
+    if (h->cfg.kinetic_warps > 0) {
+        kblocks = (h->cfg.kinetic_warps + WPB - 1) / WPB;
+        if (h->cfg.kinetic_warps < WPB) kthreads = 32 * h->cfg.kinetic_warps;
+    }
+    *blocks = kblocks;
+    *threads = kthreads;
+}
+
+// The global scratch for deletions of degree above KMAX: BIG_INTS ints per warp of the
+// kinetic launch, allocated before the first step (outside any graph capture).
+int ensure_big(kdt *h)
+{
+    int kb = 0, kt = 0;
+    kinetic_shape(h, &kb, &kt);
+    long long warps = (long long)kb * (kt / 32);
+    if (warps <= h->big_warps) return 0;
+    if (h->big) cudaFree(h->big);
+    h->big = nullptr;
+    h->big_warps = 0;
+    if (cudaMalloc(&h->big, (size_t)warps * BIG_INTS * sizeof(int)) != cudaSuccess) return KDT_ERR_CUDA;
+    h->big_warps = warps;
+    h->gen++;  // a captured step graph holds the old Dev
+    return 0;
+}
+
 int enqueue_step(kdt *h, cudaStream_t st, const Dev &d, const int3 *mp, int mi, bool from_ctl)
 {
     int cap = from_ctl ? h->mcap : mi;
@@ -606,16 +639,14 @@ int enqueue_step(kdt *h, cudaStream_t st, const Dev &d, const int3 *mp, int mi, 
     CK(cudaMemcpyAsync(h->d_moff, h->h_moff, (h->ninst + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(h->scal, 0, S_NUM * sizeof(int), st));
     CK(cudaMemsetAsync(h->head, 0xff, (size_t)h->ncells * sizeof(int), st));  // empty lists
+    CK(cudaMemsetAsync(h->deferred, 0xff, (size_t)h->mcap * sizeof(int4), st));  // empty entries (-1)
     k_intake_link<<<thread_grid(h, cap, 256), 256, 0, st>>>(d, mp, mi, I, h->cfg.domain_bits, h->head, h->next,
                                                             h->old_xy, h->gmoves);
     // inside a capture an event record must be an external node to keep its timestamp
     unsigned evflags = from_ctl ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (h->cfg.timing) CK(cudaEventRecordWithFlags(h->ev0, st, evflags));
-    int kblocks = kinetic_blocks(h), kthreads = WPB * 32;
-    if (h->cfg.kinetic_warps > 0) {
-        kblocks = (h->cfg.kinetic_warps + WPB - 1) / WPB;
-        if (h->cfg.kinetic_warps < WPB) kthreads = 32 * h->cfg.kinetic_warps;
-    }
+    int kblocks = 0, kthreads = 0;
+    kinetic_shape(h, &kblocks, &kthreads);
     k_kinetic<<<kblocks, kthreads, 0, st>>>(d, h->gmoves, h->head, h->next, I, h->ncells, h->wpp, h->deferred,
                                             h->scal + S_DEFER, h->mcap, h->viol, h->viol_cap);
     if (h->cfg.timing) CK(cudaEventRecordWithFlags(h->ev1, st, evflags));
@@ -746,6 +777,9 @@ int step_impl(kdt *h, const kdt_move *moves, const int64_t *moff, int64_t m)
     }
     rc = autotune_before(h);
     if (rc) return rc;
+    rc = ensure_big(h);
+    if (rc) return rc;
+    d = make_dev(h);
     bool timed = h->cfg.timing || (h->tune_idx >= 0 && !h->tune_done);
     if (h->cfg.use_graph) {
         // one graph launch per step
@@ -981,6 +1015,7 @@ int kdt_destroy(kdt *h)
     if (h->mlp_w) cudaFree(h->mlp_w);
     if (h->trace_count) cudaFree(h->trace_count);
     if (h->mlp_part) cudaFree(h->mlp_part);
+    if (h->big) cudaFree(h->big);
     if (h->hscal) cudaFreeHost(h->hscal);
     if (h->ctl) cudaFree(h->ctl);
     if (h->hctl) cudaFreeHost(h->hctl);

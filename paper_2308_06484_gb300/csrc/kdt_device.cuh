@@ -48,6 +48,17 @@ enum DevStatus : int {
     DEV_CAPACITY = 9,     // a work list overflowed
 };
 
+// Results of the insertion routines besides 0 (done) and a DevStatus error (> 0):
+// negative, so they never collide with a status.
+constexpr int INS_DEFER = -10;   // q lies on a vertex still moving in this step
+constexpr int INS_GLOBAL = -11;  // (staged insertion) the caller must use the global path
+constexpr int DEL_BUSY = -12;    // (deletion) claims kept failing: nothing was changed
+// Claim losses after which a move stops competing and is left to the end of the step,
+// when no other warp runs: an operation with a large footprint (a high-degree point,
+// whose star shares long thin triangles with many neighbours) can otherwise keep
+// losing against the small ones around it.
+constexpr int DEFER_AFTER = 16;
+
 enum Counter : int {
     C_FLIPS = 0, C_RETRIES, C_WALK_STEPS, C_EXACT, C_TIES, C_DEFERRED, C_VIOL, C_FIX_FLIPS,
     C_DEG_DEL, C_STACK_DROP, C_SPLIT_EDGE, C_SPLIT_GHOST, C_DELETES, C_INSERTS, C_FLIP_TESTS,
@@ -85,6 +96,23 @@ struct Dev {
     int *trace_y;               // (slot, cavity size) per row
     int *trace_count;           // rows written (may exceed trace_cap: later rows dropped)
     int trace_cap;
+    // per-warp global scratch for the deletion of a point of degree above KMAX
+    int *big;                   // BIG_INTS ints per warp of the kinetic launch (null: none)
+};
+
+constexpr int KBIG = 1024;                  // largest degree the global deletion handles
+constexpr int BIG_INTS = 9 * KBIG + 64;     // S, I, L, ON, T, LX (2), claims (2 KBIG + 64)
+
+// The star arrays of a deletion: in the warp's shared block (degree <= KMAX) or in its
+// global scratch (degree <= KBIG).
+struct Star {
+    int *S;    // star triangle slots, counter-clockwise around p
+    int *I;    // index of p in each
+    int *L;    // link vertices
+    int *ON;   // outer refs across the link edges
+    int *T;    // scratch (the ring's slots for the claims)
+    int2 *LX;  // link coordinates
+    int cap;
 };
 
 struct WarpShared {
@@ -110,7 +138,36 @@ struct WarpShared {
     int ncl;               // claims held (cl[0 .. ncl-1])
     int rlo, rn;           // the points of the instance being worked on
     unsigned earbad;       // ears found invalid in the current clipping round
+    int *clp;              // the claim list in use: cl, or a large list in global memory
+    int clcap;             // its capacity
+    int *big;              // this warp's global scratch for stars above KMAX (null: none)
 };
+
+__device__ __forceinline__ Star star_shared(WarpShared *sh)
+{
+    Star A;
+    A.S = sh->S;
+    A.I = sh->I;
+    A.L = sh->L;
+    A.ON = sh->ON;
+    A.T = sh->tmp;
+    A.LX = sh->LX;
+    A.cap = KMAX;
+    return A;
+}
+
+__device__ __forceinline__ Star star_big(int *b)
+{
+    Star A;
+    A.S = b;
+    A.I = b + KBIG;
+    A.L = b + 2 * KBIG;
+    A.ON = b + 3 * KBIG;
+    A.T = b + 4 * KBIG;
+    A.LX = reinterpret_cast<int2 *>(b + 5 * KBIG);
+    A.cap = KBIG;
+    return A;
+}
 
 // A warp's handle, passed by value: its shared block, its lane and its claim token.
 // Everything mutable lives in the shared block, so no per-lane copy of warp state
@@ -283,7 +340,8 @@ __device__ __forceinline__ int csr_find(const int *off, int cnt, int x)
 __device__ __forceinline__ bool claim_lanes(Warp w, const Dev &d, int mine, int m)
 {
     bool ok = true, added = false;
-    if (w.lane < m && mine >= 0) {
+    if (w.lane < m && mine >= d.cap) ok = false;  // never a slot: fail the claim, touch nothing
+    if (w.lane < m && mine >= 0 && mine < d.cap) {
         int old = atomicCAS(&d.tn[mine].w, 0, w.token);
         ok = (old == 0) || (old == w.token);
         added = (old == 0);
@@ -291,7 +349,7 @@ __device__ __forceinline__ bool claim_lanes(Warp w, const Dev &d, int mine, int 
     unsigned am = __ballot_sync(FULL, added);
     unsigned om = __ballot_sync(FULL, ok);
     int held = w.sh->ncl;
-    if (added) w.sh->cl[held + __popc(am & ((1u << w.lane) - 1))] = mine;
+    if (added) w.sh->clp[held + __popc(am & ((1u << w.lane) - 1))] = mine;
     __syncwarp();
     if (w.lane == 0) w.sh->ncl = held + __popc(am);
     __threadfence();
@@ -299,7 +357,7 @@ __device__ __forceinline__ bool claim_lanes(Warp w, const Dev &d, int mine, int 
     return om == FULL;
 }
 
-// Claim a list held in shared memory (any length; the caller keeps ncl + m <= MAXC).
+// Claim a list (any length; the caller keeps ncl + m <= the claim list's capacity).
 __device__ __forceinline__ bool claim_list(Warp w, const Dev &d, const int *list, int m)
 {
     bool all = true;
@@ -317,7 +375,7 @@ __device__ __forceinline__ void release_all(Warp w, const Dev &d)
     __syncwarp();
     if (w.lane == 0) {
         __threadfence();  // our writes are visible before any owner word clears
-        for (int i = 0; i < w.sh->ncl; ++i) atomicExch(&d.tn[w.sh->cl[i]].w, 0);
+        for (int i = 0; i < w.sh->ncl; ++i) atomicExch(&d.tn[w.sh->clp[i]].w, 0);
         w.sh->ncl = 0;
     }
     __syncwarp();
@@ -696,12 +754,13 @@ __device__ __noinline__ int insert_outside(Warp w, const Dev &d, int p, int2 q, 
 
 // Insert point p (its coordinates already in xy[p]) starting the walk at `start`.
 // spare0 / spare1 are two dead slots owned by the caller (a deletion's leftovers or
-// fresh slots during a build).  Returns 0, 1 = deferred (p lands on a vertex that is
+// fresh slots during a build).  Returns 0, INS_DEFER (p lands on a vertex that is
 // still moving in this step), or a DevStatus error.
 __device__ __noinline__ int insert_point(Warp w, const Dev &d, int p, int2 q, int start, int spare0, int spare1,
                             bool allow_defer)
 {
     WarpShared *sh = w.sh;
+    if (spare0 < 0 || spare0 >= d.cap || spare1 < 0 || spare1 >= d.cap) return DEV_INTERNAL;
     int t = start, walk_fail = 0;
     for (int attempt = 0;; ++attempt) {
         if (attempt > d.retry_cap) return DEV_RETRY;
@@ -723,7 +782,7 @@ __device__ __noinline__ int insert_point(Warp w, const Dev &d, int p, int2 q, in
         }
         if (where == W_VERTEX) {
             int st = __shfl_sync(FULL, __ldcg(d.pt_stamp + vtx), 0);
-            if (allow_defer && st == d.stamp) return 1;
+            if (allow_defer && st == d.stamp) return INS_DEFER;
             return DEV_DUPLICATE;
         }
         if (where == W_GHOST) {
@@ -835,15 +894,15 @@ __device__ __noinline__ int insert_point(Warp w, const Dev &d, int p, int2 q, in
 
 // ------------------------------------------------------------------ deletion
 
-// Gather the star of p counter-clockwise from pt_tri[p] into S/I/L/ON.  Returns k,
+// Gather the star of p counter-clockwise from pt_tri[p] into A (S/I/L/ON).  Returns k,
 // or -1 when the reads are inconsistent (another warp is working there), -2 when
-// the degree exceeds KMAX.  The star is walked in both directions at once (the
+// the degree exceeds A.cap.  The star is walked in both directions at once (the
 // next triangle counter-clockwise and the next clockwise are loaded in the same
 // round trip), so a star of k triangles costs about k/2 dependent loads.  The
 // clockwise part is kept at the top of the arrays and moved into place at the end.
-__device__ int gather_star(Warp w, const Dev &d, int p)
+__device__ int gather_star(Warp w, const Dev &d, int p, Star A)
 {
-    WarpShared *sh = w.sh;
+    const int cap = A.cap;
     int t0 = __ldcg(d.pt_tri + p);
     t0 = __shfl_sync(FULL, t0, 0);
     if (t0 < 0 || t0 >= d.cap) return -1;
@@ -859,12 +918,12 @@ __device__ int gather_star(Warp w, const Dev &d, int p)
         if (!(fv.w & ALIVE)) return -1;
         int If = fv.x == p ? 0 : (fv.y == p ? 1 : (fv.z == p ? 2 : -1));
         if (If < 0) return -1;
-        if (nf + nbk + 1 > KMAX) return -2;
+        if (nf + nbk + 1 > cap) return -2;
         if (w.lane == 0) {
-            sh->S[nf] = tf;
-            sh->I[nf] = If;
-            sh->L[nf] = comp(fv, (If + 1) % 3);
-            sh->ON[nf] = comp(fn, If);
+            A.S[nf] = tf;
+            A.I[nf] = If;
+            A.L[nf] = comp(fv, (If + 1) % 3);
+            A.ON[nf] = comp(fn, If);
         }
         ++nf;
         int fnext = comp(fn, (If + 1) % 3) >> 2;
@@ -875,8 +934,6 @@ __device__ int gather_star(Warp w, const Dev &d, int p)
             if (fnext < 0 || fnext >= d.cap || fprev < 0 || fprev >= d.cap) return -1;
             if (fnext == fprev) {    // two triangles
                 tf = fnext;
-                tb = -1;
-                // load it as a forward triangle in the next round, then stop
                 int4 y = make_int4(0, 0, 0, 0);
                 if (w.lane < 2) y = (w.lane & 1) ? __ldcg(d.tn + tf) : __ldcg(d.tv + tf);
                 int4 v2 = bcast4(y, 0), n2 = bcast4(y, 1);
@@ -884,10 +941,10 @@ __device__ int gather_star(Warp w, const Dev &d, int p)
                 int I2 = v2.x == p ? 0 : (v2.y == p ? 1 : (v2.z == p ? 2 : -1));
                 if (I2 < 0) return -1;
                 if (w.lane == 0) {
-                    sh->S[nf] = tf;
-                    sh->I[nf] = I2;
-                    sh->L[nf] = comp(v2, (I2 + 1) % 3);
-                    sh->ON[nf] = comp(n2, I2);
+                    A.S[nf] = tf;
+                    A.I[nf] = I2;
+                    A.L[nf] = comp(v2, (I2 + 1) % 3);
+                    A.ON[nf] = comp(n2, I2);
                 }
                 ++nf;
                 break;
@@ -901,13 +958,13 @@ __device__ int gather_star(Warp w, const Dev &d, int p)
         if (!(bv.w & ALIVE)) return -1;
         int Ib = bv.x == p ? 0 : (bv.y == p ? 1 : (bv.z == p ? 2 : -1));
         if (Ib < 0) return -1;
-        if (nf + nbk + 1 > KMAX) return -2;
+        if (nf + nbk + 1 > cap) return -2;
         if (w.lane == 0) {
-            int at = KMAX - 1 - nbk;
-            sh->S[at] = tb;
-            sh->I[at] = Ib;
-            sh->L[at] = comp(bv, (Ib + 1) % 3);
-            sh->ON[at] = comp(bn, Ib);
+            int at = cap - 1 - nbk;
+            A.S[at] = tb;
+            A.I[at] = Ib;
+            A.L[at] = comp(bv, (Ib + 1) % 3);
+            A.ON[at] = comp(bn, Ib);
         }
         ++nbk;
         int bprev = comp(bn, (Ib + 2) % 3) >> 2;
@@ -924,50 +981,34 @@ __device__ int gather_star(Warp w, const Dev &d, int p)
         tb = bprev;
     }
     __syncwarp();
-    // move the clockwise part (top of the arrays, last found first) after the rest
-    int k = nf + nbk;
-    int src = KMAX - nbk + w.lane;
-    int cS = 0, cI = 0, cL = 0, cO = 0;
-    bool mv = w.lane < nbk;
-    if (mv) {
-        cS = sh->S[src];
-        cI = sh->I[src];
-        cL = sh->L[src];
-        cO = sh->ON[src];
+    // move the clockwise part (top of the arrays, last found first) after the rest, in
+    // chunks of 32 in increasing order (a destination never lies above its source)
+    for (int c0 = 0; c0 < nbk; c0 += 32) {
+        int i = c0 + w.lane;
+        int src = cap - nbk + i;
+        bool mv = i < nbk;
+        int cS = 0, cI = 0, cL = 0, cO = 0;
+        if (mv) {
+            cS = A.S[src];
+            cI = A.I[src];
+            cL = A.L[src];
+            cO = A.ON[src];
+        }
+        __syncwarp();
+        if (mv) {
+            A.S[nf + i] = cS;
+            A.I[nf + i] = cI;
+            A.L[nf + i] = cL;
+            A.ON[nf + i] = cO;
+        }
+        __syncwarp();
     }
-    __syncwarp();
-    if (mv) {
-        sh->S[nf + w.lane] = cS;
-        sh->I[nf + w.lane] = cI;
-        sh->L[nf + w.lane] = cL;
-        sh->ON[nf + w.lane] = cO;
-    }
-    __syncwarp();
-    return k;
+    return nf + nbk;
 }
 
-// Is ear (L[i], L[i+1], L[i+2]) of the current link polygon valid?  Finite ears must
-// be counter-clockwise; no remaining link vertex may conflict with the ear
-// (SoS incircle, or the ghost rule for ears through infinity).
-__device__ bool ear_valid(const int *EL, const int2 *EX, int m, int i, const Dev &d,
-                          unsigned *exact_calls, unsigned *ties)
+__device__ __forceinline__ int gather_star(Warp w, const Dev &d, int p)
 {
-    int i1 = (i + 1) % m, i2 = (i + 2) % m;
-    int x = EL[i], y = EL[i1], z = EL[i2];
-    int2 px = EX[i], py = EX[i1], pz = EX[i2];
-    int g = x == KDT_GHOST ? 0 : (y == KDT_GHOST ? 1 : (z == KDT_GHOST ? 2 : -1));
-    if (g < 0 && orient2d(px, py, pz) <= 0) return false;
-    int2 gu = g == 0 ? py : (g == 1 ? pz : px);
-    int2 gv = g == 0 ? pz : (g == 1 ? px : py);
-    for (int j = 0; j < m; ++j) {
-        if (j == i || j == i1 || j == i2) continue;
-        int wv = EL[j];
-        if (wv == KDT_GHOST) continue;
-        bool c = g >= 0 ? ghost_conflict(gu, gv, EX[j])
-                        : incircle_sos(x, y, z, wv, px, py, pz, EX[j], d.use_filter, exact_calls, ties) > 0;
-        if (c) return false;
-    }
-    return true;
+    return gather_star(w, d, p, star_shared(w.sh));
 }
 
 // One test of ear i (L[i], L[i+1], L[i+2]) of the current link polygon of m vertices:
@@ -993,69 +1034,75 @@ __device__ __forceinline__ bool ear_test_fails(const int *EL, const int2 *EX, in
     return incircle_sos(x, y, z, wv, px, py, pz, EX[j], d.use_filter, exact_calls, ties) > 0;
 }
 
-// Delete p: claim its star and the ring of outer neighbours, re-triangulate the
-// star-shaped hole by Delaunay ears (the simple deletion the paper prefers, Section
-// IV), release.  On success the two slots the hole no longer needs are returned
+// Delete p on the global-memory path: claim its star and the ring of outer
+// neighbours, re-triangulate the star-shaped hole by Delaunay ears (the simple
+// deletion the paper prefers, Section IV) written straight to the store, release.
+// The star lives in A: the warp's shared block, or its global scratch for a degree
+// above KMAX (the claims then go to the scratch's claim list).  Each round tests every
+// (ear, remaining vertex) pair on its own lane and clips all valid, pairwise
+// non-adjacent ears.  On success the two slots the hole no longer needs are returned
 // dead in spare0/spare1 and `hint` is a new triangle next to p's old position.
-__device__ __noinline__ int delete_point(Warp w, const Dev &d, int p, int &spare0, int &spare1, int &hint)
+__device__ __noinline__ int delete_point_in(Warp w, const Dev &d, int p, int &spare0, int &spare1, int &hint,
+                                            Star A, bool may_give_up)
 {
-    WarpShared *sh = w.sh;
+    int busy = 0;
     for (int attempt = 0;; ++attempt) {
         if (attempt > d.retry_cap) return DEV_RETRY;
         if (read_status(d)) return -1;
         // an unclaimed walk around p can run round a transient loop while another warp
         // is writing p's triangles: treat every failed gather as contention, and report
         // a real degree overflow only when it persists for the whole retry budget
-        int k = gather_star(w, d, p);
+        int k = gather_star(w, d, p, A);
         if (k == -2 && attempt == d.retry_cap) return DEV_DEGREE;
         if (k < 3) {
             backoff(w, attempt);
             continue;
         }
-        // claim the star and the outer ring (outer refs > star refs in the list)
-        if (w.lane == 0)
-            for (int i = 0; i < k; ++i) sh->tmp[i] = sh->ON[i] >> 2;
+        // claim the star and the outer ring
+        for (int i = w.lane; i < k; i += 32) A.T[i] = A.ON[i] >> 2;
         __syncwarp();
-        bool ok = claim_list(w, d, sh->S, k);
-        if (ok) ok = claim_list(w, d, sh->tmp, k);
+        bool ok = claim_list(w, d, A.S, k);
+        if (ok) ok = claim_list(w, d, A.T, k);
         if (ok) {
             // validate the gathered star under the claims (one parallel pass)
             bool good = true;
             for (int i = w.lane; i < k; i += 32) {
-                int4 v = __ldcg(d.tv + sh->S[i]);
-                int4 nb = __ldcg(d.tn + sh->S[i]);
-                int I = sh->I[i];
-                good = good && (v.w & ALIVE) && comp(v, I) == p && comp(v, (I + 1) % 3) == sh->L[i] &&
-                       comp(nb, I) == sh->ON[i] && (comp(nb, (I + 1) % 3) >> 2) == sh->S[(i + 1) % k];
+                int4 v = __ldcg(d.tv + A.S[i]);
+                int4 nb = __ldcg(d.tn + A.S[i]);
+                int I = A.I[i];
+                good = good && (v.w & ALIVE) && comp(v, I) == p && comp(v, (I + 1) % 3) == A.L[i] &&
+                       comp(nb, I) == A.ON[i] && (comp(nb, (I + 1) % 3) >> 2) == A.S[i + 1 == k ? 0 : i + 1];
             }
             ok = __all_sync(FULL, good);
         }
         if (!ok) {
             release_all(w, d);
+            if (may_give_up && ++busy >= DEFER_AFTER) return DEL_BUSY;
             backoff(w, attempt);
             continue;
         }
         // link coordinates
         for (int i = w.lane; i < k; i += 32) {
-            int lv = sh->L[i];
-            sh->LX[i] = lv >= 0 ? __ldcg(d.xy + lv) : make_int2(0, 0);
+            int lv = A.L[i];
+            A.LX[i] = lv >= 0 ? __ldcg(d.xy + lv) : make_int2(0, 0);
         }
         __syncwarp();
         // degenerate check: a hull vertex whose finite link is collinear and whose
         // ring has no finite triangle would leave only collinear points behind
         int gpos = -1;
         for (int i = 0; i < k; ++i)
-            if (sh->L[i] == KDT_GHOST) gpos = i;
+            if (A.L[i] == KDT_GHOST) gpos = i;
         if (gpos >= 0) {
             int f0 = (gpos + 1) % k, f1 = (gpos + 2) % k;
             bool col = true;
-            for (int i = 0; i < k; ++i)
-                if (i != gpos && orient2d(sh->LX[f0], sh->LX[f1], sh->LX[i]) != 0) col = false;
+            for (int i = w.lane; i < k; i += 32)
+                if (i != gpos && orient2d(A.LX[f0], A.LX[f1], A.LX[i]) != 0) col = false;
+            col = __all_sync(FULL, col);
             if (col) {
                 bool finite_ring = false;
                 for (int i = w.lane; i < k; i += 32) {
-                    if (sh->L[i] == KDT_GHOST || sh->L[(i + 1) % k] == KDT_GHOST) continue;
-                    int4 ov = __ldcg(d.tv + (sh->ON[i] >> 2));
+                    if (A.L[i] == KDT_GHOST || A.L[i + 1 == k ? 0 : i + 1] == KDT_GHOST) continue;
+                    int4 ov = __ldcg(d.tv + (A.ON[i] >> 2));
                     if (ov.x != KDT_GHOST && ov.y != KDT_GHOST && ov.z != KDT_GHOST) finite_ring = true;
                 }
                 if (!__any_sync(FULL, finite_ring)) {
@@ -1064,87 +1111,108 @@ __device__ __noinline__ int delete_point(Warp w, const Dev &d, int p, int &spare
                 }
             }
         }
-        // ear clipping over the link polygon; EL/EO/EX live in L/ON/LX
+        // ear clipping over the link polygon (L, ON, LX); T holds per-ear flags and I
+        // the clipped ears of a round
         int m = k, newc = 0;
         while (m > 3) {
-            int chosen = -1;
+            for (int i = w.lane; i < m; i += 32) A.T[i] = 0;
+            __syncwarp();
             unsigned ex = 0, ti = 0;
-            for (int base = 0; base < m && chosen < 0; base += 32) {
-                int i = base + w.lane;
-                bool v = i < m && ear_valid(sh->L, sh->LX, m, i, d, &ex, &ti);
-                unsigned bm = __ballot_sync(FULL, v);
-                if (bm) chosen = base + __ffs(bm) - 1;
+            const long long npair = (long long)m * (m - 2);
+            for (long long base = 0; base < npair; base += 32) {
+                long long idx = base + w.lane;
+                if (idx < npair) {
+                    int i = (int)(idx / (m - 2)), t = (int)(idx - (long long)i * (m - 2));
+                    if (ear_test_fails(A.L, A.LX, m, i, t, d, &ex, &ti)) A.T[i] = 1;
+                }
             }
+            __syncwarp();
             cnt_add(w, C_EXACT, __reduce_add_sync(FULL, ex));
             cnt_add(w, C_TIES, __reduce_add_sync(FULL, ti));
-            if (chosen < 0) {
+            // lane 0 picks every valid ear whose neighbours are not picked (each valid
+            // ear is a triangle of the hole's unique triangulation), keeping >= 3 vertices;
+            // T[i] becomes "picked"
+            int ns = 0;
+            if (w.lane == 0) {
+                bool prev = false, first = false;
+                for (int i = 0; i < m; ++i) {
+                    bool pick = A.T[i] == 0 && !prev && !(i == m - 1 && first) && ns < m - 3;
+                    A.T[i] = pick ? 1 : 0;
+                    if (pick) {
+                        A.I[ns++] = i;
+                        if (i == 0) first = true;
+                    }
+                    prev = pick;
+                }
+            }
+            ns = __shfl_sync(FULL, ns, 0);
+            __syncwarp();
+            if (ns == 0) {
                 // cannot happen for a valid star; leave the store to the fallback
                 release_all(w, d);
                 return DEV_INTERNAL;
             }
-            int i = chosen, i1 = (i + 1) % m, i2 = (i + 2) % m;
-            int X = sh->S[newc++];
-            if (w.lane == 0) {
-                d.tv[X] = make_int4(sh->L[i], sh->L[i1], sh->L[i2], ALIVE);
-                d.tn[X] = make_int4(sh->ON[i1], -1, sh->ON[i], w.token);
-                backptr(d, sh->ON[i1], (X << 2) | 0);
-                backptr(d, sh->ON[i], (X << 2) | 2);
-                if (sh->L[i] >= 0) d.pt_tri[sh->L[i]] = X;
-                if (sh->L[i1] >= 0) d.pt_tri[sh->L[i1]] = X;
-                if (sh->L[i2] >= 0) d.pt_tri[sh->L[i2]] = X;
+            // lane r writes the r-th clipped ear into slot S[newc + r]
+            for (int r = w.lane; r < ns; r += 32) {
+                int i = A.I[r], i1 = i + 1 == m ? 0 : i + 1, i2 = i1 + 1 == m ? 0 : i1 + 1;
+                int X = A.S[newc + r];
+                int Li = A.L[i], Li1 = A.L[i1], Li2 = A.L[i2];
+                int oi = A.ON[i], oi1 = A.ON[i1];
+                d.tv[X] = make_int4(Li, Li1, Li2, ALIVE);
+                d.tn[X] = make_int4(oi1, -1, oi, w.token);
+                backptr(d, oi1, (X << 2) | 0);
+                backptr(d, oi, (X << 2) | 2);
+                if (Li >= 0) d.pt_tri[Li] = X;
+                if (Li1 >= 0) d.pt_tri[Li1] = X;
+                if (Li2 >= 0) d.pt_tri[Li2] = X;
                 dirty_push(d, X);
-                sh->ON[i] = (X << 2) | 1;
+                A.ON[i] = (X << 2) | 1;
             }
             __syncwarp();
-            // remove element i1 (shift the tail down by one)
-            int lv = 0, onv = 0;
-            int2 xv = make_int2(0, 0);
-            int j = w.lane;
-            bool mv = j >= i1 && j < m - 1;
-            if (mv) {
-                lv = sh->L[j + 1];
-                onv = sh->ON[j + 1];
-                xv = sh->LX[j + 1];
+            // drop the clipped ears' middle vertices (vertex j goes when ear j-1 was
+            // clipped), in chunks of 32 in increasing order
+            int kept = 0;
+            for (int c0 = 0; c0 < m; c0 += 32) {
+                int j = c0 + w.lane;
+                bool keep = j < m && A.T[j == 0 ? m - 1 : j - 1] == 0;
+                unsigned km = __ballot_sync(FULL, keep);
+                int nj = kept + __popc(km & ((1u << w.lane) - 1u));
+                int lv = 0, onv = 0;
+                int2 xv = make_int2(0, 0);
+                if (keep) {
+                    lv = A.L[j];
+                    onv = A.ON[j];
+                    xv = A.LX[j];
+                }
+                __syncwarp();
+                if (keep) {
+                    A.L[nj] = lv;
+                    A.ON[nj] = onv;
+                    A.LX[nj] = xv;
+                }
+                __syncwarp();
+                kept += __popc(km);
             }
-            bool mv2 = j + 32 >= i1 && j + 32 < m - 1;
-            int lv2 = 0, onv2 = 0;
-            int2 xv2 = make_int2(0, 0);
-            if (mv2) {
-                lv2 = sh->L[j + 33];
-                onv2 = sh->ON[j + 33];
-                xv2 = sh->LX[j + 33];
-            }
-            __syncwarp();
-            if (mv) {
-                sh->L[j] = lv;
-                sh->ON[j] = onv;
-                sh->LX[j] = xv;
-            }
-            if (mv2) {
-                sh->L[j + 32] = lv2;
-                sh->ON[j + 32] = onv2;
-                sh->LX[j + 32] = xv2;
-            }
-            __syncwarp();
-            --m;
+            m -= ns;
+            newc += ns;
         }
         {
-            int X = sh->S[newc++];
+            int X = A.S[newc++];
             if (w.lane == 0) {
-                d.tv[X] = make_int4(sh->L[0], sh->L[1], sh->L[2], ALIVE);
-                d.tn[X] = make_int4(sh->ON[1], sh->ON[2], sh->ON[0], w.token);
-                backptr(d, sh->ON[1], (X << 2) | 0);
-                backptr(d, sh->ON[2], (X << 2) | 1);
-                backptr(d, sh->ON[0], (X << 2) | 2);
+                d.tv[X] = make_int4(A.L[0], A.L[1], A.L[2], ALIVE);
+                d.tn[X] = make_int4(A.ON[1], A.ON[2], A.ON[0], w.token);
+                backptr(d, A.ON[1], (X << 2) | 0);
+                backptr(d, A.ON[2], (X << 2) | 1);
+                backptr(d, A.ON[0], (X << 2) | 2);
                 for (int c = 0; c < 3; ++c)
-                    if (sh->L[c] >= 0) d.pt_tri[sh->L[c]] = X;
+                    if (A.L[c] >= 0) d.pt_tri[A.L[c]] = X;
                 dirty_push(d, X);
             }
         }
         // the two slots left over
-        spare0 = sh->S[k - 2];
-        spare1 = sh->S[k - 1];
-        hint = sh->S[0];
+        spare0 = A.S[k - 2];
+        spare1 = A.S[k - 1];
+        hint = A.S[0];
         if (w.lane == 0) {
             d.tv[spare0].w = 0;
             d.tv[spare1].w = 0;
@@ -1155,6 +1223,133 @@ __device__ __noinline__ int delete_point(Warp w, const Dev &d, int p, int &spare
         release_all(w, d);
         return DEV_OK;
     }
+}
+
+__device__ __forceinline__ int delete_point(Warp w, const Dev &d, int p, int &spare0, int &spare1, int &hint,
+                                            bool may_give_up = false)
+{
+    return delete_point_in(w, d, p, spare0, spare1, hint, star_shared(w.sh), may_give_up);
+}
+
+// Move p to q without changing any triangle, when that keeps the triangulation
+// Delaunay: the triangles around p stay counter-clockwise and every edge of p's star
+// (the spokes p-v_i and the link edges v_i-v_{i+1}) stays locally Delaunay with p at q;
+// edges not in the star keep their triangles and their vertices' positions, so by the
+// Delaunay lemma nothing else can change.  Exact SoS predicates decide, as everywhere.
+// Only for an interior p.  Returns 1 (moved), 0 (not so: the caller deletes and
+// inserts), or a DevStatus error.  The star and its claims live in A and the current
+// claim list (the caller provides room for 2k claims).
+__device__ __noinline__ int move_in_place(Warp w, const Dev &d, int p, int2 q, Star A)
+{
+    for (int attempt = 0;; ++attempt) {
+        if (attempt > d.retry_cap) return DEV_RETRY;
+        if (read_status(d)) return -1;
+        int k = gather_star(w, d, p, A);
+        if (k == -2) return 0;  // beyond even the scratch: leave it to the deletion
+        if (k < 3) {
+            backoff(w, attempt);
+            continue;
+        }
+        for (int i = w.lane; i < k; i += 32) A.T[i] = A.ON[i] >> 2;
+        __syncwarp();
+        bool ok = claim_list(w, d, A.S, k);
+        if (ok) ok = claim_list(w, d, A.T, k);
+        if (ok) {
+            bool good = true;
+            for (int i = w.lane; i < k; i += 32) {
+                int4 v = __ldcg(d.tv + A.S[i]);
+                int4 nb = __ldcg(d.tn + A.S[i]);
+                int I = A.I[i];
+                good = good && (v.w & ALIVE) && comp(v, I) == p && comp(v, (I + 1) % 3) == A.L[i] &&
+                       comp(nb, I) == A.ON[i] && (comp(nb, (I + 1) % 3) >> 2) == A.S[i + 1 == k ? 0 : i + 1];
+            }
+            ok = __all_sync(FULL, good);
+        }
+        if (!ok) {
+            release_all(w, d);
+            backoff(w, attempt);
+            continue;
+        }
+        bool hull = false;
+        for (int i = w.lane; i < k; i += 32) {
+            int lv = A.L[i];
+            hull = hull || lv == KDT_GHOST;
+            A.LX[i] = lv >= 0 ? __ldcg(d.xy + lv) : make_int2(0, 0);
+        }
+        if (__any_sync(FULL, hull)) {
+            release_all(w, d);
+            return 0;
+        }
+        __syncwarp();
+        bool stays = true;
+        unsigned ex = 0, ti = 0;
+        for (int i = w.lane; i < k; i += 32) {
+            int i0 = i == 0 ? k - 1 : i - 1, i1 = i + 1 == k ? 0 : i + 1;
+            int a = A.L[i0], b = A.L[i], c = A.L[i1];
+            int2 pa = A.LX[i0], pb = A.LX[i], pc = A.LX[i1];
+            // triangle (p, b, c) counter-clockwise with p at q
+            stays = stays && orient2d(q, pb, pc) > 0;
+            // spoke p-b: c outside the circle of (p, a, b)
+            stays = stays && !conflict(p, a, b, q, pa, pb, c, pc, d.use_filter, &ex, &ti);
+            // link edge b-c: the apex across it outside the circle of (p, b, c)
+            int ref = A.ON[i];
+            int4 ov = __ldcg(d.tv + (ref >> 2));
+            int r = comp(ov, ref & 3);
+            int2 pr = r >= 0 ? __ldcg(d.xy + r) : make_int2(0, 0);
+            stays = stays && !conflict(p, b, c, q, pb, pc, r, pr, d.use_filter, &ex, &ti);
+        }
+        cnt_add(w, C_EXACT, __reduce_add_sync(FULL, ex));
+        cnt_add(w, C_TIES, __reduce_add_sync(FULL, ti));
+        stays = __all_sync(FULL, stays);
+        if (stays && w.lane == 0) {
+            d.xy[p] = q;
+            __threadfence();
+        }
+        __syncwarp();
+        release_all(w, d);
+        return stays ? 1 : 0;
+    }
+}
+
+// Delete a point of degree above KMAX with the star in the warp's global scratch (and
+// its claims in the scratch's claim list).  DEV_DEGREE when there is no scratch.
+__device__ __noinline__ int delete_point_big(Warp w, const Dev &d, int p, int &spare0, int &spare1, int &hint)
+{
+    if (!w.sh->big) return DEV_DEGREE;
+    __syncwarp();
+    if (w.lane == 0) {
+        w.sh->clp = w.sh->big + 7 * KBIG;
+        w.sh->clcap = 2 * KBIG + 64;
+    }
+    __syncwarp();
+    int rc = delete_point_in(w, d, p, spare0, spare1, hint, star_big(w.sh->big), false);
+    __syncwarp();
+    if (w.lane == 0) {
+        w.sh->clp = w.sh->cl;
+        w.sh->clcap = MAXC;
+    }
+    __syncwarp();
+    return rc;
+}
+
+// move_in_place with the star in the warp's global scratch (degree above KMAX).
+__device__ __noinline__ int move_in_place_big(Warp w, const Dev &d, int p, int2 q)
+{
+    if (!w.sh->big) return 0;
+    __syncwarp();
+    if (w.lane == 0) {
+        w.sh->clp = w.sh->big + 7 * KBIG;
+        w.sh->clcap = 2 * KBIG + 64;
+    }
+    __syncwarp();
+    int rc = move_in_place(w, d, p, q, star_big(w.sh->big));
+    __syncwarp();
+    if (w.lane == 0) {
+        w.sh->clp = w.sh->cl;
+        w.sh->clcap = MAXC;
+    }
+    __syncwarp();
+    return rc;
 }
 
 }  // namespace kd

@@ -17,7 +17,7 @@ constexpr int DEV_DUP_ID = 10;  // a move id repeated within one step (found at 
 enum Slot : int {
     S_STATUS = 0, S_DIRTY = 1, S_VIOL = 2, S_TRIS = 3, S_DEFER = 4, S_THIRD = 5,
     S_MINX = 6, S_MINY = 7, S_MAXX = 8, S_MAXY = 9, S_TOTAL = 10, S_BAD = 11, S_ALIVE = 12,
-    S_WRAPS = 13, S_FAILPT = 14, S_DONE = 15, S_CERTPEND = 16, S_TICKET = 17, S_NUM = 20
+    S_WRAPS = 13, S_FAILPT = 14, S_DONE = 15, S_CERTPEND = 16, S_TICKET = 17, S_DNEXT = 18, S_NUM = 20
 };
 
 // Instance tables (one instance for kdt_build; many for kdt_build_batch).  Every
@@ -50,6 +50,9 @@ __device__ __forceinline__ Warp make_warp(WarpShared *sh, int token, unsigned se
         sh->cyc_max = 0;
         sh->rlo = d.rlo;
         sh->rn = d.rn;
+        sh->clp = sh->cl;
+        sh->clcap = MAXC;
+        sh->big = nullptr;
     }
     __syncwarp();
     return w;
@@ -219,8 +222,120 @@ __global__ void k_intake_link(Dev d, const int3 *moves, int m, Inst I, int bits,
 // message.  A point whose target is still occupied by a point that has not moved
 // yet is deferred.  The last warp to finish inserts the deferred points and
 // certifies the triangles written on the global-memory path.
-__device__ void step_tail(Warp w, const Dev &d, Inst I, const int4 *deferred, const int *defer_count, int defer_cap,
+__device__ void step_tail(Warp w, const Dev &d, Inst I, int4 *deferred, int *defer_count, int defer_cap,
                           int *viol, int viol_cap);
+
+// Entries of the deferred list: (p, s0, s1, hint) = an insertion left to the end of the
+// step (s0 >= 0); (p, DQ_MOVE - pass, qx, qy) = a whole move left for later, pass
+// counting how often it was left; DQ_DONE once a warp has taken it.
+constexpr int DQ_MOVE = -2, DQ_DONE = -100, DQ_PASSES = 3;
+
+// Append an entry.  The list is cleared to -1 before every step and the point id is
+// written last (after a fence), so a warp that takes a reserved but unwritten entry
+// sees -1 there and waits for it (read_deferred).
+__device__ __forceinline__ void push_deferred(Warp w, const Dev &d, int4 *deferred, int *defer_count, int defer_cap,
+                                              int4 e)
+{
+    if (w.lane == 0) {
+        int pos = atomicAdd(defer_count, 1);
+        if (pos < defer_cap) {
+            int *f = reinterpret_cast<int *>(deferred + pos);
+            f[1] = e.y;
+            f[2] = e.z;
+            f[3] = e.w;
+            __threadfence();
+            atomicExch(f, e.x);
+        } else {
+            atomicCAS(d.status, 0, DEV_CAPACITY);
+        }
+    }
+    cnt_add(w, C_DEFERRED, 1);
+    __syncwarp();
+}
+
+// Entry j once its writer has published it (bounded wait); x = -1 if it never appeared.
+__device__ __forceinline__ int4 read_deferred(Warp w, const int4 *deferred, int j)
+{
+    const int *f = reinterpret_cast<const int *>(deferred + j);
+    int4 e = make_int4(-1, 0, 0, 0);
+    if (w.lane == 0) {
+        int x = -1;
+        for (int spin = 0; spin < (1 << 20); ++spin) {
+            x = __ldcg(f);
+            if (x != -1) break;
+        }
+        __threadfence();
+        e = make_int4(x, __ldcg(f + 1), __ldcg(f + 2), __ldcg(f + 3));
+    }
+    return bcast4(e, 0);
+}
+
+// One move of p to q (Fig. 4: Delete, Update, Insert): the staged move, else the
+// global-memory path.  may_give_up: a move whose claims keep failing, or whose point
+// has a degree above KMAX, returns MV_BIG untouched; otherwise claims are retried and a
+// high-degree point is deleted with its star in the warp's global scratch.  rc: 0, MV_BIG, INS_DEFER / MV_DEFER (p deleted and placed, its
+// insertion left to the end of the step with spares s0, s1 and hint), or an error.
+struct MoveOut {
+    int rc, s0, s1, hint;
+};
+
+__device__ __noinline__ MoveOut run_move(Warp w, const Dev &d, int p, int2 q, bool may_give_up)
+{
+    MoveOut o;
+    int s0 = -1, s1 = -1, hint = -1;
+    long long c0 = clock64();
+    int rc = move_point(w, d, p, q, s0, s1, hint, may_give_up);
+    if (rc == MV_BIG && !may_give_up) {
+        // a degree above KMAX: the star goes to the warp's global scratch.  A short
+        // move that leaves every triangle of the star valid and Delaunay only changes
+        // p's position; otherwise p is deleted and inserted again.
+        rc = move_in_place_big(w, d, p, q);
+        if (rc == 1) {
+            rc = 0;
+        } else if (rc == 0) {
+            rc = delete_point_big(w, d, p, s0, s1, hint);
+            if (rc == 0) rc = MV_GLOBAL;
+        }
+    }
+    if (rc == MV_GLOBAL) {
+        cnt_add(w, C_MV_GLOBAL, 1);
+        if (w.lane == 0) {
+            d.xy[p] = q;
+            __threadfence();
+        }
+        __syncwarp();
+        rc = insert_staged(w, d, p, q, hint, s0, s1, true);
+        if (rc == INS_GLOBAL) rc = insert_point(w, d, p, q, hint, s0, s1, true);
+    }
+    unsigned cy = (unsigned)((clock64() - c0) >> 6);
+    cnt_add(w, C_CYC_MOVE, cy);
+    if (w.lane == 0 && cy > w.sh->cyc_max) w.sh->cyc_max = cy;
+    o.rc = rc;
+    o.s0 = s0;
+    o.s1 = s1;
+    o.hint = hint;
+    return o;
+}
+
+// Record a move's outcome: deferred work goes to the list, an error to the status.
+// Returns false when the warp must stop.
+__device__ __forceinline__ bool settle_move(Warp w, const Dev &d, int rc, int p, int2 q, int pass, int s0, int s1,
+                                            int hint, int4 *deferred, int *defer_count, int defer_cap)
+{
+    if (rc == MV_BIG) {
+        push_deferred(w, d, deferred, defer_count, defer_cap, make_int4(p, DQ_MOVE - pass, q.x, q.y));
+        return true;
+    }
+    if (rc == MV_DEFER || rc == INS_DEFER) {
+        push_deferred(w, d, deferred, defer_count, defer_cap, make_int4(p, s0, s1, hint));
+        return true;
+    }
+    if (rc) {
+        if (rc > 0 && w.lane == 0 && atomicCAS(d.status, 0, rc) == 0) d.status[S_FAILPT] = p;
+        return false;
+    }
+    return true;
+}
 
 __global__ void __launch_bounds__(WPB * 32, 7) k_kinetic(Dev dp, const int3 *moves, const int *head, const int *next,
                                                          Inst I, int ncells, int wpp, int4 *deferred,
@@ -232,8 +347,11 @@ __global__ void __launch_bounds__(WPB * 32, 7) k_kinetic(Dev dp, const int3 *mov
     int gw = blockIdx.x * (blockDim.x >> 5) + wib;
     int nw = gridDim.x * (blockDim.x >> 5);
     Warp w = make_warp(&shs[wib], gw + 1, gw + 17 * d.stamp, d);
+    if (w.lane == 0 && d.big) w.sh->big = d.big + (size_t)gw * BIG_INTS;
+    __syncwarp();
     const int items = ncells * wpp;
-    while (true) {
+    bool run = true;
+    while (run) {
         // persistent warps pull (partition, share) work items from a ticket
         int t = 0;
         if (w.lane == 0) t = atomicAdd(d.status + S_TICKET, 1);
@@ -245,7 +363,10 @@ __global__ void __launch_bounds__(WPB * 32, 7) k_kinetic(Dev dp, const int3 *mov
         int i = __shfl_sync(FULL, __ldcg(head + c), 0);
         int k = -1;
         while (i >= 0) {
-            if (read_status(d)) break;
+            if (read_status(d)) {
+                run = false;
+                break;
+            }
             if (++k % wpp != sub) {
                 i = __shfl_sync(FULL, __ldcg(next + i), 0);
                 continue;
@@ -253,39 +374,48 @@ __global__ void __launch_bounds__(WPB * 32, 7) k_kinetic(Dev dp, const int3 *mov
             int3 mv = moves[i];
             int p = mv.x;
             int2 q = make_int2(mv.y, mv.z);
-            int s0 = -1, s1 = -1, hint = -1;
-            long long c0 = clock64();
-            // Delete + Update + Insert of Fig. 4 as one staged operation
-            int rc = move_point(w, d, p, q, s0, s1, hint);
-            if (rc == MV_GLOBAL) {
-                cnt_add(w, C_MV_GLOBAL, 1);
-                if (w.lane == 0) {
-                    d.xy[p] = q;
-                    __threadfence();
-                }
-                __syncwarp();
-                rc = insert_staged(w, d, p, q, hint, s0, s1, true);
-                if (rc == 2) rc = insert_point(w, d, p, q, hint, s0, s1, true);
-            }
-            {
-                unsigned cy = (unsigned)((clock64() - c0) >> 6);
-                cnt_add(w, C_CYC_MOVE, cy);
-                if (w.lane == 0 && cy > w.sh->cyc_max) w.sh->cyc_max = cy;
-            }
-            if (rc == MV_DEFER || rc == 1) {
-                if (w.lane == 0) {
-                    int pos = atomicAdd(defer_count, 1);
-                    if (pos < defer_cap) deferred[pos] = make_int4(p, s0, s1, hint);
-                    else atomicCAS(d.status, 0, DEV_CAPACITY);
-                }
-                cnt_add(w, C_DEFERRED, 1);
-                __syncwarp();
-            } else if (rc) {
-                if (rc > 0 && w.lane == 0 && atomicCAS(d.status, 0, rc) == 0) d.status[S_FAILPT] = p;
+            MoveOut o = run_move(w, d, p, q, true);
+            if (!settle_move(w, d, o.rc, p, q, 0, o.s0, o.s1, o.hint, deferred, defer_count, defer_cap)) {
+                run = false;
                 break;
             }
             i = __shfl_sync(FULL, __ldcg(next + i), 0);
         }
+    }
+    // then drain the whole moves left so far, in parallel with the warps still busy: each
+    // may be left again (DQ_PASSES times) before it runs without giving up
+    while (run) {
+        if (read_status(d)) break;
+        int j = -1;
+        if (w.lane == 0) {
+            int nx = __ldcg(d.status + S_DNEXT);
+            while (true) {
+                int cnt = min(__ldcg(defer_count), defer_cap);
+                if (nx >= cnt) break;
+                int prev = atomicCAS(d.status + S_DNEXT, nx, nx + 1);
+                if (prev == nx) {
+                    j = nx;
+                    break;
+                }
+                nx = prev;
+            }
+        }
+        j = __shfl_sync(FULL, j, 0);
+        if (j < 0) break;
+        int4 e = read_deferred(w, deferred, j);
+        if (e.x < 0) continue;  // not published in time: the last warp takes it
+        // an insertion (for the end), a taken entry, or a move left too often (the
+        // last warp runs those when nothing else competes)
+        if (e.y > DQ_MOVE || e.y <= DQ_DONE || DQ_MOVE - e.y >= DQ_PASSES) continue;
+        if (w.lane == 0) deferred[j].y = DQ_DONE;
+        __syncwarp();
+        int pass = DQ_MOVE - e.y + 1;
+        int p = e.x;
+        int2 q = make_int2(e.z, e.w);
+        int inst = I.ninst > 1 ? csr_find(I.pofs, I.ninst + 1, p) : 0;
+        set_instance(w, I.pofs[inst], I.pofs[inst + 1] - I.pofs[inst]);
+        MoveOut o = run_move(w, d, p, q, true);
+        if (!settle_move(w, d, o.rc, p, q, pass, o.s0, o.s1, o.hint, deferred, defer_count, defer_cap)) break;
     }
     // the last warp to finish does the tail work
     int done = 0;
@@ -366,23 +496,44 @@ __device__ void certify_one(const Dev &d, int t, int *viol, int *viol_count, int
 // Tail of a step (one warp, after every other warp finished): insert the deferred
 // points, then certify the triangles written on the global-memory path (the staged
 // path certified its own).  A long dirty list is left to the host.
-__device__ void step_tail(Warp w, const Dev &d, Inst I, const int4 *deferred, const int *defer_count, int defer_cap,
+__device__ void step_tail(Warp w, const Dev &d, Inst I, int4 *deferred, int *defer_count, int defer_cap,
                           int *viol, int viol_cap)
 {
     if (read_status(d)) return;
     int cnt = __shfl_sync(FULL, __ldcg(defer_count), 0);
     if (cnt > defer_cap) cnt = defer_cap;
+    // whole moves not taken yet (left by the last warps), without giving up; an
+    // insertion onto a point still to be inserted is deferred again
+    for (int j = 0; j < min(__shfl_sync(FULL, __ldcg(defer_count), 0), defer_cap); ++j) {
+        if (read_status(d)) return;
+        int4 e = read_deferred(w, deferred, j);
+        if (e.x < 0) continue;
+        if (e.y > DQ_MOVE || e.y <= DQ_DONE) continue;
+        if (w.lane == 0) deferred[j].y = DQ_DONE;
+        __syncwarp();
+        int p = e.x;
+        int2 q = make_int2(e.z, e.w);
+        int inst = I.ninst > 1 ? csr_find(I.pofs, I.ninst + 1, p) : 0;
+        set_instance(w, I.pofs[inst], I.pofs[inst + 1] - I.pofs[inst]);
+        MoveOut o = run_move(w, d, p, q, false);
+        if (o.rc == MV_BIG) o.rc = DEV_INTERNAL;  // never returned without giving up
+        if (!settle_move(w, d, o.rc, p, q, DQ_PASSES, o.s0, o.s1, o.hint, deferred, defer_count, defer_cap)) return;
+    }
+    __threadfence();
+    cnt = __shfl_sync(FULL, __ldcg(defer_count), 0);
+    if (cnt > defer_cap) cnt = defer_cap;
     for (int j = 0; j < cnt; ++j) {
         if (read_status(d)) return;
-        int4 e = deferred[j];
+        int4 e = read_deferred(w, deferred, j);
+        if (e.x < 0 || e.y < 0) continue;  // whole moves (done above)
         int2 q = __ldcg(d.xy + e.x);
         q = bcast2(q, 0);
         int inst = I.ninst > 1 ? csr_find(I.pofs, I.ninst + 1, e.x) : 0;
         set_instance(w, I.pofs[inst], I.pofs[inst + 1] - I.pofs[inst]);
         int rc = insert_staged(w, d, e.x, q, e.w, e.y, e.z, false);
-        if (rc == 2) rc = insert_point(w, d, e.x, q, e.w, e.y, e.z, false);
+        if (rc == INS_GLOBAL) rc = insert_point(w, d, e.x, q, e.w, e.y, e.z, false);
         if (rc) {
-            if (rc > 0) set_status(d, rc);
+            if (rc > 0 && w.lane == 0 && atomicCAS(d.status, 0, rc) == 0) d.status[S_FAILPT] = e.x;
             return;
         }
     }
@@ -578,7 +729,7 @@ __global__ void __launch_bounds__(WPB * 32) k_insert_level(Dev dp, const int *or
         }
         int2 q = d.xy[v];
         int rc = insert_staged(w, d, v, q, start, s, s + 1, false);
-        if (rc == 2) rc = insert_point(w, d, v, q, start, s, s + 1, false);
+        if (rc == INS_GLOBAL) rc = insert_point(w, d, v, q, start, s, s + 1, false);
         if (rc) {
             if (rc > 0) set_status(d, rc);
             break;

@@ -31,7 +31,11 @@
 namespace kd {
 
 // outcome of move_point
-enum MoveResult : int { MV_DONE = 0, MV_DEFER = 1, MV_GLOBAL = 2, MV_ABORT = -1 };
+// (0, negative: none of them a DevStatus, which are all positive)
+// MV_BIG: p's degree is above what the shared arrays hold (KMAX), or its claims kept
+// failing; nothing was done, the move is left to the end of the step, when no other
+// warp competes for claims.
+enum MoveResult : int { MV_DONE = 0, MV_DEFER = -20, MV_GLOBAL = -21, MV_BIG = -22, MV_ABORT = -1 };
 
 struct Region {
     int cnt;                   // staged triangles
@@ -77,7 +81,7 @@ __device__ __noinline__ int ensure_local(Warp w, const Dev &d, int cnt, int slot
     WarpShared *sh = w.sh;
     int j = local_find(sh, cnt, slot);
     if (j >= 0) return j;
-    if (cnt >= LM || w.sh->ncl >= MAXC || slot < 0 || slot >= d.cap) return -1;
+    if (cnt >= LM || w.sh->ncl >= w.sh->clcap || slot < 0 || slot >= d.cap) return -1;
     int mine = w.lane == 0 ? slot : -1;
     if (!claim_lanes(w, d, mine, 1)) return -1;
     int4 v, nb;
@@ -260,7 +264,7 @@ __device__ __forceinline__ int bw_grow(Warp w, const Dev &d, Region &R, int p, i
         if (mine2 < 0 || mine2 >= d.cap) keep2 = false;
         unsigned k1 = __ballot_sync(FULL, keep), k2 = __ballot_sync(FULL, keep2);
         const int nu = __popc(k1) + __popc(k2);
-        if (R.cnt + nu > LM || w.sh->ncl + nu > MAXC) return BW_FULL;
+        if (R.cnt + nu > LM || w.sh->ncl + nu > w.sh->clcap) return BW_FULL;
         __syncwarp();
         if (keep) need[__popc(k1 & ((1u << w.lane) - 1u))] = mine;
         if (keep2) need[__popc(k1) + __popc(k2 & ((1u << w.lane) - 1u))] = mine2;
@@ -535,9 +539,10 @@ __device__ __forceinline__ int hole_rank(const WarpShared *sh, const int *L0, in
 // deletion is written back and the caller inserts p at q with insert_point starting
 // at `hint` with the spares (s0, s1); on MV_DEFER likewise but q is still occupied by
 // a point that moves later in this step.
-__device__ int move_point(Warp w, const Dev &d, int p, int2 q, int &s0, int &s1, int &hint)
+__device__ int move_point(Warp w, const Dev &d, int p, int2 q, int &s0, int &s1, int &hint, bool may_give_up = true)
 {
     WarpShared *sh = w.sh;
+    int claim_fail = 0;
     for (int attempt = 0;; ++attempt) {
         if (attempt > d.retry_cap) return DEV_RETRY;
         if (read_status(d)) return MV_ABORT;
@@ -545,11 +550,14 @@ __device__ int move_point(Warp w, const Dev &d, int p, int2 q, int &s0, int &s1,
         int k = gather_star(w, d, p);
         long long t1 = clock64();
         cnt_add(w, C_CYC_GATHER, (unsigned)((t1 - t0) >> 6));
+        if (k == -2 && w.sh->big) return MV_BIG;
         if (k == -2 && attempt == d.retry_cap) return DEV_DEGREE;
         if (k < 3 || 2 * k + 8 > LM) {
             if (k >= 3) {
-                // a star too large to stage: take the plain global path
-                int rc = delete_point(w, d, p, s0, s1, hint);
+                // a star too large to stage: take the plain global path (or leave the
+                // whole move to the end of the step when its claims keep failing)
+                int rc = delete_point(w, d, p, s0, s1, hint, may_give_up && w.sh->big != nullptr);
+                if (rc == DEL_BUSY) return MV_BIG;
                 return rc ? rc : MV_GLOBAL;
             }
             backoff(w, attempt);
@@ -560,19 +568,24 @@ __device__ int move_point(Warp w, const Dev &d, int p, int2 q, int &s0, int &s1,
         R.cnt = 2 * k;
         R.dirty = 0;
         R.vchg = 0;
+        // (an unclaimed gather can read a neighbour word another warp holds and has not
+        // finished, e.g. -1: such a slot is kept out of range and fails validation)
+        bool inrange = true;
         for (int i = w.lane; i < 2 * k; i += 32) {
             int slot = i < k ? sh->S[i] : (sh->ON[i - k] >> 2);
-            sh->lslot[i] = slot;
-            sh->lv[i] = __ldcg(d.tv + slot);
-            sh->ln[i] = __ldcg(d.tn + slot);
+            bool in = slot >= 0 && slot < d.cap;
+            inrange = inrange && in;
+            sh->lslot[i] = in ? slot : -1;
+            sh->lv[i] = in ? __ldcg(d.tv + slot) : make_int4(0, 0, 0, 0);
+            sh->ln[i] = in ? __ldcg(d.tn + slot) : make_int4(-1, -1, -1, 0);
         }
         __syncwarp();
-        bool ok = claim_list(w, d, sh->lslot, 2 * k);
+        bool ok = __all_sync(FULL, inrange) && claim_list(w, d, sh->lslot, 2 * k);
         if (ok) {
             // validate under the claims and load every vertex's coordinates (one pass)
             bool good = true;
             for (int i = w.lane; i < 2 * k; i += 32) {
-                int slot = sh->lslot[i];
+                int slot = sh->lslot[i];  // in range (checked above)
                 int4 v = __ldcg(d.tv + slot), nb = __ldcg(d.tn + slot);
                 int4 v0 = sh->lv[i], n0 = sh->ln[i];
                 good = good && v.x == v0.x && v.y == v0.y && v.z == v0.z && v.w == v0.w && nb.x == n0.x &&
@@ -591,6 +604,7 @@ __device__ int move_point(Warp w, const Dev &d, int p, int2 q, int &s0, int &s1,
         }
         if (!ok) {
             release_all(w, d);
+            if (may_give_up && w.sh->big && ++claim_fail >= DEFER_AFTER) return MV_BIG;
             backoff(w, attempt);
             continue;
         }
@@ -899,14 +913,16 @@ namespace kd {
 // a triangle holding q; it and the two spare slots are claimed and staged, the cavity
 // is grown and replaced as in the staged move, certified on the staged copy and
 // written back.  spare0 / spare1: two dead slots the caller owns (a deletion's
-// leftovers, or fresh slots during a build).  Returns 0, 1 = deferred (q lies on a
-// vertex that is still moving in this step), 2 = the cavity outgrew a staged region
-// (the caller uses the global-memory insertion), or an error.
+// leftovers, or fresh slots during a build).  Returns 0, INS_DEFER (q lies on a
+// vertex that is still moving in this step), INS_GLOBAL (the cavity outgrew a staged
+// region, or the region is not Delaunay: the caller uses the global-memory
+// insertion), or a DevStatus error.
 __device__ __noinline__ int insert_staged(Warp w, const Dev &d, int p, int2 q, int start, int spare0, int spare1,
                                           bool allow_defer)
 {
     WarpShared *sh = w.sh;
-    int t = start, walk_fail = 0;
+    if (spare0 < 0 || spare0 >= d.cap || spare1 < 0 || spare1 >= d.cap) return DEV_INTERNAL;
+    int t = start, walk_fail = 0, cavity_fail = 0;
     for (int attempt = 0;; ++attempt) {
         if (attempt > d.retry_cap) return DEV_RETRY;
         if (read_status(d)) return -1;
@@ -926,7 +942,7 @@ __device__ __noinline__ int insert_staged(Warp w, const Dev &d, int p, int2 q, i
         }
         if (wr.where == W_VERTEX) {
             int st = __shfl_sync(FULL, __ldcg(d.pt_stamp + wr.vtx), 0);
-            if (allow_defer && st == d.stamp) return 1;
+            if (allow_defer && st == d.stamp) return INS_DEFER;
             return DEV_DUPLICATE;
         }
         // claim the triangle and the spares; read the triangle under its claim
@@ -977,10 +993,15 @@ __device__ __noinline__ int insert_staged(Warp w, const Dev &d, int p, int2 q, i
         int bw = bw_insert(w, d, R, p, q, 0, 1, 2, ncav);
         if (bw == BW_FULL || bw == BW_BAD) {
             release_all(w, d);
-            return 2;
+            return INS_GLOBAL;
         }
         if (bw != BW_OK) {
+            // a cavity claim lost a race.  A large cavity (a point beside long, thin
+            // triangles whose circles are huge) overlaps many other operations and can
+            // keep losing; after a few losses the insertion by split and Lawson flips,
+            // which claims a few triangles at a time, takes over.
             release_all(w, d);
+            if (++cavity_fail >= 4) return INS_GLOBAL;
             backoff(w, attempt);
             t = wr.t;
             continue;
