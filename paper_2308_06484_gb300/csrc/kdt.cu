@@ -206,7 +206,7 @@ Dev make_dev(kdt *h)
     d.trace_y = h->trace_y;
     d.trace_count = h->trace_count;
     d.trace_cap = h->trace_cap;
-    d.big = h->big;
+    d.big = nullptr;  // set for the kinetic launch only (enqueue_step)
     return d;
 }
 
@@ -647,7 +647,9 @@ int enqueue_step(kdt *h, cudaStream_t st, const Dev &d, const int3 *mp, int mi, 
     if (h->cfg.timing) CK(cudaEventRecordWithFlags(h->ev0, st, evflags));
     int kblocks = 0, kthreads = 0;
     kinetic_shape(h, &kblocks, &kthreads);
-    k_kinetic<<<kblocks, kthreads, 0, st>>>(d, h->gmoves, h->head, h->next, I, h->ncells, h->wpp, h->deferred,
+    Dev dk = d;
+    dk.big = h->big;
+    k_kinetic<<<kblocks, kthreads, 0, st>>>(dk, h->gmoves, h->head, h->next, I, h->ncells, h->wpp, h->deferred,
                                             h->scal + S_DEFER, h->mcap, h->viol, h->viol_cap);
     if (h->cfg.timing) CK(cudaEventRecordWithFlags(h->ev1, st, evflags));
     CK(cudaGetLastError());

@@ -96,8 +96,9 @@ struct Dev {
     int *trace_y;               // (slot, cavity size) per row
     int *trace_count;           // rows written (may exceed trace_cap: later rows dropped)
     int trace_cap;
-    // per-warp global scratch for the deletion of a point of degree above KMAX
-    int *big;                   // BIG_INTS ints per warp of the kinetic launch (null: none)
+    // per-warp global scratch for the deletion of a point of degree above KMAX: set for
+    // the kinetic launch only (BIG_INTS ints per warp of that launch), else null
+    int *big;
 };
 
 constexpr int KBIG = 1024;                  // largest degree the global deletion handles
@@ -138,9 +139,7 @@ struct WarpShared {
     int ncl;               // claims held (cl[0 .. ncl-1])
     int rlo, rn;           // the points of the instance being worked on
     unsigned earbad;       // ears found invalid in the current clipping round
-    int *clp;              // the claim list in use: cl, or a large list in global memory
-    int clcap;             // its capacity
-    int *big;              // this warp's global scratch for stars above KMAX (null: none)
+    int clbig;             // claims go to the warp's global scratch (a large star) instead of cl
 };
 
 __device__ __forceinline__ Star star_shared(WarpShared *sh)
@@ -182,6 +181,23 @@ __device__ __forceinline__ void cnt_add(const Warp w, int i, unsigned v)
 {
     if (w.lane == 0) w.sh->cnt[i] += v;
 }
+
+// This warp's global scratch for stars above KMAX (only the kinetic launch has one;
+// BIG_INTS ints per warp of the launch), or null.
+__device__ __forceinline__ int *warp_big(const Dev &d)
+{
+    if (!d.big) return nullptr;
+    size_t gw = (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    return d.big + gw * BIG_INTS;
+}
+
+// The claim list in use and its capacity.
+__device__ __forceinline__ int *claim_list_of(const Warp &w, const Dev &d)
+{
+    return w.sh->clbig ? warp_big(d) + 7 * KBIG : w.sh->cl;
+}
+
+__device__ __forceinline__ int claim_cap(const Warp &w) { return w.sh->clbig ? 2 * KBIG + 64 : MAXC; }
 
 // next value of the warp's random state (uniform across the warp)
 __device__ __forceinline__ unsigned warp_rand(const Warp w)
@@ -279,7 +295,7 @@ __device__ __forceinline__ void dirty_push(const Dev &d, int t)
 
 __device__ __forceinline__ void backoff(Warp w, int attempt)
 {
-    unsigned lim = 32u << (attempt < 10 ? attempt : 10);  // up to ~33 us
+    unsigned lim = 32u << (attempt < 7 ? attempt : 7);  // up to ~4 us
     unsigned ns = 16 + (warp_rand(w) % lim);
     if (w.lane == 0) __nanosleep(ns);
     __syncwarp();
@@ -349,7 +365,7 @@ __device__ __forceinline__ bool claim_lanes(Warp w, const Dev &d, int mine, int 
     unsigned am = __ballot_sync(FULL, added);
     unsigned om = __ballot_sync(FULL, ok);
     int held = w.sh->ncl;
-    if (added) w.sh->clp[held + __popc(am & ((1u << w.lane) - 1))] = mine;
+    if (added) claim_list_of(w, d)[held + __popc(am & ((1u << w.lane) - 1))] = mine;
     __syncwarp();
     if (w.lane == 0) w.sh->ncl = held + __popc(am);
     __threadfence();
@@ -375,7 +391,8 @@ __device__ __forceinline__ void release_all(Warp w, const Dev &d)
     __syncwarp();
     if (w.lane == 0) {
         __threadfence();  // our writes are visible before any owner word clears
-        for (int i = 0; i < w.sh->ncl; ++i) atomicExch(&d.tn[w.sh->clp[i]].w, 0);
+        const int *cl = claim_list_of(w, d);
+        for (int i = 0; i < w.sh->ncl; ++i) atomicExch(&d.tn[cl[i]].w, 0);
         w.sh->ncl = 0;
     }
     __syncwarp();
@@ -900,7 +917,7 @@ __device__ __noinline__ int insert_point(Warp w, const Dev &d, int p, int2 q, in
 // next triangle counter-clockwise and the next clockwise are loaded in the same
 // round trip), so a star of k triangles costs about k/2 dependent loads.  The
 // clockwise part is kept at the top of the arrays and moved into place at the end.
-__device__ int gather_star(Warp w, const Dev &d, int p, Star A)
+__device__ __noinline__ int gather_star(Warp w, const Dev &d, int p, Star A)
 {
     const int cap = A.cap;
     int t0 = __ldcg(d.pt_tri + p);
@@ -1006,9 +1023,104 @@ __device__ int gather_star(Warp w, const Dev &d, int p, Star A)
     return nf + nbk;
 }
 
+// The same walk with the star in the warp's shared block (degree <= KMAX), written with
+// direct shared-memory accesses: this is the hot path of every staged move.
 __device__ __forceinline__ int gather_star(Warp w, const Dev &d, int p)
 {
-    return gather_star(w, d, p, star_shared(w.sh));
+    WarpShared *sh = w.sh;
+    int t0 = __ldcg(d.pt_tri + p);
+    t0 = __shfl_sync(FULL, t0, 0);
+    if (t0 < 0 || t0 >= d.cap) return -1;
+    int nf = 0, nbk = 0;
+    int tf = t0, tb = -1;
+    while (true) {
+        int4 x = make_int4(0, 0, 0, 0);
+        int tl = w.lane < 2 ? tf : (w.lane < 4 ? tb : -1);
+        if (tl >= 0 && tl < d.cap) x = (w.lane & 1) ? __ldcg(d.tn + tl) : __ldcg(d.tv + tl);
+        int4 fv = bcast4(x, 0), fn = bcast4(x, 1), bv = bcast4(x, 2), bn = bcast4(x, 3);
+        if (!(fv.w & ALIVE)) return -1;
+        int If = fv.x == p ? 0 : (fv.y == p ? 1 : (fv.z == p ? 2 : -1));
+        if (If < 0) return -1;
+        if (nf + nbk + 1 > KMAX) return -2;
+        if (w.lane == 0) {
+            sh->S[nf] = tf;
+            sh->I[nf] = If;
+            sh->L[nf] = comp(fv, (If + 1) % 3);
+            sh->ON[nf] = comp(fn, If);
+        }
+        ++nf;
+        int fnext = comp(fn, (If + 1) % 3) >> 2;
+        if (tb < 0) {
+            int fprev = comp(fn, (If + 2) % 3) >> 2;
+            if (fnext == t0) break;
+            if (fnext < 0 || fnext >= d.cap || fprev < 0 || fprev >= d.cap) return -1;
+            if (fnext == fprev) {
+                tf = fnext;
+                int4 y = make_int4(0, 0, 0, 0);
+                if (w.lane < 2) y = (w.lane & 1) ? __ldcg(d.tn + tf) : __ldcg(d.tv + tf);
+                int4 v2 = bcast4(y, 0), n2 = bcast4(y, 1);
+                if (!(v2.w & ALIVE)) return -1;
+                int I2 = v2.x == p ? 0 : (v2.y == p ? 1 : (v2.z == p ? 2 : -1));
+                if (I2 < 0) return -1;
+                if (w.lane == 0) {
+                    sh->S[nf] = tf;
+                    sh->I[nf] = I2;
+                    sh->L[nf] = comp(v2, (I2 + 1) % 3);
+                    sh->ON[nf] = comp(n2, I2);
+                }
+                ++nf;
+                break;
+            }
+            tf = fnext;
+            tb = fprev;
+            continue;
+        }
+        if (tb == tf) break;
+        if (!(bv.w & ALIVE)) return -1;
+        int Ib = bv.x == p ? 0 : (bv.y == p ? 1 : (bv.z == p ? 2 : -1));
+        if (Ib < 0) return -1;
+        if (nf + nbk + 1 > KMAX) return -2;
+        if (w.lane == 0) {
+            int at = KMAX - 1 - nbk;
+            sh->S[at] = tb;
+            sh->I[at] = Ib;
+            sh->L[at] = comp(bv, (Ib + 1) % 3);
+            sh->ON[at] = comp(bn, Ib);
+        }
+        ++nbk;
+        int bprev = comp(bn, (Ib + 2) % 3) >> 2;
+        if (fnext == tb) break;
+        if (bprev == tf) break;
+        if (fnext < 0 || fnext >= d.cap || bprev < 0 || bprev >= d.cap) return -1;
+        if (fnext == bprev) {
+            tf = fnext;
+            tb = fnext;
+            continue;
+        }
+        tf = fnext;
+        tb = bprev;
+    }
+    __syncwarp();
+    // move the clockwise part (at most KMAX/2 = 32 entries: one lane each) after the rest
+    int k = nf + nbk;
+    int src = KMAX - nbk + w.lane;
+    int cS = 0, cI = 0, cL = 0, cO = 0;
+    bool mv = w.lane < nbk;
+    if (mv) {
+        cS = sh->S[src];
+        cI = sh->I[src];
+        cL = sh->L[src];
+        cO = sh->ON[src];
+    }
+    __syncwarp();
+    if (mv) {
+        sh->S[nf + w.lane] = cS;
+        sh->I[nf + w.lane] = cI;
+        sh->L[nf + w.lane] = cL;
+        sh->ON[nf + w.lane] = cO;
+    }
+    __syncwarp();
+    return k;
 }
 
 // One test of ear i (L[i], L[i+1], L[i+2]) of the current link polygon of m vertices:
@@ -1315,19 +1427,14 @@ __device__ __noinline__ int move_in_place(Warp w, const Dev &d, int p, int2 q, S
 // its claims in the scratch's claim list).  DEV_DEGREE when there is no scratch.
 __device__ __noinline__ int delete_point_big(Warp w, const Dev &d, int p, int &spare0, int &spare1, int &hint)
 {
-    if (!w.sh->big) return DEV_DEGREE;
+    int *big = warp_big(d);
+    if (!big) return DEV_DEGREE;
     __syncwarp();
-    if (w.lane == 0) {
-        w.sh->clp = w.sh->big + 7 * KBIG;
-        w.sh->clcap = 2 * KBIG + 64;
-    }
+    if (w.lane == 0) w.sh->clbig = 1;
     __syncwarp();
-    int rc = delete_point_in(w, d, p, spare0, spare1, hint, star_big(w.sh->big), false);
+    int rc = delete_point_in(w, d, p, spare0, spare1, hint, star_big(big), false);
     __syncwarp();
-    if (w.lane == 0) {
-        w.sh->clp = w.sh->cl;
-        w.sh->clcap = MAXC;
-    }
+    if (w.lane == 0) w.sh->clbig = 0;
     __syncwarp();
     return rc;
 }
@@ -1335,19 +1442,14 @@ __device__ __noinline__ int delete_point_big(Warp w, const Dev &d, int p, int &s
 // move_in_place with the star in the warp's global scratch (degree above KMAX).
 __device__ __noinline__ int move_in_place_big(Warp w, const Dev &d, int p, int2 q)
 {
-    if (!w.sh->big) return 0;
+    int *big = warp_big(d);
+    if (!big) return 0;
     __syncwarp();
-    if (w.lane == 0) {
-        w.sh->clp = w.sh->big + 7 * KBIG;
-        w.sh->clcap = 2 * KBIG + 64;
-    }
+    if (w.lane == 0) w.sh->clbig = 1;
     __syncwarp();
-    int rc = move_in_place(w, d, p, q, star_big(w.sh->big));
+    int rc = move_in_place(w, d, p, q, star_big(big));
     __syncwarp();
-    if (w.lane == 0) {
-        w.sh->clp = w.sh->cl;
-        w.sh->clcap = MAXC;
-    }
+    if (w.lane == 0) w.sh->clbig = 0;
     __syncwarp();
     return rc;
 }

@@ -35,6 +35,10 @@ struct Inst {
 // The warp's handle and its shared state (counters zero, claims none, random state
 // from `seed`, instance = the points [d.rlo, d.rlo + d.rn)).
 static_assert(C_NUM <= 32, "one lane clears each counter");
+// Seven 128-thread blocks of k_kinetic per SM: 7 x (static shared memory, rounded up to
+// 128 bytes, + 1 KB reserved per block) must fit the SM's 228 KB.  Growing the per-warp
+// block past this drops a block per SM (a quarter of the resident moves) at once.
+static_assert(WPB * sizeof(WarpShared) + sizeof(Dev) <= 32256, "k_kinetic must keep 7 blocks per SM");
 
 __device__ __forceinline__ Warp make_warp(WarpShared *sh, int token, unsigned seed, const Dev &d)
 {
@@ -50,9 +54,7 @@ __device__ __forceinline__ Warp make_warp(WarpShared *sh, int token, unsigned se
         sh->cyc_max = 0;
         sh->rlo = d.rlo;
         sh->rn = d.rn;
-        sh->clp = sh->cl;
-        sh->clcap = MAXC;
-        sh->big = nullptr;
+        sh->clbig = 0;
     }
     __syncwarp();
     return w;
@@ -222,8 +224,8 @@ __global__ void k_intake_link(Dev d, const int3 *moves, int m, Inst I, int bits,
 // message.  A point whose target is still occupied by a point that has not moved
 // yet is deferred.  The last warp to finish inserts the deferred points and
 // certifies the triangles written on the global-memory path.
-__device__ void step_tail(Warp w, const Dev &d, Inst I, int4 *deferred, int *defer_count, int defer_cap,
-                          int *viol, int viol_cap);
+__device__ __noinline__ void step_tail(Warp w, const Dev &d, Inst I, int4 *deferred, int *defer_count,
+                                       int defer_cap, int *viol, int viol_cap);
 
 // Entries of the deferred list: (p, s0, s1, hint) = an insertion left to the end of the
 // step (s0 >= 0); (p, DQ_MOVE - pass, qx, qy) = a whole move left for later, pass
@@ -279,7 +281,7 @@ struct MoveOut {
     int rc, s0, s1, hint;
 };
 
-__device__ __noinline__ MoveOut run_move(Warp w, const Dev &d, int p, int2 q, bool may_give_up)
+__device__ __forceinline__ MoveOut run_move(Warp w, const Dev &d, int p, int2 q, bool may_give_up)
 {
     MoveOut o;
     int s0 = -1, s1 = -1, hint = -1;
@@ -347,73 +349,73 @@ __global__ void __launch_bounds__(WPB * 32, 7) k_kinetic(Dev dp, const int3 *mov
     int gw = blockIdx.x * (blockDim.x >> 5) + wib;
     int nw = gridDim.x * (blockDim.x >> 5);
     Warp w = make_warp(&shs[wib], gw + 1, gw + 17 * d.stamp, d);
-    if (w.lane == 0 && d.big) w.sh->big = d.big + (size_t)gw * BIG_INTS;
-    __syncwarp();
     const int items = ncells * wpp;
-    bool run = true;
-    while (run) {
-        // persistent warps pull (partition, share) work items from a ticket
-        int t = 0;
-        if (w.lane == 0) t = atomicAdd(d.status + S_TICKET, 1);
-        t = __shfl_sync(FULL, t, 0);
-        if (t >= items) break;
-        int c = t / wpp, sub = t - c * wpp;
-        int inst = I.ninst > 1 ? csr_find(I.cofs, I.ninst + 1, c) : 0;
-        set_instance(w, I.pofs[inst], I.pofs[inst + 1] - I.pofs[inst]);
-        int i = __shfl_sync(FULL, __ldcg(head + c), 0);
-        int k = -1;
-        while (i >= 0) {
-            if (read_status(d)) {
-                run = false;
-                break;
-            }
-            if (++k % wpp != sub) {
-                i = __shfl_sync(FULL, __ldcg(next + i), 0);
-                continue;
+    // One loop, one move per iteration: first the moves of the (partition, share) work
+    // items the warp takes from a ticket; when those are gone, the whole moves left
+    // so far (drained in parallel with the warps still busy; each may be left again,
+    // DQ_PASSES times, before the last warp runs it when nothing else competes).
+    int i = -1, kk = -1, sub = 0, c = 0;  // position in the current partition's list
+    bool tickets = true;
+    while (true) {
+        int p, pass = 0;
+        int2 q;
+        if (tickets) {
+            // next move of this work item (every wpp-th of the partition's list)
+            if (i >= 0) i = __shfl_sync(FULL, __ldcg(next + i), 0);
+            while (i >= 0 && ++kk % wpp != sub) i = __shfl_sync(FULL, __ldcg(next + i), 0);
+            if (i < 0) {
+                if (read_status(d)) break;
+                int t = 0;
+                if (w.lane == 0) t = atomicAdd(d.status + S_TICKET, 1);
+                t = __shfl_sync(FULL, t, 0);
+                if (t >= items) {
+                    tickets = false;
+                    // nothing was left for later so far: this warp is done
+                    if (__shfl_sync(FULL, w.lane == 0 ? __ldcg(defer_count) : 0, 0) == 0) break;
+                    continue;
+                }
+                c = t / wpp;
+                sub = t - c * wpp;
+                kk = -1;
+                i = __shfl_sync(FULL, __ldcg(head + c), 0);
+                int inst = I.ninst > 1 ? csr_find(I.cofs, I.ninst + 1, c) : 0;
+                set_instance(w, I.pofs[inst], I.pofs[inst + 1] - I.pofs[inst]);
+                while (i >= 0 && ++kk % wpp != sub) i = __shfl_sync(FULL, __ldcg(next + i), 0);
+                if (i < 0) continue;
             }
             int3 mv = moves[i];
-            int p = mv.x;
-            int2 q = make_int2(mv.y, mv.z);
-            MoveOut o = run_move(w, d, p, q, true);
-            if (!settle_move(w, d, o.rc, p, q, 0, o.s0, o.s1, o.hint, deferred, defer_count, defer_cap)) {
-                run = false;
-                break;
-            }
-            i = __shfl_sync(FULL, __ldcg(next + i), 0);
-        }
-    }
-    // then drain the whole moves left so far, in parallel with the warps still busy: each
-    // may be left again (DQ_PASSES times) before it runs without giving up
-    while (run) {
-        if (read_status(d)) break;
-        int j = -1;
-        if (w.lane == 0) {
-            int nx = __ldcg(d.status + S_DNEXT);
-            while (true) {
-                int cnt = min(__ldcg(defer_count), defer_cap);
-                if (nx >= cnt) break;
-                int prev = atomicCAS(d.status + S_DNEXT, nx, nx + 1);
-                if (prev == nx) {
-                    j = nx;
-                    break;
+            p = mv.x;
+            q = make_int2(mv.y, mv.z);
+        } else {
+            if (read_status(d)) break;
+            int j = -1;
+            if (w.lane == 0) {
+                int nx = __ldcg(d.status + S_DNEXT);
+                while (true) {
+                    int cnt = min(__ldcg(defer_count), defer_cap);
+                    if (nx >= cnt) break;
+                    int prev = atomicCAS(d.status + S_DNEXT, nx, nx + 1);
+                    if (prev == nx) {
+                        j = nx;
+                        break;
+                    }
+                    nx = prev;
                 }
-                nx = prev;
             }
+            j = __shfl_sync(FULL, j, 0);
+            if (j < 0) break;
+            int4 e = read_deferred(w, deferred, j);
+            // an unpublished entry, an insertion (for the end), a taken entry, or a move
+            // left too often: the last warp takes those
+            if (e.x < 0 || e.y > DQ_MOVE || e.y <= DQ_DONE || DQ_MOVE - e.y >= DQ_PASSES) continue;
+            if (w.lane == 0) deferred[j].y = DQ_DONE;
+            __syncwarp();
+            pass = DQ_MOVE - e.y + 1;
+            p = e.x;
+            q = make_int2(e.z, e.w);
+            int inst = I.ninst > 1 ? csr_find(I.pofs, I.ninst + 1, p) : 0;
+            set_instance(w, I.pofs[inst], I.pofs[inst + 1] - I.pofs[inst]);
         }
-        j = __shfl_sync(FULL, j, 0);
-        if (j < 0) break;
-        int4 e = read_deferred(w, deferred, j);
-        if (e.x < 0) continue;  // not published in time: the last warp takes it
-        // an insertion (for the end), a taken entry, or a move left too often (the
-        // last warp runs those when nothing else competes)
-        if (e.y > DQ_MOVE || e.y <= DQ_DONE || DQ_MOVE - e.y >= DQ_PASSES) continue;
-        if (w.lane == 0) deferred[j].y = DQ_DONE;
-        __syncwarp();
-        int pass = DQ_MOVE - e.y + 1;
-        int p = e.x;
-        int2 q = make_int2(e.z, e.w);
-        int inst = I.ninst > 1 ? csr_find(I.pofs, I.ninst + 1, p) : 0;
-        set_instance(w, I.pofs[inst], I.pofs[inst + 1] - I.pofs[inst]);
         MoveOut o = run_move(w, d, p, q, true);
         if (!settle_move(w, d, o.rc, p, q, pass, o.s0, o.s1, o.hint, deferred, defer_count, defer_cap)) break;
     }
@@ -496,8 +498,8 @@ __device__ void certify_one(const Dev &d, int t, int *viol, int *viol_count, int
 // Tail of a step (one warp, after every other warp finished): insert the deferred
 // points, then certify the triangles written on the global-memory path (the staged
 // path certified its own).  A long dirty list is left to the host.
-__device__ void step_tail(Warp w, const Dev &d, Inst I, int4 *deferred, int *defer_count, int defer_cap,
-                          int *viol, int viol_cap)
+__device__ __noinline__ void step_tail(Warp w, const Dev &d, Inst I, int4 *deferred, int *defer_count,
+                                       int defer_cap, int *viol, int viol_cap)
 {
     if (read_status(d)) return;
     int cnt = __shfl_sync(FULL, __ldcg(defer_count), 0);

@@ -81,7 +81,7 @@ __device__ __noinline__ int ensure_local(Warp w, const Dev &d, int cnt, int slot
     WarpShared *sh = w.sh;
     int j = local_find(sh, cnt, slot);
     if (j >= 0) return j;
-    if (cnt >= LM || w.sh->ncl >= w.sh->clcap || slot < 0 || slot >= d.cap) return -1;
+    if (cnt >= LM || w.sh->ncl >= claim_cap(w) || slot < 0 || slot >= d.cap) return -1;
     int mine = w.lane == 0 ? slot : -1;
     if (!claim_lanes(w, d, mine, 1)) return -1;
     int4 v, nb;
@@ -264,7 +264,7 @@ __device__ __forceinline__ int bw_grow(Warp w, const Dev &d, Region &R, int p, i
         if (mine2 < 0 || mine2 >= d.cap) keep2 = false;
         unsigned k1 = __ballot_sync(FULL, keep), k2 = __ballot_sync(FULL, keep2);
         const int nu = __popc(k1) + __popc(k2);
-        if (R.cnt + nu > LM || w.sh->ncl + nu > w.sh->clcap) return BW_FULL;
+        if (R.cnt + nu > LM || w.sh->ncl + nu > claim_cap(w)) return BW_FULL;
         __syncwarp();
         if (keep) need[__popc(k1 & ((1u << w.lane) - 1u))] = mine;
         if (keep2) need[__popc(k1) + __popc(k2 & ((1u << w.lane) - 1u))] = mine2;
@@ -550,13 +550,13 @@ __device__ int move_point(Warp w, const Dev &d, int p, int2 q, int &s0, int &s1,
         int k = gather_star(w, d, p);
         long long t1 = clock64();
         cnt_add(w, C_CYC_GATHER, (unsigned)((t1 - t0) >> 6));
-        if (k == -2 && w.sh->big) return MV_BIG;
+        if (k == -2 && d.big) return MV_BIG;
         if (k == -2 && attempt == d.retry_cap) return DEV_DEGREE;
         if (k < 3 || 2 * k + 8 > LM) {
             if (k >= 3) {
                 // a star too large to stage: take the plain global path (or leave the
                 // whole move to the end of the step when its claims keep failing)
-                int rc = delete_point(w, d, p, s0, s1, hint, may_give_up && w.sh->big != nullptr);
+                int rc = delete_point(w, d, p, s0, s1, hint, may_give_up && d.big != nullptr);
                 if (rc == DEL_BUSY) return MV_BIG;
                 return rc ? rc : MV_GLOBAL;
             }
@@ -604,7 +604,7 @@ __device__ int move_point(Warp w, const Dev &d, int p, int2 q, int &s0, int &s1,
         }
         if (!ok) {
             release_all(w, d);
-            if (may_give_up && w.sh->big && ++claim_fail >= DEFER_AFTER) return MV_BIG;
+            if (may_give_up && d.big && ++claim_fail >= DEFER_AFTER) return MV_BIG;
             backoff(w, attempt);
             continue;
         }
