@@ -1001,7 +1001,7 @@ __device__ __noinline__ int insert_staged(Warp w, const Dev &d, int p, int2 q, i
             // keep losing; after a few losses the insertion by split and Lawson flips,
             // which claims a few triangles at a time, takes over.
             release_all(w, d);
-            if (++cavity_fail >= 4) return INS_GLOBAL;
+            if (allow_defer && ++cavity_fail >= 4) return INS_GLOBAL;  // during a step
             backoff(w, attempt);
             t = wr.t;
             continue;
