@@ -642,6 +642,27 @@ def main():
     e2e_sec = sum(a.elapsed_time(b) for a, b in ev2) / 1000.0
     tri2.close()
 
+    # ---- comparator: the same steps with the in-place variant (kdt_config.variant = 1)
+    w3 = W.c2(n=args.n, grid=args.grid, seed=2 + 1000 * rank)
+    tri3 = kdt.Triangulation(kdt.default_config(grid=args.grid, domain_bits=24, variant=1), device=local)
+    tri3.build(torch.from_numpy(w3.positions).to(dev))
+    for i in range(args.warmup):
+        tri3.step(d_moves[i])
+    tri3.reset_stats()
+    ev3 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        i = args.warmup + k
+        ev3[k][0].record()
+        tri3.step(d_moves[i])
+        ev3[k][1].record()
+        flush.zero_()
+    torch.cuda.synchronize()
+    var_sec = sum(a.elapsed_time(b) for a, b in ev3) / 1000.0
+    st3 = tri3.stats()
+    var_in_place = (st3["moves"] - st3["deletes"]) / max(1, st3["moves"])
+    tri3.close()
+
     # ---- comparator: GPU full rebuild of the same point set per step
     tri.reset_stats()
     evr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -685,6 +706,8 @@ def main():
                 "gpu_kinetic_plain": {"value": value, "unit": "updates/s"},
                 "gpu_full_rebuild": {"value": m / (rebuild_ms / 1000.0), "unit": "updates/s",
                                      "ms_per_rebuild": rebuild_ms},
+                "gpu_kinetic_variant_in_place": {"value": local_updates / var_sec, "unit": "updates/s",
+                                                 "moved_in_place": var_in_place},
             },
             "gpu_launches": int(launches),
             "fallbacks": int(fallbacks),

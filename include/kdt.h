@@ -87,6 +87,13 @@ typedef struct {
     int32_t warps_per_partition;  /* warps sharing one partition's moves (0 = 1)             */
     int32_t autotune;      /* 1: time the first steps over points per partition {128, 256,
                               512} x warps per partition {1, 2, 4} and keep the fastest       */
+    int32_t variant;       /* 0: every move deletes and re-inserts the point (the paper's
+                              method, default).  1: first test whether the point can move
+                              in place: every triangle of its star stays counter-clockwise
+                              and every edge of the star stays locally Delaunay at the new
+                              position (a safe-region test in the spirit of the paper's
+                              related work [6]); if so only the position changes, else
+                              delete + insert.  The triangulation is the same either way.  */
 } kdt_config;
 
 /* Counters since creation (or kdt_reset_stats). */

@@ -207,6 +207,7 @@ Dev make_dev(kdt *h)
     d.trace_count = h->trace_count;
     d.trace_cap = h->trace_cap;
     d.big = nullptr;  // set for the kinetic launch only (enqueue_step)
+    d.variant = h->cfg.variant;
     return d;
 }
 
@@ -968,6 +969,7 @@ int kdt_default_config(kdt_config *cfg)
     cfg->points_per_partition = 0;
     cfg->warps_per_partition = 0;
     cfg->autotune = 0;
+    cfg->variant = 0;
     return KDT_OK;
 }
 
@@ -979,7 +981,8 @@ int kdt_create(kdt **out, const kdt_config *cfg, int device, void *cuda_stream)
     if (cfg) c = *cfg;
     else kdt_default_config(&c);
     if (c.domain_bits <= 0 || c.domain_bits > 28 || c.grid < 0 || c.grid > 4096 || c.retry_cap < 0 ||
-        c.points_per_partition < 0 || c.warps_per_partition < 0 || c.warps_per_partition > 32)
+        c.points_per_partition < 0 || c.warps_per_partition < 0 || c.warps_per_partition > 32 ||
+        c.variant < 0 || c.variant > 1)
         return KDT_ERR_ARG;
     if (c.retry_cap == 0) c.retry_cap = 4096;
     if (cudaSetDevice(device) != cudaSuccess) return KDT_ERR_CUDA;

@@ -69,36 +69,39 @@ enum Counter : int {
 };
 
 struct Dev {
+    // (pointers first, then 32-bit fields: no padding, the struct is copied into every
+    // block's shared memory)
     int2 *xy;
     int *pt_tri;
     int4 *tv;
     int4 *tn;
-    int n;
-    int cap;
     int *status;
     int *dirty;          // slots written in this step (for certification)
     int *dirty_count;
-    int dirty_cap;
     int *pt_stamp;       // step stamp of points moved in this step
-    int stamp;
     const int *ctl;      // graph-launched steps: ctl[0] = moves, ctl[1] = stamp,
                          // ctl[2..3] = the moves' device address
     int *viol;           // edges found not locally Delaunay: (slot << 2) | edge
     int *viol_count;
-    int viol_cap;
-    int rlo, rn;         // the points of the instance being worked on (walk restarts)
     unsigned long long *counters;
-    int use_filter;
-    int retry_cap;
     // learned locate proposal (kdt_mlp.cuh) and its training rows; null = off
     const unsigned short *mlp;  // network parameters, BF16
     float *trace_x;             // features, trace_cap x 32
     int *trace_y;               // (slot, cavity size) per row
     int *trace_count;           // rows written (may exceed trace_cap: later rows dropped)
-    int trace_cap;
     // per-warp global scratch for the deletion of a point of degree above KMAX: set for
     // the kinetic launch only (BIG_INTS ints per warp of that launch), else null
     int *big;
+    int n;
+    int cap;
+    int dirty_cap;
+    int stamp;
+    int viol_cap;
+    int rlo, rn;         // the points of the instance being worked on (walk restarts)
+    int use_filter;
+    int retry_cap;
+    int trace_cap;
+    int variant;         // 1: try a move in place before delete + insert (kdt_config.variant)
 };
 
 constexpr int KBIG = 1024;                  // largest degree the global deletion handles

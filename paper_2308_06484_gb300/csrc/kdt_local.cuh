@@ -660,6 +660,39 @@ __device__ int move_point(Warp w, const Dev &d, int p, int2 q, int &s0, int &s1,
                 }
             }
         }
+        // ---- variant 1 (kdt_config.variant): a move that keeps every triangle of the
+        // star counter-clockwise and every edge of the star (spokes p-v_i, link edges
+        // v_i-v_{i+1} against the staged ring apex) locally Delaunay at q changes only
+        // p's position: every other edge keeps its triangles and their vertices, so the
+        // triangulation stays Delaunay (Delaunay lemma) and nothing is written.
+        if (d.variant == 1 && gpos < 0) {
+            bool stays = true;
+            unsigned ex = 0, ti = 0;
+            for (int i = w.lane; i < k; i += 32) {
+                int i0 = i == 0 ? k - 1 : i - 1, i1 = i + 1 == k ? 0 : i + 1;
+                int a = sh->L[i0], b = sh->L[i], c = sh->L[i1];
+                int2 pa = sh->LX[i0], pb = sh->LX[i], pc = sh->LX[i1];
+                int eo = sh->EO[i];
+                int o = eo >> 2, f = eo & 3;
+                int r = ic(sh->lv[o], f);
+                int2 pr = sh->lp[o][f];
+                stays = stays && orient2d(q, pb, pc) > 0 &&
+                        !conflict(p, a, b, q, pa, pb, c, pc, d.use_filter, &ex, &ti) &&
+                        !conflict(p, b, c, q, pb, pc, r, pr, d.use_filter, &ex, &ti);
+            }
+            cnt_add(w, C_EXACT, __reduce_add_sync(FULL, ex));
+            cnt_add(w, C_TIES, __reduce_add_sync(FULL, ti));
+            if (__all_sync(FULL, stays)) {
+                if (w.lane == 0) {
+                    d.xy[p] = q;
+                    __threadfence();
+                }
+                __syncwarp();
+                release_all(w, d);
+                cnt_add(w, C_CYC_LOCAL, (unsigned)((clock64() - t2) >> 6));
+                return MV_DONE;
+            }
+        }
         // ---- learned proposal / training rows: the move's features (interior p only);
         // the link order is kept in I for the hole ranks (I is not needed any more)
         const bool learn = (d.mlp != nullptr || d.trace_x != nullptr) && gpos < 0;
@@ -1001,7 +1034,7 @@ __device__ __noinline__ int insert_staged(Warp w, const Dev &d, int p, int2 q, i
             // keep losing; after a few losses the insertion by split and Lawson flips,
             // which claims a few triangles at a time, takes over.
             release_all(w, d);
-            if (allow_defer && ++cavity_fail >= 4) return INS_GLOBAL;  // during a step
+            if (++cavity_fail >= (allow_defer ? 4 : 32)) return INS_GLOBAL;  // (4 during a step)
             backoff(w, attempt);
             t = wr.t;
             continue;

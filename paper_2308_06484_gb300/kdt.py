@@ -40,7 +40,8 @@ class Config(ctypes.Structure):
                 ("warps_per_block", ctypes.c_int32), ("build_warps", ctypes.c_int32),
                 ("kinetic_warps", ctypes.c_int32), ("debug", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("points_per_partition", ctypes.c_int32),
-                ("warps_per_partition", ctypes.c_int32), ("autotune", ctypes.c_int32)]
+                ("warps_per_partition", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("variant", ctypes.c_int32)]
 
 
 _STAT_FIELDS = ["steps", "moves", "rebuilds", "fallbacks", "kernel_launches", "flips", "retries",

@@ -223,3 +223,18 @@ def test_fallback_rebuild_and_retry_cap():
     t2 = _setup(w2, rebuild_ratio=0.0001)  # every step is done as a full rebuild
     run_kinetic(t2, w2, 3, every=1)
     assert t2.stats()["rebuilds"] == 3  # one full rebuild per step
+
+
+@pytest.mark.parametrize("make", [lambda: W.c1(), lambda: W.c2(n=30000, grid=16, seed=44),
+                                  lambda: W.KineticWorkload(W.mixture_lattice_points(30000, 24, 45), 16, 24,
+                                                            (1, 16), (1, 8), seed=46, name="mix")])
+def test_variant_in_place_moves(make):
+    """kdt_config.variant = 1 (move in place when the star stays Delaunay, else delete +
+    insert) gives the oracle's triangulation after every step."""
+    w = make()
+    t = _setup(w, variant=1)
+    run_kinetic(t, w, 8, every=1)
+    st = t.stats()
+    assert st["fallbacks"] == 0
+    assert st["deletes"] < st["moves"]  # some moves were done in place
+    assert t.verify() == 0
