@@ -116,7 +116,12 @@ typedef struct {
     int64_t proposal_moves;       /* staged moves located with the learned proposal on      */
     int64_t proposal_hits;        /* ... whose proposed hole triangle held the new position */
     int64_t trace_rows;           /* training rows written (kdt_set_trace)                  */
-    int64_t reserved[8];
+    int64_t tail_moves;           /* moves the last warp of a step ran alone                */
+    int64_t cycles_tail;          /* SM cycles of those last-warp tails                      */
+    int64_t big_moves;            /* moves of points of degree above 64 (star in scratch)    */
+    int64_t cycles_big;           /* SM cycles of those moves                                */
+    int64_t drain_moves;          /* moves taken again from the list of moves left for later */
+    int64_t reserved[3];
 } kdt_stats;
 
 /* ---- lifecycle ------------------------------------------------------------------ */

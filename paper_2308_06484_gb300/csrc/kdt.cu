@@ -63,7 +63,7 @@ struct kdt {
     int4 *tv = nullptr;
     int4 *tn = nullptr;
     int *scal = nullptr;                     // S_NUM device scalars
-    unsigned long long *counters = nullptr;  // C_NUM + 1
+    unsigned long long *counters = nullptr;  // C_SLOTS
     int *dirty = nullptr;
     int dirty_cap = 0;
     int *viol = nullptr;
@@ -539,7 +539,7 @@ int alloc_state(kdt *h, const int64_t *offs, int n_inst)
 
 void add_counters(kdt *h)
 {
-    unsigned long long c[C_NUM + 1];
+    unsigned long long c[C_SLOTS];
     if (cudaMemcpy(c, h->counters, sizeof c, cudaMemcpyDeviceToHost) != cudaSuccess) return;
     cudaMemset(h->counters, 0, sizeof c);
     kdt_stats &s = h->stats;
@@ -570,6 +570,11 @@ void add_counters(kdt *h)
     s.proposal_moves += c[C_PROP_MOVES];
     s.proposal_hits += c[C_PROP_HITS];
     s.trace_rows += c[C_TRACE_ROWS];
+    s.tail_moves += c[C_TAIL_MOVES];
+    s.cycles_tail += (int64_t)c[C_CYC_TAIL];
+    s.big_moves += c[C_BIG_MOVES];
+    s.cycles_big += (int64_t)c[C_CYC_BIG];
+    s.drain_moves += c[C_DRAIN_MOVES];
 }
 
 // Undo a step that failed after it started: restore the old positions and rebuild.
@@ -992,7 +997,7 @@ int kdt_create(kdt **out, const kdt_config *cfg, int device, void *cuda_stream)
     h->stream = (cudaStream_t)cuda_stream;
     h->cfg = c;
     if (cudaMalloc(&h->scal, S_NUM * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&h->counters, (C_NUM + 1) * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&h->counters, C_SLOTS * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost(&h->hscal, S_NUM * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&h->ctl, 4 * sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&h->hctl, 4 * sizeof(int)) != cudaSuccess ||
@@ -1003,7 +1008,7 @@ int kdt_create(kdt **out, const kdt_config *cfg, int device, void *cuda_stream)
         return KDT_ERR_CUDA;
     }
     cudaMemset(h->scal, 0, S_NUM * sizeof(int));
-    cudaMemset(h->counters, 0, (C_NUM + 1) * sizeof(unsigned long long));
+    cudaMemset(h->counters, 0, C_SLOTS * sizeof(unsigned long long));
     *out = h;
     return KDT_OK;
 }

@@ -53,6 +53,7 @@ enum DevStatus : int {
 constexpr int INS_DEFER = -10;   // q lies on a vertex still moving in this step
 constexpr int INS_GLOBAL = -11;  // (staged insertion) the caller must use the global path
 constexpr int DEL_BUSY = -12;    // (deletion) claims kept failing: nothing was changed
+constexpr int DEL_HUGE = -13;    // (deletion) the degree grew above the star arrays: nothing was changed
 // Claim losses after which a move stops competing and is left to the end of the step,
 // when no other warp runs: an operation with a large footprint (a high-degree point,
 // whose star shares long thin triangles with many neighbours) can otherwise keep
@@ -65,7 +66,10 @@ enum Counter : int {
     C_MV_GLOBAL, C_CYC_MOVE, C_CYC_GATHER, C_CYC_CLAIM, C_CYC_LOCAL, C_CYC_WB,
     C_CYC_EAR, C_CYC_LAWSON, C_CYC_CERT, C_PROP_MOVES, C_PROP_HITS, C_TRACE_ROWS,
     C_NUM,
-    C_CYC_MAX = C_NUM  // a second device slot, updated with atomicMax
+    C_CYC_MAX = C_NUM,  // a second device slot, updated with atomicMax
+    // device-only slots for rare events, added straight to global memory (dev_count)
+    C_TAIL_MOVES, C_CYC_TAIL, C_BIG_MOVES, C_CYC_BIG, C_DRAIN_MOVES,
+    C_SLOTS
 };
 
 struct Dev {
@@ -312,6 +316,12 @@ __device__ __forceinline__ void flush_counters(Warp w, const Dev &d)
             if (w.sh->cnt[i]) atomicAdd(d.counters + i, (unsigned long long)w.sh->cnt[i]);
         if (w.sh->cyc_max) atomicMax(d.counters + C_CYC_MAX, (unsigned long long)w.sh->cyc_max);
     }
+}
+
+// a rare event, counted straight into the device slot
+__device__ __forceinline__ void dev_count(const Warp w, const Dev &d, int i, unsigned long long v)
+{
+    if (w.lane == 0 && d.counters) atomicAdd(d.counters + i, v);
 }
 
 // ------------------------------------------------------------------ certification
@@ -1126,6 +1136,16 @@ __device__ __forceinline__ int gather_star(Warp w, const Dev &d, int p)
     return k;
 }
 
+// A word another lane of the warp may have updated (shared or global memory)
+__device__ __forceinline__ int vload(const int *p) { return *reinterpret_cast<const volatile int *>(p); }
+
+// Bit i of a bit set spread over the warp (lane c holds bits 32c .. 32c+31); every
+// lane must take part.
+__device__ __forceinline__ bool bit_of(unsigned words, int i)
+{
+    return (__shfl_sync(FULL, words, i >> 5) >> (i & 31)) & 1u;
+}
+
 // One test of ear i (L[i], L[i+1], L[i+2]) of the current link polygon of m vertices:
 // t = 0 fails a finite ear that is not counter-clockwise; t >= 1 fails it when
 // vertex i+2+t conflicts with it (the conditions ear_valid checks, one per call).
@@ -1168,6 +1188,9 @@ __device__ __noinline__ int delete_point_in(Warp w, const Dev &d, int p, int &sp
         // is writing p's triangles: treat every failed gather as contention, and report
         // a real degree overflow only when it persists for the whole retry budget
         int k = gather_star(w, d, p, A);
+        // a degree above the shared arrays (it can grow after the caller looked): the
+        // warp's global scratch takes it, if the launch has one
+        if (k == -2 && A.cap < KBIG && d.big) return DEL_HUGE;
         if (k == -2 && attempt == d.retry_cap) return DEV_DEGREE;
         if (k < 3) {
             backoff(w, attempt);
@@ -1226,47 +1249,75 @@ __device__ __noinline__ int delete_point_in(Warp w, const Dev &d, int p, int &sp
                 }
             }
         }
-        // ear clipping over the link polygon (L, ON, LX); T holds per-ear flags and I
-        // the clipped ears of a round
-        int m = k, newc = 0;
+        // Ear clipping over the link polygon (L, ON, LX).  T[i] counts the failed tests
+        // of ear i (L[i], L[i+1], L[i+2]): its orientation, and one per other link
+        // vertex in conflict with it, so the valid ears are those with T[i] == 0.  A
+        // round clips every valid ear no neighbour of which is clipped (each valid ear is
+        // a triangle of the hole's unique triangulation).  Removing vertices only removes
+        // conflicts from an ear whose three vertices stay consecutive, so such an ear
+        // loses the clipped vertices it conflicted with, and only the ears next to a
+        // clipped one are tested in full again: O(m^2) tests for the whole hole, not per
+        // round (a point beside a straight lattice row has hundreds of collinear link
+        // vertices and loses about one ear per round).  I lists the ears to test, then
+        // the clipped ears; lane c holds the bits of ears 32c .. 32c+31 in word registers.
+        int m = k, newc = 0, nt = k;
+        for (int i = w.lane; i < m; i += 32) {
+            A.T[i] = 0;
+            A.I[i] = i;
+        }
+        __syncwarp();
         while (m > 3) {
-            for (int i = w.lane; i < m; i += 32) A.T[i] = 0;
-            __syncwarp();
             unsigned ex = 0, ti = 0;
-            const long long npair = (long long)m * (m - 2);
-            for (long long base = 0; base < npair; base += 32) {
-                long long idx = base + w.lane;
-                if (idx < npair) {
-                    int i = (int)(idx / (m - 2)), t = (int)(idx - (long long)i * (m - 2));
-                    if (ear_test_fails(A.L, A.LX, m, i, t, d, &ex, &ti)) A.T[i] = 1;
+            {
+                const long long npair = (long long)nt * (m - 2);
+                for (long long base = 0; base < npair; base += 32) {
+                    long long idx = base + w.lane;
+                    if (idx < npair) {
+                        int r = (int)(idx / (m - 2)), t = (int)(idx - (long long)r * (m - 2));
+                        int i = A.I[r];
+                        if (ear_test_fails(A.L, A.LX, m, i, t, d, &ex, &ti)) atomicAdd(A.T + i, 1);
+                    }
                 }
             }
             __syncwarp();
-            cnt_add(w, C_EXACT, __reduce_add_sync(FULL, ex));
-            cnt_add(w, C_TIES, __reduce_add_sync(FULL, ti));
-            // lane 0 picks every valid ear whose neighbours are not picked (each valid
-            // ear is a triangle of the hole's unique triangulation), keeping >= 3 vertices;
-            // T[i] becomes "picked"
+            // greedy choice in index order, keeping >= 3 vertices (warp-uniform on ballots)
+            const int nch = (m + 31) >> 5;
+            unsigned pw = 0;
             int ns = 0;
-            if (w.lane == 0) {
+            {
                 bool prev = false, first = false;
-                for (int i = 0; i < m; ++i) {
-                    bool pick = A.T[i] == 0 && !prev && !(i == m - 1 && first) && ns < m - 3;
-                    A.T[i] = pick ? 1 : 0;
-                    if (pick) {
-                        A.I[ns++] = i;
+                for (int c = 0; c < nch; ++c) {
+                    int idx = (c << 5) + w.lane;
+                    unsigned vm = __ballot_sync(FULL, idx < m && vload(A.T + idx) == 0);
+                    unsigned pm = 0;
+                    int last = -2;
+                    while (vm && ns < m - 3) {
+                        int b = __ffs(vm) - 1;
+                        vm &= vm - 1u;
+                        int i = (c << 5) + b;
+                        if (b == 0 ? prev : last == b - 1) continue;
+                        if (i == m - 1 && first) continue;
+                        pm |= 1u << b;
+                        last = b;
+                        ++ns;
                         if (i == 0) first = true;
                     }
-                    prev = pick;
+                    prev = (pm >> 31) & 1u;
+                    if (w.lane == c) pw = pm;
                 }
             }
-            ns = __shfl_sync(FULL, ns, 0);
-            __syncwarp();
             if (ns == 0) {
                 // cannot happen for a valid star; leave the store to the fallback
                 release_all(w, d);
                 return DEV_INTERNAL;
             }
+            // the clipped ears in index order
+            for (int c = 0, at = 0; c < nch; ++c) {
+                unsigned pm = __shfl_sync(FULL, pw, c);
+                if ((pm >> w.lane) & 1u) A.I[at + __popc(pm & ((1u << w.lane) - 1u))] = (c << 5) + w.lane;
+                at += __popc(pm);
+            }
+            __syncwarp();
             // lane r writes the r-th clipped ear into slot S[newc + r]
             for (int r = w.lane; r < ns; r += 32) {
                 int i = A.I[r], i1 = i + 1 == m ? 0 : i + 1, i2 = i1 + 1 == m ? 0 : i1 + 1;
@@ -1284,32 +1335,65 @@ __device__ __noinline__ int delete_point_in(Warp w, const Dev &d, int p, int &sp
                 A.ON[i] = (X << 2) | 1;
             }
             __syncwarp();
+            // an invalid ear whose vertices all stay loses the clipped vertices (the
+            // middles of the clipped ears) that conflict with it
+            {
+                const long long npair = (long long)m * ns;
+                for (long long base = 0; base < npair; base += 32) {
+                    long long idx = base + w.lane;
+                    const bool act = idx < npair;
+                    int e = act ? (int)(idx / ns) : 0, r = act ? (int)(idx - (long long)e * ns) : 0;
+                    int em = e == 0 ? m - 1 : e - 1, e1 = e + 1 == m ? 0 : e + 1;
+                    // (shuffles: every lane takes part)
+                    bool pem = bit_of(pw, em), pe = bit_of(pw, e), pe1 = bit_of(pw, e1);
+                    if (act && !pem && !pe && !pe1 && vload(A.T + e) > 0) {
+                        int v = A.I[r] + 1 == m ? 0 : A.I[r] + 1;
+                        int t = v - e - 2;
+                        if (t < 0) t += m;
+                        if (ear_test_fails(A.L, A.LX, m, e, t, d, &ex, &ti)) atomicAdd(A.T + e, -1);
+                    }
+                }
+            }
+            __syncwarp();
+            cnt_add(w, C_EXACT, __reduce_add_sync(FULL, ex));
+            cnt_add(w, C_TIES, __reduce_add_sync(FULL, ti));
             // drop the clipped ears' middle vertices (vertex j goes when ear j-1 was
-            // clipped), in chunks of 32 in increasing order
-            int kept = 0;
+            // clipped), in chunks of 32 in increasing order; the ear at a kept vertex j is
+            // new when ear j or ear j+1 was clipped, and is listed for the full tests
+            int kept = 0, nlist = 0;
             for (int c0 = 0; c0 < m; c0 += 32) {
                 int j = c0 + w.lane;
-                bool keep = j < m && A.T[j == 0 ? m - 1 : j - 1] == 0;
+                int jm = j == 0 ? m - 1 : j - 1, j1 = j + 1 >= m ? j + 1 - m : j + 1;
+                bool pj = bit_of(pw, j < m ? j : 0), pjm = bit_of(pw, j < m ? jm : 0),
+                     pj1 = bit_of(pw, j < m ? j1 : 0);
+                bool keep = j < m && !pjm;
+                bool fresh = keep && (pj || pj1);
                 unsigned km = __ballot_sync(FULL, keep);
+                unsigned fm = __ballot_sync(FULL, fresh);
                 int nj = kept + __popc(km & ((1u << w.lane) - 1u));
-                int lv = 0, onv = 0;
+                int lv = 0, onv = 0, tv = 0;
                 int2 xv = make_int2(0, 0);
                 if (keep) {
                     lv = A.L[j];
                     onv = A.ON[j];
                     xv = A.LX[j];
+                    tv = fresh ? 0 : vload(A.T + j);
                 }
                 __syncwarp();
                 if (keep) {
                     A.L[nj] = lv;
                     A.ON[nj] = onv;
                     A.LX[nj] = xv;
+                    A.T[nj] = tv;
                 }
+                if (fresh) A.I[nlist + __popc(fm & ((1u << w.lane) - 1u))] = nj;
                 __syncwarp();
                 kept += __popc(km);
+                nlist += __popc(fm);
             }
             m -= ns;
             newc += ns;
+            nt = nlist;
         }
         {
             int X = A.S[newc++];
@@ -1346,15 +1430,20 @@ __device__ __forceinline__ int delete_point(Warp w, const Dev &d, int p, int &sp
     return delete_point_in(w, d, p, spare0, spare1, hint, star_shared(w.sh), may_give_up);
 }
 
-// Move p to q without changing any triangle, when that keeps the triangulation
-// Delaunay: the triangles around p stay counter-clockwise and every edge of p's star
-// (the spokes p-v_i and the link edges v_i-v_{i+1}) stays locally Delaunay with p at q;
-// edges not in the star keep their triangles and their vertices' positions, so by the
-// Delaunay lemma nothing else can change.  Exact SoS predicates decide, as everywhere.
-// Only for an interior p.  Returns 1 (moved), 0 (not so: the caller deletes and
-// inserts), or a DevStatus error.  The star and its claims live in A and the current
-// claim list (the caller provides room for 2k claims).
-__device__ __noinline__ int move_in_place(Warp w, const Dev &d, int p, int2 q, Star A)
+// Move p to q in place (no deletion): when every triangle around p stays counter-
+// clockwise with p at q, the star is still a triangulation of the same star-shaped
+// link polygon, so the whole triangulation stays valid; edges not in the star keep
+// their triangles and their vertices' positions, so by the Delaunay lemma only the
+// star's edges (the spokes p-v_i and the link edges v_i-v_{i+1}) can fail to be locally
+// Delaunay.  If none fails, only p's coordinate changes.  Otherwise, with `flip`, the
+// failing edges are flipped (Lawson's algorithm from a valid triangulation reaches
+// the unique Delaunay triangulation; the kinetic move-and-flip of the related work
+// in Section II) and their triangles go to the dirty list, so the certification that
+// ends every step settles anything the flip stack drops.  Exact SoS predicates decide,
+// as everywhere.  Only for an interior p.  Returns 1 (moved), 0 (not so: the caller
+// deletes and inserts), or a DevStatus error.  The star and its claims live in A and
+// the current claim list (the caller provides room for 2k claims).
+__device__ __noinline__ int move_in_place(Warp w, const Dev &d, int p, int2 q, Star A, bool flip)
 {
     for (int attempt = 0;; ++attempt) {
         if (attempt > d.retry_cap) return DEV_RETRY;
@@ -1396,33 +1485,71 @@ __device__ __noinline__ int move_in_place(Warp w, const Dev &d, int p, int2 q, S
             return 0;
         }
         __syncwarp();
-        bool stays = true;
+        bool ccw = true;
         unsigned ex = 0, ti = 0;
+        // T[i]: bit 0 = spoke p-L[i] fails, bit 1 = link edge L[i]-L[i+1] fails
         for (int i = w.lane; i < k; i += 32) {
             int i0 = i == 0 ? k - 1 : i - 1, i1 = i + 1 == k ? 0 : i + 1;
             int a = A.L[i0], b = A.L[i], c = A.L[i1];
             int2 pa = A.LX[i0], pb = A.LX[i], pc = A.LX[i1];
             // triangle (p, b, c) counter-clockwise with p at q
-            stays = stays && orient2d(q, pb, pc) > 0;
+            ccw = ccw && orient2d(q, pb, pc) > 0;
             // spoke p-b: c outside the circle of (p, a, b)
-            stays = stays && !conflict(p, a, b, q, pa, pb, c, pc, d.use_filter, &ex, &ti);
+            int fails = conflict(p, a, b, q, pa, pb, c, pc, d.use_filter, &ex, &ti) ? 1 : 0;
             // link edge b-c: the apex across it outside the circle of (p, b, c)
             int ref = A.ON[i];
             int4 ov = __ldcg(d.tv + (ref >> 2));
             int r = comp(ov, ref & 3);
             int2 pr = r >= 0 ? __ldcg(d.xy + r) : make_int2(0, 0);
-            stays = stays && !conflict(p, b, c, q, pb, pc, r, pr, d.use_filter, &ex, &ti);
+            if (conflict(p, b, c, q, pb, pc, r, pr, d.use_filter, &ex, &ti)) fails |= 2;
+            A.T[i] = fails;
         }
         cnt_add(w, C_EXACT, __reduce_add_sync(FULL, ex));
         cnt_add(w, C_TIES, __reduce_add_sync(FULL, ti));
-        stays = __all_sync(FULL, stays);
-        if (stays && w.lane == 0) {
+        ccw = __all_sync(FULL, ccw);
+        __syncwarp();
+        bool del = true;
+        for (int i = w.lane; i < k; i += 32) del = del && A.T[i] == 0;
+        del = __all_sync(FULL, del);
+        if (!ccw || (!del && !flip)) {
+            release_all(w, d);
+            return 0;
+        }
+        if (w.lane == 0) {
             d.xy[p] = q;
             __threadfence();
         }
         __syncwarp();
+        if (del) {
+            release_all(w, d);
+            return 1;
+        }
+        // the failing edges onto the flip stack (triangle i = (p, L[i], L[i+1]) holds p
+        // at index I[i]: the link edge is opposite p, the spoke p-L[i] opposite
+        // L[i+1]); their triangles (both sides of a spoke) to the dirty list
+        int top = 0;
+        for (int c0 = 0; c0 < k; c0 += 32) {
+            int i = c0 + w.lane;
+            int f = i < k ? A.T[i] : 0;
+            if (f) {
+                int im = i == 0 ? k - 1 : i - 1;
+                dirty_push(d, A.S[i]);
+                if (f & 1) dirty_push(d, A.S[im]);
+            }
+            unsigned sm = __ballot_sync(FULL, f & 1), lm = __ballot_sync(FULL, (f & 2) != 0);
+            int lt = __popc(sm & ((1u << w.lane) - 1u)) + __popc(lm & ((1u << w.lane) - 1u));
+            if (f & 1 && top + lt < STACK) w.sh->stack[top + lt] = make_int2(A.S[i], (A.I[i] + 2) % 3);
+            if (f & 2 && top + lt + (f & 1) < STACK) w.sh->stack[top + lt + (f & 1)] = make_int2(A.S[i], A.I[i]);
+            top += __popc(sm) + __popc(lm);
+        }
+        if (top > STACK) {
+            cnt_add(w, C_STACK_DROP, 1);
+            top = STACK;
+        }
+        __syncwarp();
         release_all(w, d);
-        return stays ? 1 : 0;
+        lawson(w, d, top, -2, false);
+        return 1;
     }
 }
 
@@ -1442,7 +1569,8 @@ __device__ __noinline__ int delete_point_big(Warp w, const Dev &d, int p, int &s
     return rc;
 }
 
-// move_in_place with the star in the warp's global scratch (degree above KMAX).
+// move_in_place with the star in the warp's global scratch (degree above KMAX), with
+// flips when the move keeps the star valid but not Delaunay.
 __device__ __noinline__ int move_in_place_big(Warp w, const Dev &d, int p, int2 q)
 {
     int *big = warp_big(d);
@@ -1450,7 +1578,7 @@ __device__ __noinline__ int move_in_place_big(Warp w, const Dev &d, int p, int2 
     __syncwarp();
     if (w.lane == 0) w.sh->clbig = 1;
     __syncwarp();
-    int rc = move_in_place(w, d, p, q, star_big(big));
+    int rc = move_in_place(w, d, p, q, star_big(big), true);
     __syncwarp();
     if (w.lane == 0) w.sh->clbig = 0;
     __syncwarp();

@@ -229,8 +229,10 @@ __device__ __noinline__ void step_tail(Warp w, const Dev &d, Inst I, int4 *defer
 
 // Entries of the deferred list: (p, s0, s1, hint) = an insertion left to the end of the
 // step (s0 >= 0); (p, DQ_MOVE - pass, qx, qy) = a whole move left for later, pass
-// counting how often it was left; DQ_DONE once a warp has taken it.
-constexpr int DQ_MOVE = -2, DQ_DONE = -100, DQ_PASSES = 3;
+// counting how often it was left; (p, DQ_HUGE, qx, qy) = the move of a point of degree
+// above KMAX, for the first warp that runs out of partitions; DQ_DONE once a warp has
+// taken it.
+constexpr int DQ_MOVE = -2, DQ_HUGE = -50, DQ_DONE = -100, DQ_PASSES = 3;
 
 // Append an entry.  The list is cleared to -1 before every step and the point id is
 // written last (after a fence), so a warp that takes a reserved but unwritten entry
@@ -273,10 +275,11 @@ __device__ __forceinline__ int4 read_deferred(Warp w, const int4 *deferred, int 
 }
 
 // One move of p to q (Fig. 4: Delete, Update, Insert): the staged move, else the
-// global-memory path.  may_give_up: a move whose claims keep failing, or whose point
-// has a degree above KMAX, returns MV_BIG untouched; otherwise claims are retried and a
-// high-degree point is deleted with its star in the warp's global scratch.  rc: 0, MV_BIG, INS_DEFER / MV_DEFER (p deleted and placed, its
-// insertion left to the end of the step with spares s0, s1 and hint), or an error.
+// global-memory path.  may_give_up: a move whose claims keep failing returns MV_BIG
+// untouched, one whose point has a degree above KMAX MV_HUGE; otherwise claims are
+// retried and a high-degree point is moved with its star in the warp's global scratch.
+// rc: 0, MV_BIG, MV_HUGE, INS_DEFER / MV_DEFER (p deleted and placed, its insertion
+// left to the end of the step with spares s0, s1 and hint), or an error.
 struct MoveOut {
     int rc, s0, s1, hint;
 };
@@ -287,10 +290,11 @@ __device__ __forceinline__ MoveOut run_move(Warp w, const Dev &d, int p, int2 q,
     int s0 = -1, s1 = -1, hint = -1;
     long long c0 = clock64();
     int rc = move_point(w, d, p, q, s0, s1, hint, may_give_up);
-    if (rc == MV_BIG && !may_give_up) {
+    if ((rc == MV_BIG || rc == MV_HUGE) && !may_give_up) {
         // a degree above KMAX: the star goes to the warp's global scratch.  A short
         // move that leaves every triangle of the star valid and Delaunay only changes
         // p's position; otherwise p is deleted and inserted again.
+        long long cb = clock64();
         rc = move_in_place_big(w, d, p, q);
         if (rc == 1) {
             rc = 0;
@@ -298,6 +302,8 @@ __device__ __forceinline__ MoveOut run_move(Warp w, const Dev &d, int p, int2 q,
             rc = delete_point_big(w, d, p, s0, s1, hint);
             if (rc == 0) rc = MV_GLOBAL;
         }
+        dev_count(w, d, C_BIG_MOVES, 1);
+        dev_count(w, d, C_CYC_BIG, (unsigned long long)(clock64() - cb));
     }
     if (rc == MV_GLOBAL) {
         cnt_add(w, C_MV_GLOBAL, 1);
@@ -324,8 +330,9 @@ __device__ __forceinline__ MoveOut run_move(Warp w, const Dev &d, int p, int2 q,
 __device__ __forceinline__ bool settle_move(Warp w, const Dev &d, int rc, int p, int2 q, int pass, int s0, int s1,
                                             int hint, int4 *deferred, int *defer_count, int defer_cap)
 {
-    if (rc == MV_BIG) {
-        push_deferred(w, d, deferred, defer_count, defer_cap, make_int4(p, DQ_MOVE - pass, q.x, q.y));
+    if (rc == MV_BIG || rc == MV_HUGE) {
+        push_deferred(w, d, deferred, defer_count, defer_cap,
+                      make_int4(p, rc == MV_HUGE ? DQ_HUGE : DQ_MOVE - pass, q.x, q.y));
         return true;
     }
     if (rc == MV_DEFER || rc == INS_DEFER) {
@@ -358,6 +365,7 @@ __global__ void __launch_bounds__(WPB * 32, 7) k_kinetic(Dev dp, const int3 *mov
     bool tickets = true;
     while (true) {
         int p, pass = 0;
+        bool huge = false;  // a high-degree point's move, run without giving up
         int2 q;
         if (tickets) {
             // next move of this work item (every wpp-th of the partition's list)
@@ -407,16 +415,19 @@ __global__ void __launch_bounds__(WPB * 32, 7) k_kinetic(Dev dp, const int3 *mov
             int4 e = read_deferred(w, deferred, j);
             // an unpublished entry, an insertion (for the end), a taken entry, or a move
             // left too often: the last warp takes those
-            if (e.x < 0 || e.y > DQ_MOVE || e.y <= DQ_DONE || DQ_MOVE - e.y >= DQ_PASSES) continue;
+            if (e.x < 0 || e.y > DQ_MOVE || e.y <= DQ_DONE) continue;
+            huge = e.y == DQ_HUGE;
+            if (!huge && DQ_MOVE - e.y >= DQ_PASSES) continue;
             if (w.lane == 0) deferred[j].y = DQ_DONE;
             __syncwarp();
-            pass = DQ_MOVE - e.y + 1;
+            pass = huge ? 0 : DQ_MOVE - e.y + 1;
+            dev_count(w, d, C_DRAIN_MOVES, 1);
             p = e.x;
             q = make_int2(e.z, e.w);
             int inst = I.ninst > 1 ? csr_find(I.pofs, I.ninst + 1, p) : 0;
             set_instance(w, I.pofs[inst], I.pofs[inst + 1] - I.pofs[inst]);
         }
-        MoveOut o = run_move(w, d, p, q, true);
+        MoveOut o = run_move(w, d, p, q, !huge);
         if (!settle_move(w, d, o.rc, p, q, pass, o.s0, o.s1, o.hint, deferred, defer_count, defer_cap)) break;
     }
     // the last warp to finish does the tail work
@@ -502,43 +513,57 @@ __device__ __noinline__ void step_tail(Warp w, const Dev &d, Inst I, int4 *defer
                                        int defer_cap, int *viol, int viol_cap)
 {
     if (read_status(d)) return;
-    int cnt = __shfl_sync(FULL, __ldcg(defer_count), 0);
-    if (cnt > defer_cap) cnt = defer_cap;
-    // whole moves not taken yet (left by the last warps), without giving up; an
-    // insertion onto a point still to be inserted is deferred again
-    for (int j = 0; j < min(__shfl_sync(FULL, __ldcg(defer_count), 0), defer_cap); ++j) {
-        if (read_status(d)) return;
-        int4 e = read_deferred(w, deferred, j);
-        if (e.x < 0) continue;
-        if (e.y > DQ_MOVE || e.y <= DQ_DONE) continue;
-        if (w.lane == 0) deferred[j].y = DQ_DONE;
-        __syncwarp();
-        int p = e.x;
-        int2 q = make_int2(e.z, e.w);
-        int inst = I.ninst > 1 ? csr_find(I.pofs, I.ninst + 1, p) : 0;
-        set_instance(w, I.pofs[inst], I.pofs[inst + 1] - I.pofs[inst]);
-        MoveOut o = run_move(w, d, p, q, false);
-        if (o.rc == MV_BIG) o.rc = DEV_INTERNAL;  // never returned without giving up
-        if (!settle_move(w, d, o.rc, p, q, DQ_PASSES, o.s0, o.s1, o.hint, deferred, defer_count, defer_cap)) return;
-    }
-    __threadfence();
-    cnt = __shfl_sync(FULL, __ldcg(defer_count), 0);
-    if (cnt > defer_cap) cnt = defer_cap;
-    for (int j = 0; j < cnt; ++j) {
-        if (read_status(d)) return;
-        int4 e = read_deferred(w, deferred, j);
-        if (e.x < 0 || e.y < 0) continue;  // whole moves (done above)
-        int2 q = __ldcg(d.xy + e.x);
-        q = bcast2(q, 0);
-        int inst = I.ninst > 1 ? csr_find(I.pofs, I.ninst + 1, e.x) : 0;
-        set_instance(w, I.pofs[inst], I.pofs[inst + 1] - I.pofs[inst]);
-        int rc = insert_staged(w, d, e.x, q, e.w, e.y, e.z, false);
-        if (rc == INS_GLOBAL) rc = insert_point(w, d, e.x, q, e.w, e.y, e.z, false);
-        if (rc) {
-            if (rc > 0 && w.lane == 0 && atomicCAS(d.status, 0, rc) == 0) d.status[S_FAILPT] = e.x;
-            return;
+    const long long c0 = clock64();
+    // Every other warp has finished, so every entry is published.  The lanes read 32
+    // entries at a time and the warp runs the ones with work in list order; entries
+    // appended meanwhile are read when the scan reaches them.  Pass 0: whole moves not
+    // taken yet (left by the last warps), run without giving up (an insertion onto a
+    // point still to be inserted is deferred again); pass 1: the deferred insertions.
+    for (int pass = 0; pass < 2; ++pass) {
+        int scanned = 0;
+        while (true) {
+            if (read_status(d)) return;
+            int cnt = min(__shfl_sync(FULL, __ldcg(defer_count), 0), defer_cap);
+            if (scanned >= cnt) break;
+            int j = scanned + w.lane;
+            int4 e = j < cnt ? __ldcg(deferred + j) : make_int4(-1, 0, 0, 0);
+            bool todo = e.x >= 0 && (pass == 0 ? (e.y <= DQ_MOVE && e.y > DQ_DONE) : e.y >= 0);
+            unsigned tm = __ballot_sync(FULL, todo);
+            scanned = min(scanned + 32, cnt);
+            while (tm) {
+                const int src = __ffs(tm) - 1;
+                tm &= tm - 1u;
+                int4 ei = bcast4(e, src);
+                if (pass == 0) {
+                    if (w.lane == 0) deferred[j - w.lane + src].y = DQ_DONE;
+                    __syncwarp();
+                    int p = ei.x;
+                    int2 q = make_int2(ei.z, ei.w);
+                    int inst = I.ninst > 1 ? csr_find(I.pofs, I.ninst + 1, p) : 0;
+                    set_instance(w, I.pofs[inst], I.pofs[inst + 1] - I.pofs[inst]);
+                    MoveOut o = run_move(w, d, p, q, false);
+                    dev_count(w, d, C_TAIL_MOVES, 1);
+                    if (o.rc == MV_BIG || o.rc == MV_HUGE) o.rc = DEV_INTERNAL;  // never returned without giving up
+                    if (!settle_move(w, d, o.rc, p, q, DQ_PASSES, o.s0, o.s1, o.hint, deferred, defer_count,
+                                     defer_cap))
+                        return;
+                } else {
+                    int2 q = __ldcg(d.xy + ei.x);
+                    q = bcast2(q, 0);
+                    int inst = I.ninst > 1 ? csr_find(I.pofs, I.ninst + 1, ei.x) : 0;
+                    set_instance(w, I.pofs[inst], I.pofs[inst + 1] - I.pofs[inst]);
+                    int rc = insert_staged(w, d, ei.x, q, ei.w, ei.y, ei.z, false);
+                    if (rc == INS_GLOBAL) rc = insert_point(w, d, ei.x, q, ei.w, ei.y, ei.z, false);
+                    if (rc) {
+                        if (rc > 0 && w.lane == 0 && atomicCAS(d.status, 0, rc) == 0) d.status[S_FAILPT] = ei.x;
+                        return;
+                    }
+                }
+            }
         }
+        __threadfence();
     }
+    dev_count(w, d, C_CYC_TAIL, (unsigned long long)(clock64() - c0));
     __threadfence();
     int hi = __shfl_sync(FULL, __ldcg(d.dirty_count), 0);
     if (hi > 4096) {

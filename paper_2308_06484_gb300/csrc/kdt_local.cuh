@@ -32,10 +32,10 @@ namespace kd {
 
 // outcome of move_point
 // (0, negative: none of them a DevStatus, which are all positive)
-// MV_BIG: p's degree is above what the shared arrays hold (KMAX), or its claims kept
-// failing; nothing was done, the move is left to the end of the step, when no other
-// warp competes for claims.
-enum MoveResult : int { MV_DONE = 0, MV_DEFER = -20, MV_GLOBAL = -21, MV_BIG = -22, MV_ABORT = -1 };
+// MV_BIG: p's claims kept failing; MV_HUGE: p's degree is above what the shared arrays
+// hold (KMAX).  Nothing was done in either case: the move is left for later, when
+// fewer warps compete for claims (MV_HUGE then takes the warp's global scratch).
+enum MoveResult : int { MV_DONE = 0, MV_DEFER = -20, MV_GLOBAL = -21, MV_BIG = -22, MV_HUGE = -23, MV_ABORT = -1 };
 
 struct Region {
     int cnt;                   // staged triangles
@@ -550,7 +550,7 @@ __device__ int move_point(Warp w, const Dev &d, int p, int2 q, int &s0, int &s1,
         int k = gather_star(w, d, p);
         long long t1 = clock64();
         cnt_add(w, C_CYC_GATHER, (unsigned)((t1 - t0) >> 6));
-        if (k == -2 && d.big) return MV_BIG;
+        if (k == -2 && d.big) return MV_HUGE;
         if (k == -2 && attempt == d.retry_cap) return DEV_DEGREE;
         if (k < 3 || 2 * k + 8 > LM) {
             if (k >= 3) {
@@ -558,6 +558,7 @@ __device__ int move_point(Warp w, const Dev &d, int p, int2 q, int &s0, int &s1,
                 // whole move to the end of the step when its claims keep failing)
                 int rc = delete_point(w, d, p, s0, s1, hint, may_give_up && d.big != nullptr);
                 if (rc == DEL_BUSY) return MV_BIG;
+                if (rc == DEL_HUGE) return MV_HUGE;
                 return rc ? rc : MV_GLOBAL;
             }
             backoff(w, attempt);

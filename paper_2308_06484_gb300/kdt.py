@@ -54,7 +54,7 @@ _STAT_FIELDS2 = ["staged_to_global", "cycles_move", "cycles_move_max", "cycles_g
                  "cycles_local", "cycles_writeback"]
 
 _STAT_FIELDS3 = ["cycles_ear", "cycles_lawson", "cycles_certify", "proposal_moves", "proposal_hits",
-                 "trace_rows"]
+                 "trace_rows", "tail_moves", "cycles_tail", "big_moves", "cycles_big", "drain_moves"]
 
 
 class Stats(ctypes.Structure):
@@ -65,7 +65,7 @@ class Stats(ctypes.Structure):
                 + [("step_graph_ms", ctypes.c_double), ("tuned_points_per_partition", ctypes.c_int64),
                    ("tuned_warps_per_partition", ctypes.c_int64)]
                 + [(f, ctypes.c_int64) for f in _STAT_FIELDS3]
-                + [("reserved", ctypes.c_int64 * 8)])
+                + [("reserved", ctypes.c_int64 * 3)])
 
 
 _lib = None

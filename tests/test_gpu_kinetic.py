@@ -238,3 +238,61 @@ def test_variant_in_place_moves(make):
     assert st["fallbacks"] == 0
     assert st["deletes"] < st["moves"]  # some moves were done in place
     assert t.verify() == 0
+
+
+def _row_points(seed):
+    """A straight row of 1000 points (spacing 64) with a few points beside it at heights
+    of 600-2500 (each with a hundred or more row points in its star: degrees above the
+    64 a shared-memory star holds), some of them with a companion a few units away (so
+    that a short move can turn a triangle of the star over), and background points far
+    from the row."""
+    rng = np.random.default_rng(seed)
+    y0 = 1 << 21
+    row = np.stack([30000 + 64 * np.arange(1000), np.full(1000, y0)], 1)
+    xs = 30000 + np.linspace(3000, 60000, 8).astype(np.int64) + 29
+    hs = np.array([650, 900, 1400, 2500, -700, -1000, -1600, -2300])
+    side = np.stack([xs, y0 + hs], 1)
+    comp = side[[0, 2, 5, 7]] + np.array([[5, 3], [-4, 6], [6, -2], [3, 5]])
+    bg = rng.integers(0, 1 << 22, size=(6000, 2))
+    bg = bg[np.abs(bg[:, 1] - y0) > 60000][:2000]
+    xy = np.concatenate([row, side, comp, bg]).astype(np.int32)
+    assert np.unique(xy, axis=0).shape[0] == xy.shape[0]
+    return xy, np.arange(1000, 1012)
+
+
+def test_high_degree_points_move():
+    """Points of degree above 64 (star in the warp's global scratch) moved by 1-8 units
+    every step, beside and across their companions' edges: moved in place (with flips
+    where the star stays valid but not Delaunay) or deleted (incremental ear clipping
+    over a link of ~100 collinear row points) and inserted; the oracle's triangulation
+    after every step."""
+    import torch
+    from paper_2308_06484_gb300 import kdt
+    xy, movers = _row_points(61)
+    t = kdt.Triangulation(kdt.default_config(grid=16, domain_bits=22))
+    t.build(xy)
+    assert_same(t.export_triangles(), xy, "initial")
+    t.reset_stats()
+    rng = np.random.default_rng(62)
+    occ = set(map(tuple, xy.tolist()))
+    dirs = [(1, 0), (-1, 0), (0, 1), (0, -1)]
+    for s in range(12):
+        mv = []
+        ids = list(movers) + list(rng.choice(np.arange(1012, xy.shape[0]), 20, replace=False))
+        for p in ids:
+            for _ in range(16):
+                dx, dy = dirs[int(rng.integers(0, 4))]
+                k = int(rng.integers(1, 9))
+                q = (int(xy[p, 0]) + dx * k, int(xy[p, 1]) + dy * k)
+                if 0 <= q[0] < 1 << 22 and 0 <= q[1] < 1 << 22 and q not in occ:
+                    occ.discard(tuple(xy[p].tolist()))
+                    occ.add(q)
+                    xy[p] = q
+                    mv.append((p, q[0], q[1]))
+                    break
+        t.step(torch.from_numpy(np.array(mv, dtype=np.int32)).cuda())
+        assert_same(t.export_triangles(), xy, "row step %d" % s)
+    st = t.stats()
+    assert st["fallbacks"] == 0
+    assert st["big_moves"] > 0
+    assert t.verify() == 0
