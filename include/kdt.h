@@ -81,7 +81,8 @@ typedef struct {
     int32_t build_warps;   /* warps inserting concurrently during a build (0 = auto)         */
     int32_t kinetic_warps; /* warps moving points concurrently in a step (0 = one per cell)  */
     int32_t debug;         /* bit 0: on an in-step failure keep the failed state (no
-                              fallback, no roll-back) so kdt_export_store can inspect it     */
+                              fallback, no roll-back) so kdt_export_store can inspect it;
+                              bit 1: record the kinetic launch's timeline (span_* stats)     */
     int32_t use_graph;     /* 1: launch each step as one captured CUDA graph (default)       */
     int32_t points_per_partition; /* partition size of batched instances (0 = 256)           */
     int32_t warps_per_partition;  /* warps sharing one partition's moves (0 = 1)             */
@@ -121,7 +122,15 @@ typedef struct {
     int64_t big_moves;            /* moves of points of degree above 64 (star in scratch)    */
     int64_t cycles_big;           /* SM cycles of those moves                                */
     int64_t drain_moves;          /* moves taken again from the list of moves left for later */
-    int64_t reserved[3];
+    int64_t span_tickets_ns;      /* kinetic launches (global timer, summed; debug bit 1):  */
+                                  /* start to the                                           */
+    int64_t span_drain_ns;        /* last warp out of partitions, to the last warp out of   */
+    int64_t span_kernel_ns;       /* the moves left for later, to the end of the step tail  */
+    int64_t span_huge_ns;         /* ... start to the end of the last high-degree move      */
+    int64_t span_drained_ns;      /* ... start to the end of the last other drained move    */
+    int64_t cycles_drained_max;   /* longest move taken from the list, cycles (debug bit 1) */
+    int64_t redeferred;           /* drained moves left for later again (debug bit 1)       */
+    int64_t reserved[8];
 } kdt_stats;
 
 /* ---- lifecycle ------------------------------------------------------------------ */
@@ -233,6 +242,9 @@ const char *kdt_error_string(int code);
 
 /* ABI version (incremented on any incompatible change). */
 int kdt_version(void);
+
+/* sizeof(kdt_stats) as this library was built (a binding checks its own layout). */
+int64_t kdt_stats_size(void);
 
 /* ---- diagnostics ---------------------------------------------------------------- */
 

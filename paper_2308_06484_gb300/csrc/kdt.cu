@@ -26,7 +26,7 @@ using namespace kd;
 
 namespace {
 
-constexpr int ABI_VERSION = 3;
+constexpr int ABI_VERSION = 4;
 
 struct Buf {
     void *p = nullptr;
@@ -208,6 +208,7 @@ Dev make_dev(kdt *h)
     d.trace_cap = h->trace_cap;
     d.big = nullptr;  // set for the kinetic launch only (enqueue_step)
     d.variant = h->cfg.variant;
+    d.timeline = (h->cfg.debug >> 1) & 1;
     return d;
 }
 
@@ -575,6 +576,13 @@ void add_counters(kdt *h)
     s.big_moves += c[C_BIG_MOVES];
     s.cycles_big += (int64_t)c[C_CYC_BIG];
     s.drain_moves += c[C_DRAIN_MOVES];
+    s.span_tickets_ns += (int64_t)c[C_SPAN_TICKETS];
+    s.span_drain_ns += (int64_t)c[C_SPAN_DRAIN];
+    s.span_kernel_ns += (int64_t)c[C_SPAN_ALL];
+    s.span_huge_ns += (int64_t)c[C_SPAN_HUGE];
+    s.span_drained_ns += (int64_t)c[C_SPAN_DRAINED];
+    if ((int64_t)c[C_DRAINED_MAX] > s.cycles_drained_max) s.cycles_drained_max = (int64_t)c[C_DRAINED_MAX];
+    s.redeferred += (int64_t)c[C_REDEFER];
 }
 
 // Undo a step that failed after it started: restore the old positions and rebuild.
@@ -938,6 +946,8 @@ int build_impl(kdt *h, const int32_t *xy, const int64_t *offs, int n_inst)
 extern "C" {
 
 int kdt_version(void) { return ABI_VERSION; }
+
+int64_t kdt_stats_size(void) { return (int64_t)sizeof(kdt_stats); }
 
 const char *kdt_error_string(int code)
 {

@@ -69,6 +69,10 @@ enum Counter : int {
     C_CYC_MAX = C_NUM,  // a second device slot, updated with atomicMax
     // device-only slots for rare events, added straight to global memory (dev_count)
     C_TAIL_MOVES, C_CYC_TAIL, C_BIG_MOVES, C_CYC_BIG, C_DRAIN_MOVES,
+    // timeline of a kinetic launch (global timer, ns): its start, the latest end of a
+    // warp's partitions and of its drain; summed spans from the start
+    C_T0, C_TT, C_TD, C_SPAN_TICKETS, C_SPAN_DRAIN, C_SPAN_ALL,
+    C_TH, C_TDM, C_SPAN_HUGE, C_SPAN_DRAINED, C_DRAINED_MAX, C_REDEFER,
     C_SLOTS
 };
 
@@ -106,6 +110,7 @@ struct Dev {
     int retry_cap;
     int trace_cap;
     int variant;         // 1: try a move in place before delete + insert (kdt_config.variant)
+    int timeline;        // record the kinetic launch's timeline (the C_T* / C_SPAN* slots)
 };
 
 constexpr int KBIG = 1024;                  // largest degree the global deletion handles
@@ -318,6 +323,13 @@ __device__ __forceinline__ void flush_counters(Warp w, const Dev &d)
     }
 }
 
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // a rare event, counted straight into the device slot
 __device__ __forceinline__ void dev_count(const Warp w, const Dev &d, int i, unsigned long long v)
 {
@@ -363,15 +375,39 @@ __device__ __forceinline__ int csr_find(const int *off, int cnt, int x)
 
 // ------------------------------------------------------------------ claims
 
+// Claim tokens with this bit are "patient": the warp is on a move that must not keep
+// losing (the star of a high-degree point, claimed whole).  A patient
+// claim waits (bounded) for a slot another warp holds, unless the holder is patient
+// too and has the smaller token; then it fails like any claim.  Other claims never
+// wait while holding slots, and patient waits only go from a smaller to a larger
+// token, so no cycle of waiting warps can form.
+constexpr int TOK_PATIENT = 1 << 30;
+constexpr int PATIENCE = 1 << 13;  // tries per slot (back-off up to ~1 us: < 10 ms)
+
+// A patient claim of `slot` that found it held by `old`: wait for it (see above).
+// Returns the last owner word seen (0 or token: claimed).
+__device__ __noinline__ int claim_wait(const Dev &d, int slot, int token, int old)
+{
+    for (int it = 0; it < PATIENCE; ++it) {
+        if ((old & TOK_PATIENT) && old < token) break;
+        __nanosleep(32u << (it < 5 ? it : 5));
+        old = atomicCAS(&d.tn[slot].w, 0, token);
+        if (old == 0 || old == token) break;
+    }
+    return old;
+}
+
 // Try to claim the slots lane j holds in `mine` (j < m).  Returns true when every
 // slot is now owned by this warp.  Newly taken slots are appended to the claim
 // list either way; the caller releases everything on failure.
+template <bool PATIENT = false>
 __device__ __forceinline__ bool claim_lanes(Warp w, const Dev &d, int mine, int m)
 {
     bool ok = true, added = false;
     if (w.lane < m && mine >= d.cap) ok = false;  // never a slot: fail the claim, touch nothing
     if (w.lane < m && mine >= 0 && mine < d.cap) {
         int old = atomicCAS(&d.tn[mine].w, 0, w.token);
+        if (PATIENT && old != 0 && old != w.token) old = claim_wait(d, mine, w.token, old);
         ok = (old == 0) || (old == w.token);
         added = (old == 0);
     }
@@ -387,16 +423,24 @@ __device__ __forceinline__ bool claim_lanes(Warp w, const Dev &d, int mine, int 
 }
 
 // Claim a list (any length; the caller keeps ncl + m <= the claim list's capacity).
+template <bool PATIENT = false>
 __device__ __forceinline__ bool claim_list(Warp w, const Dev &d, const int *list, int m)
 {
     bool all = true;
     for (int base = 0; base < m; base += 32) {
         int j = base + w.lane;
         int mine = j < m ? list[j] : -1;
-        all = claim_lanes(w, d, mine, m - base < 32 ? m - base : 32) && all;
+        all = claim_lanes<PATIENT>(w, d, mine, m - base < 32 ? m - base : 32) && all;
         if (!all) break;
     }
     return all;
+}
+
+// claim_list, patient when the warp's token says so (the global-memory deletions and
+// in-place moves of a high-degree point's star)
+__device__ __forceinline__ bool claim_star_list(Warp w, const Dev &d, const int *list, int m)
+{
+    return (w.token & TOK_PATIENT) ? claim_list<true>(w, d, list, m) : claim_list<false>(w, d, list, m);
 }
 
 __device__ __forceinline__ void release_all(Warp w, const Dev &d)
@@ -408,6 +452,19 @@ __device__ __forceinline__ void release_all(Warp w, const Dev &d)
         for (int i = 0; i < w.sh->ncl; ++i) atomicExch(&d.tn[cl[i]].w, 0);
         w.sh->ncl = 0;
     }
+    __syncwarp();
+}
+
+// release_all for a long claim list (a star gathered whole): all lanes clear words
+__device__ __forceinline__ void release_star(Warp w, const Dev &d)
+{
+    __threadfence();  // every lane's writes are visible before any owner word clears
+    __syncwarp();
+    const int n = w.sh->ncl;
+    const int *cl = claim_list_of(w, d);
+    for (int i = w.lane; i < n; i += 32) atomicExch(&d.tn[cl[i]].w, 0);
+    __syncwarp();
+    if (w.lane == 0) w.sh->ncl = 0;
     __syncwarp();
 }
 
@@ -1199,8 +1256,8 @@ __device__ __noinline__ int delete_point_in(Warp w, const Dev &d, int p, int &sp
         // claim the star and the outer ring
         for (int i = w.lane; i < k; i += 32) A.T[i] = A.ON[i] >> 2;
         __syncwarp();
-        bool ok = claim_list(w, d, A.S, k);
-        if (ok) ok = claim_list(w, d, A.T, k);
+        bool ok = claim_star_list(w, d, A.S, k);
+        if (ok) ok = claim_star_list(w, d, A.T, k);
         if (ok) {
             // validate the gathered star under the claims (one parallel pass)
             bool good = true;
@@ -1214,7 +1271,7 @@ __device__ __noinline__ int delete_point_in(Warp w, const Dev &d, int p, int &sp
             ok = __all_sync(FULL, good);
         }
         if (!ok) {
-            release_all(w, d);
+            release_star(w, d);
             if (may_give_up && ++busy >= DEFER_AFTER) return DEL_BUSY;
             backoff(w, attempt);
             continue;
@@ -1244,7 +1301,7 @@ __device__ __noinline__ int delete_point_in(Warp w, const Dev &d, int p, int &sp
                     if (ov.x != KDT_GHOST && ov.y != KDT_GHOST && ov.z != KDT_GHOST) finite_ring = true;
                 }
                 if (!__any_sync(FULL, finite_ring)) {
-                    release_all(w, d);
+                    release_star(w, d);
                     return DEV_DEGENERATE;
                 }
             }
@@ -1308,7 +1365,7 @@ __device__ __noinline__ int delete_point_in(Warp w, const Dev &d, int p, int &sp
             }
             if (ns == 0) {
                 // cannot happen for a valid star; leave the store to the fallback
-                release_all(w, d);
+                release_star(w, d);
                 return DEV_INTERNAL;
             }
             // the clipped ears in index order
@@ -1419,7 +1476,7 @@ __device__ __noinline__ int delete_point_in(Warp w, const Dev &d, int p, int &sp
         }
         cnt_add(w, C_DEG_DEL, k);
         cnt_add(w, C_DELETES, 1);
-        release_all(w, d);
+        release_star(w, d);
         return DEV_OK;
     }
 }
@@ -1456,8 +1513,8 @@ __device__ __noinline__ int move_in_place(Warp w, const Dev &d, int p, int2 q, S
         }
         for (int i = w.lane; i < k; i += 32) A.T[i] = A.ON[i] >> 2;
         __syncwarp();
-        bool ok = claim_list(w, d, A.S, k);
-        if (ok) ok = claim_list(w, d, A.T, k);
+        bool ok = claim_star_list(w, d, A.S, k);
+        if (ok) ok = claim_star_list(w, d, A.T, k);
         if (ok) {
             bool good = true;
             for (int i = w.lane; i < k; i += 32) {
@@ -1470,7 +1527,7 @@ __device__ __noinline__ int move_in_place(Warp w, const Dev &d, int p, int2 q, S
             ok = __all_sync(FULL, good);
         }
         if (!ok) {
-            release_all(w, d);
+            release_star(w, d);
             backoff(w, attempt);
             continue;
         }
@@ -1481,7 +1538,7 @@ __device__ __noinline__ int move_in_place(Warp w, const Dev &d, int p, int2 q, S
             A.LX[i] = lv >= 0 ? __ldcg(d.xy + lv) : make_int2(0, 0);
         }
         if (__any_sync(FULL, hull)) {
-            release_all(w, d);
+            release_star(w, d);
             return 0;
         }
         __syncwarp();
@@ -1512,7 +1569,7 @@ __device__ __noinline__ int move_in_place(Warp w, const Dev &d, int p, int2 q, S
         for (int i = w.lane; i < k; i += 32) del = del && A.T[i] == 0;
         del = __all_sync(FULL, del);
         if (!ccw || (!del && !flip)) {
-            release_all(w, d);
+            release_star(w, d);
             return 0;
         }
         if (w.lane == 0) {
@@ -1521,7 +1578,7 @@ __device__ __noinline__ int move_in_place(Warp w, const Dev &d, int p, int2 q, S
         }
         __syncwarp();
         if (del) {
-            release_all(w, d);
+            release_star(w, d);
             return 1;
         }
         // the failing edges onto the flip stack (triangle i = (p, L[i], L[i+1]) holds p
@@ -1547,7 +1604,7 @@ __device__ __noinline__ int move_in_place(Warp w, const Dev &d, int p, int2 q, S
             top = STACK;
         }
         __syncwarp();
-        release_all(w, d);
+        release_star(w, d);
         lawson(w, d, top, -2, false);
         return 1;
     }

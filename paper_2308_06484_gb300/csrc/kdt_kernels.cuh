@@ -17,7 +17,9 @@ constexpr int DEV_DUP_ID = 10;  // a move id repeated within one step (found at 
 enum Slot : int {
     S_STATUS = 0, S_DIRTY = 1, S_VIOL = 2, S_TRIS = 3, S_DEFER = 4, S_THIRD = 5,
     S_MINX = 6, S_MINY = 7, S_MAXX = 8, S_MAXY = 9, S_TOTAL = 10, S_BAD = 11, S_ALIVE = 12,
-    S_WRAPS = 13, S_FAILPT = 14, S_DONE = 15, S_CERTPEND = 16, S_TICKET = 17, S_DNEXT = 18, S_NUM = 20
+    S_WRAPS = 13, S_FAILPT = 14, S_DONE = 15, S_CERTPEND = 16, S_TICKET = 17, S_DNEXT = 18,
+    S_DRUN = 19,  // warps running a move taken from the deferred list (kinetic launch)
+    S_NUM = 20
 };
 
 // Instance tables (one instance for kdt_build; many for kdt_build_batch).  Every
@@ -292,14 +294,17 @@ __device__ __forceinline__ MoveOut run_move(Warp w, const Dev &d, int p, int2 q,
     int rc = move_point(w, d, p, q, s0, s1, hint, may_give_up);
     if ((rc == MV_BIG || rc == MV_HUGE) && !may_give_up) {
         // a degree above KMAX: the star goes to the warp's global scratch.  A short
-        // move that leaves every triangle of the star valid and Delaunay only changes
-        // p's position; otherwise p is deleted and inserted again.
+        // move that keeps every triangle of the star valid changes p's position (and
+        // flips the star's edges that stop being Delaunay); otherwise p is deleted and
+        // inserted again.  Its claims are patient.
         long long cb = clock64();
-        rc = move_in_place_big(w, d, p, q);
+        Warp wb = w;
+        wb.token |= TOK_PATIENT;
+        rc = move_in_place_big(wb, d, p, q);
         if (rc == 1) {
             rc = 0;
         } else if (rc == 0) {
-            rc = delete_point_big(w, d, p, s0, s1, hint);
+            rc = delete_point_big(wb, d, p, s0, s1, hint);
             if (rc == 0) rc = MV_GLOBAL;
         }
         dev_count(w, d, C_BIG_MOVES, 1);
@@ -346,6 +351,89 @@ __device__ __forceinline__ bool settle_move(Warp w, const Dev &d, int rc, int p,
     return true;
 }
 
+// A warp stops running a move taken from the deferred list; the entries it pushed
+// were counted first.
+__device__ __noinline__ void drain_stop(Warp w, const Dev &d)
+{
+    if (w.lane == 0) {
+        __threadfence();
+        atomicSub(d.status + S_DRUN, 1);
+    }
+    __syncwarp();
+}
+
+// A move taken from the deferred list: j < 0 when there is none to take (stop
+// draining), skip when the entry is not this phase's work.
+struct Drained {
+    int j, p, pass;
+    int2 q;
+    bool skip, huge;
+};
+
+// Reserve the next entry of the deferred list with one atomic add (a compare-and-swap
+// loop on one word costs entries x contenders atomics when thousands of warps drain at
+// once).  An entry reserved before it was pushed is waited for while a warp may still
+// push one (one is still on its partitions: a warp leaves them with the one ticket it
+// takes beyond the last; or one is on a move from the list); one pushed after all of
+// them stopped is left to the last warp.  A taken move counts as running (S_DRUN)
+// until drain_stop.
+__device__ __noinline__ Drained take_deferred(Warp w, const Dev &d, int4 *deferred, const int *defer_count,
+                                              int defer_cap, int items, int nw)
+{
+    Drained t;
+    t.j = -1;
+    t.skip = false;
+    t.huge = false;
+    t.p = -1;
+    t.pass = 0;
+    t.q = make_int2(0, 0);
+    if (read_status(d)) return t;
+    int j = -1;
+    if (w.lane == 0) {
+        if (__ldcg(d.status + S_DNEXT) < min(__ldcg(defer_count), defer_cap)) {
+            const int r = atomicAdd(d.status + S_DNEXT, 1);
+            for (int spin = 0; spin < (1 << 16) && r < defer_cap; ++spin) {
+                if (r < min(__ldcg(defer_count), defer_cap)) {
+                    j = r;
+                    break;
+                }
+                if (__ldcg(d.status + S_TICKET) - items >= nw && __ldcg(d.status + S_DRUN) == 0) break;
+                __nanosleep(256);
+            }
+            if (j >= 0) atomicAdd(d.status + S_DRUN, 1);
+        }
+    }
+    t.j = __shfl_sync(FULL, j, 0);
+    if (t.j < 0) return t;
+    int4 e = read_deferred(w, deferred, t.j);
+    // an unpublished entry, an insertion (for the end), a taken entry, or a move left
+    // too often: the last warp takes those
+    bool skip = e.x < 0 || e.y > DQ_MOVE || e.y <= DQ_DONE;
+    t.huge = !skip && e.y == DQ_HUGE;
+    t.skip = skip || (!t.huge && DQ_MOVE - e.y >= DQ_PASSES);
+    if (t.skip) {
+        drain_stop(w, d);
+        return t;
+    }
+    if (w.lane == 0) deferred[t.j].y = DQ_DONE;
+    __syncwarp();
+    t.pass = t.huge ? 0 : DQ_MOVE - e.y + 1;
+    dev_count(w, d, C_DRAIN_MOVES, 1);
+    t.p = e.x;
+    t.q = make_int2(e.z, e.w);
+    return t;
+}
+
+// timeline notes of a drained move (debug)
+__device__ __noinline__ void drained_done(Warp w, const Dev &d, int rc, bool huge, long long cycles)
+{
+    if (d.timeline && d.counters && w.lane == 0) {
+        atomicMax(d.counters + (huge ? C_TH : C_TDM), global_ns());
+        atomicMax(d.counters + C_DRAINED_MAX, (unsigned long long)cycles);
+        if (rc == MV_BIG) atomicAdd(d.counters + C_REDEFER, 1ull);
+    }
+}
+
 __global__ void __launch_bounds__(WPB * 32, 7) k_kinetic(Dev dp, const int3 *moves, const int *head, const int *next,
                                                          Inst I, int ncells, int wpp, int4 *deferred,
                                                          int *defer_count, int defer_cap, int *viol, int viol_cap)
@@ -356,6 +444,8 @@ __global__ void __launch_bounds__(WPB * 32, 7) k_kinetic(Dev dp, const int3 *mov
     int gw = blockIdx.x * (blockDim.x >> 5) + wib;
     int nw = gridDim.x * (blockDim.x >> 5);
     Warp w = make_warp(&shs[wib], gw + 1, gw + 17 * d.stamp, d);
+    const bool tl = d.timeline && d.counters;
+    if (tl && gw == 0 && w.lane == 0) d.counters[C_T0] = global_ns();
     const int items = ncells * wpp;
     // One loop, one move per iteration: first the moves of the (partition, share) work
     // items the warp takes from a ticket; when those are gone, the whole moves left
@@ -378,6 +468,7 @@ __global__ void __launch_bounds__(WPB * 32, 7) k_kinetic(Dev dp, const int3 *mov
                 t = __shfl_sync(FULL, t, 0);
                 if (t >= items) {
                     tickets = false;
+                    if (tl && w.lane == 0) atomicMax(d.counters + C_TT, global_ns());
                     // nothing was left for later so far: this warp is done
                     if (__shfl_sync(FULL, w.lane == 0 ? __ldcg(defer_count) : 0, 0) == 0) break;
                     continue;
@@ -395,45 +486,30 @@ __global__ void __launch_bounds__(WPB * 32, 7) k_kinetic(Dev dp, const int3 *mov
             p = mv.x;
             q = make_int2(mv.y, mv.z);
         } else {
-            if (read_status(d)) break;
-            int j = -1;
-            if (w.lane == 0) {
-                int nx = __ldcg(d.status + S_DNEXT);
-                while (true) {
-                    int cnt = min(__ldcg(defer_count), defer_cap);
-                    if (nx >= cnt) break;
-                    int prev = atomicCAS(d.status + S_DNEXT, nx, nx + 1);
-                    if (prev == nx) {
-                        j = nx;
-                        break;
-                    }
-                    nx = prev;
-                }
-            }
-            j = __shfl_sync(FULL, j, 0);
-            if (j < 0) break;
-            int4 e = read_deferred(w, deferred, j);
-            // an unpublished entry, an insertion (for the end), a taken entry, or a move
-            // left too often: the last warp takes those
-            if (e.x < 0 || e.y > DQ_MOVE || e.y <= DQ_DONE) continue;
-            huge = e.y == DQ_HUGE;
-            if (!huge && DQ_MOVE - e.y >= DQ_PASSES) continue;
-            if (w.lane == 0) deferred[j].y = DQ_DONE;
-            __syncwarp();
-            pass = huge ? 0 : DQ_MOVE - e.y + 1;
-            dev_count(w, d, C_DRAIN_MOVES, 1);
-            p = e.x;
-            q = make_int2(e.z, e.w);
+            const Drained t = take_deferred(w, d, deferred, defer_count, defer_cap, items, nw);
+            if (t.j < 0) break;
+            if (t.skip) continue;
+            huge = t.huge;
+            pass = t.pass;
+            p = t.p;
+            q = t.q;
             int inst = I.ninst > 1 ? csr_find(I.pofs, I.ninst + 1, p) : 0;
             set_instance(w, I.pofs[inst], I.pofs[inst + 1] - I.pofs[inst]);
         }
+        const long long cm = tl ? clock64() : 0;
         MoveOut o = run_move(w, d, p, q, !huge);
-        if (!settle_move(w, d, o.rc, p, q, pass, o.s0, o.s1, o.hint, deferred, defer_count, defer_cap)) break;
+        if (!tickets) drained_done(w, d, o.rc, huge, tl ? clock64() - cm : 0);
+        if (!settle_move(w, d, o.rc, p, q, pass, o.s0, o.s1, o.hint, deferred, defer_count, defer_cap)) {
+            if (!tickets) drain_stop(w, d);
+            break;
+        }
+        if (!tickets) drain_stop(w, d);
     }
     // the last warp to finish does the tail work
     int done = 0;
     __syncwarp();
     if (w.lane == 0) {
+        if (tl) atomicMax(d.counters + C_TD, global_ns());
         __threadfence();
         done = atomicAdd(d.status + S_DONE, 1);
     }
@@ -441,6 +517,20 @@ __global__ void __launch_bounds__(WPB * 32, 7) k_kinetic(Dev dp, const int3 *mov
     if (done == nw - 1) {
         __threadfence();
         step_tail(w, d, I, deferred, defer_count, defer_cap, viol, viol_cap);
+        if (tl && w.lane == 0) {
+            unsigned long long t0 = __ldcg(d.counters + C_T0), tt = __ldcg(d.counters + C_TT);
+            unsigned long long td = __ldcg(d.counters + C_TD), now = global_ns();
+            if (t0 && tt >= t0) d.counters[C_SPAN_TICKETS] += tt - t0;
+            if (t0 && td >= t0) d.counters[C_SPAN_DRAIN] += td - t0;
+            if (t0 && now >= t0) d.counters[C_SPAN_ALL] += now - t0;
+            unsigned long long th = __ldcg(d.counters + C_TH), tdm = __ldcg(d.counters + C_TDM);
+            if (t0 && th >= t0) d.counters[C_SPAN_HUGE] += th - t0;
+            if (t0 && tdm >= t0) d.counters[C_SPAN_DRAINED] += tdm - t0;
+            d.counters[C_TT] = 0;
+            d.counters[C_TD] = 0;
+            d.counters[C_TH] = 0;
+            d.counters[C_TDM] = 0;
+        }
     }
     flush_counters(w, d);
 }

@@ -54,7 +54,9 @@ _STAT_FIELDS2 = ["staged_to_global", "cycles_move", "cycles_move_max", "cycles_g
                  "cycles_local", "cycles_writeback"]
 
 _STAT_FIELDS3 = ["cycles_ear", "cycles_lawson", "cycles_certify", "proposal_moves", "proposal_hits",
-                 "trace_rows", "tail_moves", "cycles_tail", "big_moves", "cycles_big", "drain_moves"]
+                 "trace_rows", "tail_moves", "cycles_tail", "big_moves", "cycles_big", "drain_moves",
+                 "span_tickets_ns", "span_drain_ns", "span_kernel_ns", "span_huge_ns", "span_drained_ns",
+                 "cycles_drained_max", "redeferred"]
 
 
 class Stats(ctypes.Structure):
@@ -65,7 +67,7 @@ class Stats(ctypes.Structure):
                 + [("step_graph_ms", ctypes.c_double), ("tuned_points_per_partition", ctypes.c_int64),
                    ("tuned_warps_per_partition", ctypes.c_int64)]
                 + [(f, ctypes.c_int64) for f in _STAT_FIELDS3]
-                + [("reserved", ctypes.c_int64 * 3)])
+                + [("reserved", ctypes.c_int64 * 8)])
 
 
 _lib = None
@@ -74,7 +76,7 @@ _lib = None
 SYMBOLS = ["kdt_default_config", "kdt_create", "kdt_destroy", "kdt_build", "kdt_step",
            "kdt_rebuild", "kdt_export_triangles", "kdt_export_points", "kdt_verify",
            "kdt_num_points", "kdt_get_stats", "kdt_reset_stats", "kdt_error_string",
-           "kdt_version", "kdt_eval_predicates", "kdt_export_store",
+           "kdt_version", "kdt_stats_size", "kdt_eval_predicates", "kdt_export_store",
            "kdt_export_triangles_noalloc", "kdt_build_batch", "kdt_step_batch",
            "kdt_export_triangles_inst", "kdt_num_instances", "kdt_set_trace", "kdt_trace_count",
            "kdt_set_proposal", "kdt_mlp_forward", "kdt_mlp_loss_grad", "kdt_mlp_adam"]
@@ -113,6 +115,7 @@ def load(build_if_stale: bool = True):
     L.kdt_error_string.argtypes = [i32]
     L.kdt_error_string.restype = ctypes.c_char_p
     L.kdt_version.restype = i32
+    L.kdt_stats_size.restype = i64
     L.kdt_eval_predicates.argtypes = [vp, vp, i64, vp, i32, vp]
     L.kdt_export_store.argtypes = [vp, vp, vp, vp, i64]
     L.kdt_export_triangles_noalloc.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
