@@ -22,6 +22,7 @@ Under torchrun (N > 1) every rank advances its own independent instance (replica
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -675,6 +676,19 @@ def main():
     torch.cuda.synchronize()
     rebuild_ms = statistics.median(a.elapsed_time(b) for a, b in evr)
 
+    # ---- d-calculation (Section III/IV) on the final state: N-th nearest neighbours of
+    # every point, per-partition and global minima (one warm-up call allocates scratch)
+    dcalc = {}
+    for N in (1, 4):
+        tri.d_values(N)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = 5
+        for _ in range(reps):
+            info = tri.d_values(N)
+        dcalc["N%d" % N] = {"ms": 1000.0 * (time.perf_counter() - t0) / reps, "min_dist": math.sqrt(info["min2"]),
+                            "spread": info["spread"]}
+
     check = None
     if args.check:
         import oracle
@@ -712,6 +726,7 @@ def main():
             "gpu_launches": int(launches),
             "fallbacks": int(fallbacks),
             "clocks": clk,
+            "d_calculation": dcalc,
         }
         if check is not None:
             line["final_state_matches_oracle"] = check

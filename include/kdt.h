@@ -225,6 +225,35 @@ int kdt_export_points(kdt *h, int32_t *xy, int64_t cap_points);
 #define KDT_NOALLOC_MAX_POINTS (1 << 20)
 int kdt_export_triangles_noalloc(kdt *h, int32_t *out, int64_t cap, int64_t *n_tri);
 
+/* ---- d-calculation (Section III "Notation and definitions"; Section IV) ------------
+ * For a constant N (1 <= N <= 16, N < the smallest instance's point count): for every
+ * point p, dist_p^2 = the squared distance to its N-th nearest other point of its own
+ * instance (exact int64); the minimum of dist_p^2 over the points of each partition
+ * (the grid cells of the steps: cell = (x * G >> domain_bits, y * G >> domain_bits),
+ * row-major, instances one after another) and over all points, mindistance(P)^2; and
+ * d^2 = the minimum of mindistance^2 over the calls since the last kdt_build /
+ * kdt_build_batch with the same N (the paper's d = min over the time steps; a call
+ * with another N starts the minimum again).  The N-th nearest neighbour is found on
+ * the triangulation (exact: see kdt_dcalc.cuh); nothing in the state changes.
+ *   dist2:     n int64 (host or device), or NULL;
+ *   cell_min2: one int64 per partition (host or device; INT64_MAX for an empty cell),
+ *              or NULL;
+ *   info:      host, required.
+ * Errors: KDT_ERR_ARG (N out of range, info NULL), KDT_ERR_STATE (not built),
+ * KDT_ERR_CUDA.  Allocates device scratch (neighbour lists, ~28 bytes per point). */
+typedef struct {
+    int64_t min2;     /* mindistance(P)^2 of this call                                     */
+    int64_t d2;       /* d^2: the running minimum (see above)                              */
+    double spread;    /* N-spread of a block, Delta_N(P_i) = diam(P_i) / d with diam(P_i)
+                         the cell's diagonal (one instance; 0 for a batch)                 */
+    int64_t max_degree; /* largest vertex degree met (the search's fan-out)                */
+    int64_t cells;    /* partitions (entries of cell_min2)                                 */
+} kdt_dinfo;
+int kdt_d_values(kdt *h, int32_t N, int64_t *dist2, int64_t *cell_min2, kdt_dinfo *info);
+
+/* Partitions of the current state (entries of kdt_d_values' cell_min2; 0 before a build). */
+int64_t kdt_num_cells(const kdt *h);
+
 /* Full GPU verifier: every triangle alive and counter-clockwise, adjacency
  * reciprocal, every edge locally Delaunay (SoS), 2n - 2 triangles with ghosts, every
  * point's incident-triangle pointer valid.  *bad receives the number of failures. */

@@ -21,6 +21,7 @@
 
 #include "../../include/kdt.h"
 #include "kdt_kernels.cuh"
+#include "kdt_dcalc.cuh"
 
 using namespace kd;
 
@@ -80,6 +81,10 @@ struct kdt {
     int scan_tmp_cap = 0;
     // build / export temporaries (kept between calls)
     Buf key, bord, hist, hoff, exp_cnt, exp_off, exp_fill, exp_out;
+    // d-calculation: neighbour lists, results, running minimum (per N)
+    Buf nb_deg, nb_off, nb_list, dc_dist, dc_cmin, dc_scal;
+    int64_t d2_run = INT64_MAX;
+    int d_n = 0;
     // graph-launched step: control words (moves, stamp, moves address) and the graph
     int *ctl = nullptr;   // device
     int *hctl = nullptr;  // pinned host
@@ -496,7 +501,8 @@ void free_state(kdt *h)
     h->d_pofs = nullptr; h->d_cofs = nullptr; h->d_grid = nullptr; h->d_moff = nullptr; h->h_moff = nullptr;
     h->d_tofs = nullptr;
     h->mcap = 0; h->dirty_cap = 0; h->scan_tmp_cap = 0;
-    Buf *bs[] = {&h->key, &h->bord, &h->hist, &h->hoff, &h->exp_cnt, &h->exp_off, &h->exp_fill, &h->exp_out};
+    Buf *bs[] = {&h->key, &h->bord, &h->hist, &h->hoff, &h->exp_cnt, &h->exp_off, &h->exp_fill, &h->exp_out,
+                 &h->nb_deg, &h->nb_off, &h->nb_list, &h->dc_dist, &h->dc_cmin, &h->dc_scal};
     for (Buf *b : bs) free_buf(*b);
     h->n = 0;
     h->cap = 0;
@@ -1052,10 +1058,13 @@ int64_t kdt_num_points(const kdt *h) { return h && h->built ? h->n : 0; }
 
 int32_t kdt_num_instances(const kdt *h) { return h && h->built ? h->ninst : 0; }
 
+int64_t kdt_num_cells(const kdt *h) { return h && h->built ? h->ncells : 0; }
+
 int kdt_build(kdt *h, const int32_t *xy, int64_t n)
 {
     if (!h || !xy || n < 0 || n > (1ll << 28)) return KDT_ERR_ARG;
     if (n < 3) return KDT_ERR_DEGENERATE;
+    h->d2_run = INT64_MAX;
     int64_t offs[2] = {0, n};
     return build_impl(h, xy, offs, 1);
 }
@@ -1069,6 +1078,7 @@ int kdt_build_batch(kdt *h, const int32_t *xy, const int64_t *offsets, int32_t n
         if (offsets[i + 1] - offsets[i] < 3) return KDT_ERR_DEGENERATE;
     }
     if (offsets[n_inst] > (1ll << 28)) return KDT_ERR_ARG;
+    h->d2_run = INT64_MAX;
     return build_impl(h, xy, offsets, n_inst);
 }
 
@@ -1129,6 +1139,82 @@ int kdt_export_points(kdt *h, int32_t *xy, int64_t cap_points)
     CK(cudaMemcpyAsync(xy, h->xy, (size_t)h->n * sizeof(int2),
                        is_device_ptr(xy) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    return KDT_OK;
+}
+
+int kdt_d_values(kdt *h, int32_t N, int64_t *dist2, int64_t *cell_min2, kdt_dinfo *info)
+{
+    if (!h || !info || N < 1 || N > DC_MAX_N) return KDT_ERR_ARG;
+    if (!h->built) return KDT_ERR_STATE;
+    for (int i = 0; i < h->ninst; ++i)
+        if (h->pofs[i + 1] - h->pofs[i] <= N) return KDT_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    cudaStream_t st = h->stream;
+    const int n = (int)h->n;
+    // neighbour lists (CSR) from the live triangles
+    if (grow(h->nb_deg, (size_t)n * sizeof(int)) || grow(h->nb_off, (size_t)(n + 1) * sizeof(int)) ||
+        grow(h->dc_scal, 4 * sizeof(unsigned long long)))
+        return KDT_ERR_CUDA;
+    int *deg = (int *)h->nb_deg.p, *off = (int *)h->nb_off.p;
+    CK(cudaMemsetAsync(deg, 0, (size_t)n * sizeof(int), st));
+    k_nbr_count<<<thread_grid(h, h->cap, 256), 256, 0, st>>>(h->tv, h->cap, deg);
+    if (scan(h, deg, off, n, off + n, st)) return KDT_ERR_CUDA;
+    int total = 0;
+    CK(cudaMemcpyAsync(&total, off + n, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (grow(h->nb_list, (size_t)std::max(total, 1) * sizeof(int))) return KDT_ERR_CUDA;
+    CK(cudaMemsetAsync(deg, 0, (size_t)n * sizeof(int), st));  // now the fill positions
+    k_nbr_fill<<<thread_grid(h, h->cap, 256), 256, 0, st>>>(h->tv, h->cap, off, deg, (int *)h->nb_list.p);
+    // the N-th nearest neighbours and their minima
+    const bool dist_dev = dist2 && is_device_ptr(dist2);
+    const bool cmin_dev = cell_min2 && is_device_ptr(cell_min2);
+    long long *dd = nullptr;
+    unsigned long long *cm = nullptr;
+    if (dist2) {
+        if (dist_dev) {
+            dd = (long long *)dist2;
+        } else {
+            if (grow(h->dc_dist, (size_t)n * sizeof(long long))) return KDT_ERR_CUDA;
+            dd = (long long *)h->dc_dist.p;
+        }
+    }
+    if (cell_min2) {
+        if (cmin_dev) {
+            cm = (unsigned long long *)cell_min2;
+        } else {
+            if (grow(h->dc_cmin, (size_t)std::max(h->ncells, 1) * sizeof(long long))) return KDT_ERR_CUDA;
+            cm = (unsigned long long *)h->dc_cmin.p;
+        }
+        k_fill_u64<<<thread_grid(h, h->ncells, 256), 256, 0, st>>>(cm, h->ncells, (unsigned long long)INT64_MAX);
+    }
+    unsigned long long *sc = (unsigned long long *)h->dc_scal.p;  // [0] minimum, [1] largest degree
+    unsigned long long init[2] = {(unsigned long long)INT64_MAX, 0ull};
+    CK(cudaMemcpyAsync(sc, init, sizeof init, cudaMemcpyHostToDevice, st));
+    k_nth_nn<<<thread_grid(h, n, 128), 128, 0, st>>>(h->xy, off, (const int *)h->nb_list.p, n, N, make_inst(h),
+                                                    h->cfg.domain_bits, dd, cm, sc, (int *)(sc + 1));
+    h->stats.kernel_launches += 7;
+    CK(cudaGetLastError());
+    if (dist2 && !dist_dev)
+        CK(cudaMemcpyAsync(dist2, dd, (size_t)n * sizeof(long long), cudaMemcpyDeviceToHost, st));
+    if (cell_min2 && !cmin_dev)
+        CK(cudaMemcpyAsync(cell_min2, cm, (size_t)h->ncells * sizeof(long long), cudaMemcpyDeviceToHost, st));
+    unsigned long long res[2];
+    CK(cudaMemcpyAsync(res, sc, sizeof res, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h->d_n != N) {
+        h->d_n = N;
+        h->d2_run = INT64_MAX;
+    }
+    info->min2 = (int64_t)res[0];
+    if (info->min2 < h->d2_run) h->d2_run = info->min2;
+    info->d2 = h->d2_run;
+    info->max_degree = (int64_t)(int)(unsigned)res[1];
+    info->cells = h->ncells;
+    info->spread = 0.0;
+    if (h->ninst == 1 && h->d2_run > 0) {
+        const double side = (double)(1ll << h->cfg.domain_bits) / (double)h->igrid[0];
+        info->spread = side * std::sqrt(2.0) / std::sqrt((double)h->d2_run);
+    }
     return KDT_OK;
 }
 

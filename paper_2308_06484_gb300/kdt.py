@@ -70,6 +70,11 @@ class Stats(ctypes.Structure):
                 + [("reserved", ctypes.c_int64 * 8)])
 
 
+class DInfo(ctypes.Structure):
+    _fields_ = [("min2", ctypes.c_int64), ("d2", ctypes.c_int64), ("spread", ctypes.c_double),
+                ("max_degree", ctypes.c_int64), ("cells", ctypes.c_int64)]
+
+
 _lib = None
 
 # every symbol include/kdt.h declares (checked by the loader test)
@@ -79,7 +84,8 @@ SYMBOLS = ["kdt_default_config", "kdt_create", "kdt_destroy", "kdt_build", "kdt_
            "kdt_version", "kdt_stats_size", "kdt_eval_predicates", "kdt_export_store",
            "kdt_export_triangles_noalloc", "kdt_build_batch", "kdt_step_batch",
            "kdt_export_triangles_inst", "kdt_num_instances", "kdt_set_trace", "kdt_trace_count",
-           "kdt_set_proposal", "kdt_mlp_forward", "kdt_mlp_loss_grad", "kdt_mlp_adam"]
+           "kdt_set_proposal", "kdt_mlp_forward", "kdt_mlp_loss_grad", "kdt_mlp_adam", "kdt_d_values",
+           "kdt_num_cells"]
 
 MLP_IN, MLP_OUT, MLP_SLOTS, MLP_PARAMS = 32, 18, 17, 7442
 
@@ -131,6 +137,9 @@ def load(build_if_stale: bool = True):
     L.kdt_mlp_forward.argtypes = [vp, vp, vp, i64, vp]
     L.kdt_mlp_loss_grad.argtypes = [vp, vp, vp, vp, vp, i64, f32, vp, vp]
     L.kdt_mlp_adam.argtypes = [vp, vp, vp, vp, vp, i64, f32, f32, f32, f32, vp]
+    L.kdt_d_values.argtypes = [vp, ctypes.c_int32, vp, vp, ctypes.POINTER(DInfo)]
+    L.kdt_num_cells.argtypes = [vp]
+    L.kdt_num_cells.restype = i64
     for s in SYMBOLS:
         getattr(L, s)
     _lib = L
@@ -292,6 +301,33 @@ class Triangulation:
         p, cap = _ptr(out)
         _check(self.L.kdt_export_points(self.h, p, cap), "kdt_export_points")
         return out
+
+    def d_values(self, N: int, dist2=None, cell_min2=None) -> dict:
+        """d-calculation (kdt_d_values): the N-th nearest-neighbour squared distance of
+        every point into dist2 and the per-partition minima into cell_min2 (int64 numpy
+        arrays or CUDA tensors, or None); returns min2, d2, spread, max_degree, cells."""
+        def ptr64(a):
+            if a is None:
+                return None
+            if hasattr(a, "data_ptr"):
+                import torch
+                if a.dtype != torch.int64 or not a.is_contiguous():
+                    raise ValueError("expected a contiguous int64 tensor")
+                return ctypes.c_void_p(a.data_ptr())
+            if not isinstance(a, np.ndarray) or a.dtype != np.int64 or not a.flags["C_CONTIGUOUS"]:
+                raise ValueError("expected a C-contiguous int64 numpy array")
+            return a.ctypes.data_as(ctypes.c_void_p)
+        if dist2 is not None and dist2.shape[0] < self.L.kdt_num_points(self.h):
+            raise ValueError("dist2 needs one entry per point")
+        if cell_min2 is not None and cell_min2.shape[0] < self.L.kdt_num_cells(self.h):
+            raise ValueError("cell_min2 needs one entry per partition")
+        info = DInfo()
+        _check(self.L.kdt_d_values(self.h, int(N), ptr64(dist2), ptr64(cell_min2), ctypes.byref(info)),
+               "kdt_d_values")
+        return {f: getattr(info, f) for f, _ in DInfo._fields_}
+
+    def num_cells(self) -> int:
+        return int(self.L.kdt_num_cells(self.h))
 
     def verify(self) -> int:
         bad = ctypes.c_int64(0)
