@@ -400,6 +400,25 @@ def run_c3(args):
     b.record()
     torch.cuda.synchronize()
     rebuild_ms = a.elapsed_time(b)
+    tri.close()
+    # comparator: the same steps on the paper's quad-tree partitions (threshold 256)
+    tq = kdt.Triangulation(kdt.default_config(domain_bits=24, timing=1, quadtree=1, points_per_partition=256))
+    tq.build(xy0)
+    for i in range(args.warmup):
+        tq.step(moves[i])
+    tq.reset_stats()
+    evq = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k, (qa, qb) in enumerate(evq):
+        qa.record()
+        tq.step(moves[args.warmup + k])
+        qb.record()
+    torch.cuda.synchronize()
+    qsec = sum(qa.elapsed_time(qb) for qa, qb in evq) / 1000.0
+    stq = tq.stats()
+    quadtree = {"value": stq["moves"] / qsec, "unit": "updates/s", "ms_per_step": 1000.0 * qsec / args.steps,
+                "leaves": tq.num_cells(), "threshold": 256, "fallbacks": int(stq["fallbacks"])}
+    tq.close()
     m_avg = st["moves"] / args.steps
     peak, peak_kind = measured_peaks()
     kin_ms = st["kinetic_kernel_ms"] / max(1, st["kinetic_kernel_timed"])
@@ -415,13 +434,13 @@ def run_c3(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "kernel": "k_kinetic", "kernel_ms": kin_ms, "peak_kind": peak_kind},
         "comparators": {"gpu_full_rebuild": {"value": m_avg / (rebuild_ms / 1000.0), "unit": "updates/s",
-                                             "ms_per_rebuild": rebuild_ms}},
+                                             "ms_per_rebuild": rebuild_ms},
+                        "gpu_kinetic_quadtree_partitions": quadtree},
         "gpu_launches": int(st["kernel_launches"]), "fallbacks": int(st["fallbacks"]), "clocks": clk,
         "verify_violations": int(verify_bad), "staged_to_global": int(st["staged_to_global"]),
         "retries": int(st["retries"]),
     }
     print(json.dumps(line), flush=True)
-    tri.close()
 
 
 def run_c5(args):

@@ -95,6 +95,17 @@ typedef struct {
                               position (a safe-region test in the spirit of the paper's
                               related work [6]); if so only the position changes, else
                               delete + insert.  The triangulation is the same either way.  */
+    int32_t quadtree;      /* 1: partitions are the leaves of the paper's quad-tree (Section
+                              III, Data structure) instead of the grid: the square of side
+                              S (a power of two >= the points' larger extent) at the points'
+                              minimum corner is divided into four, recursively, until every
+                              square holds at most points_per_partition points (256 if 0) or
+                              has side S / 2^11; blocks are numbered depth-first (children
+                              low-x low-y, high-x low-y, low-x high-y, high-x high-y).  Built
+                              by kdt_build from the initial positions; a moved point's block
+                              is the leaf holding its current position (clamped into the
+                              square).  Single-instance handles only (kdt_build_batch returns
+                              KDT_ERR_ARG).  Scheduling only: the triangulation is the same. */
 } kdt_config;
 
 /* Counters since creation (or kdt_reset_stats). */
@@ -229,8 +240,9 @@ int kdt_export_triangles_noalloc(kdt *h, int32_t *out, int64_t cap, int64_t *n_t
  * For a constant N (1 <= N <= 16, N < the smallest instance's point count): for every
  * point p, dist_p^2 = the squared distance to its N-th nearest other point of its own
  * instance (exact int64); the minimum of dist_p^2 over the points of each partition
- * (the grid cells of the steps: cell = (x * G >> domain_bits, y * G >> domain_bits),
- * row-major, instances one after another) and over all points, mindistance(P)^2; and
+ * (the partitions of the steps: grid cell (x * G >> domain_bits, y * G >> domain_bits),
+ * row-major, instances one after another, or the quad-tree leaf) and over all points,
+ * mindistance(P)^2; and
  * d^2 = the minimum of mindistance^2 over the calls since the last kdt_build /
  * kdt_build_batch with the same N (the paper's d = min over the time steps; a call
  * with another N starts the minimum again).  The N-th nearest neighbour is found on
@@ -245,13 +257,15 @@ typedef struct {
     int64_t min2;     /* mindistance(P)^2 of this call                                     */
     int64_t d2;       /* d^2: the running minimum (see above)                              */
     double spread;    /* N-spread of a block, Delta_N(P_i) = diam(P_i) / d with diam(P_i)
-                         the cell's diagonal (one instance; 0 for a batch)                 */
+                         the grid cell's diagonal (one instance on the grid; the largest
+                         leaf's for the quad-tree; 0 for a batch)                           */
     int64_t max_degree; /* largest vertex degree met (the search's fan-out)                */
     int64_t cells;    /* partitions (entries of cell_min2)                                 */
 } kdt_dinfo;
 int kdt_d_values(kdt *h, int32_t N, int64_t *dist2, int64_t *cell_min2, kdt_dinfo *info);
 
-/* Partitions of the current state (entries of kdt_d_values' cell_min2; 0 before a build). */
+/* Partitions of the current state (grid cells or quad-tree leaves: the entries of
+ * kdt_d_values' cell_min2; 0 before a build). */
 int64_t kdt_num_cells(const kdt *h);
 
 /* Full GPU verifier: every triangle alive and counter-clockwise, adjacency

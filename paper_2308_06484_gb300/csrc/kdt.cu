@@ -27,7 +27,7 @@ using namespace kd;
 
 namespace {
 
-constexpr int ABI_VERSION = 4;
+constexpr int ABI_VERSION = 5;
 
 struct Buf {
     void *p = nullptr;
@@ -85,6 +85,9 @@ struct kdt {
     Buf nb_deg, nb_off, nb_list, dc_dist, dc_cmin, dc_scal;
     int64_t d2_run = INT64_MAX;
     int d_n = 0;
+    // quad-tree partitions (kdt_config.quadtree): leaf of every fine cell, the square
+    int *qmap = nullptr;
+    int qx0 = 0, qy0 = 0, qshift = 0, qF = 0, qleaves = 0, qleaf_side_lg = 0;
     // graph-launched step: control words (moves, stamp, moves address) and the graph
     int *ctl = nullptr;   // device
     int *hctl = nullptr;  // pinned host
@@ -226,6 +229,11 @@ Inst make_inst(kdt *h)
     I.tofs = h->d_tofs;
     I.moff = h->d_moff;
     I.ninst = h->ninst;
+    I.qmap = h->qmap;
+    I.qx0 = h->qx0;
+    I.qy0 = h->qy0;
+    I.qshift = h->qshift;
+    I.qF = h->qF;
     return I;
 }
 
@@ -452,7 +460,13 @@ int set_partitions(kdt *h, int ppp)
     h->cofs.assign(h->ninst + 1, 0);
     h->igrid.assign(h->ninst, 1);
     long long cells = 0;
-    for (int i = 0; i < h->ninst; ++i) {
+    if (h->qmap) {
+        // the quad-tree's leaves (one instance)
+        h->igrid[0] = 0;
+        h->cofs[0] = 0;
+        cells = h->qleaves;
+    }
+    for (int i = 0; i < h->ninst && !h->qmap; ++i) {
         int ni = h->pofs[i + 1] - h->pofs[i];
         int G;
         if (h->ninst == 1 && h->cfg.grid > 0) {
@@ -491,7 +505,7 @@ void free_state(kdt *h)
     h->gen++;
     void *ps[] = {h->xy, h->pt_tri, h->pt_stamp, h->tv, h->tn, h->viol, h->moves, h->gmoves, h->old_xy,
                   h->next, h->head, h->deferred, h->dirty, h->scan_tmp, h->d_pofs, h->d_cofs, h->d_grid,
-                  h->d_moff, h->d_tofs};
+                  h->d_moff, h->d_tofs, h->qmap};
     for (void *p : ps)
         if (p) cudaFree(p);
     if (h->h_moff) cudaFreeHost(h->h_moff);
@@ -500,6 +514,8 @@ void free_state(kdt *h)
     h->head = nullptr; h->deferred = nullptr; h->dirty = nullptr; h->scan_tmp = nullptr;
     h->d_pofs = nullptr; h->d_cofs = nullptr; h->d_grid = nullptr; h->d_moff = nullptr; h->h_moff = nullptr;
     h->d_tofs = nullptr;
+    h->qmap = nullptr;
+    h->qleaves = 0;
     h->mcap = 0; h->dirty_cap = 0; h->scan_tmp_cap = 0;
     Buf *bs[] = {&h->key, &h->bord, &h->hist, &h->hoff, &h->exp_cnt, &h->exp_off, &h->exp_fill, &h->exp_out,
                  &h->nb_deg, &h->nb_off, &h->nb_list, &h->dc_dist, &h->dc_cmin, &h->dc_scal};
@@ -717,7 +733,7 @@ int repair_step(kdt *h, int *ds)
 // partition) pair are timed with events around the step; then the pair with the
 // least time per move is kept.  Results do not depend on the pair.  A single instance with a configured
 // grid tunes the warps per partition only.
-bool tune_fixed_grid(const kdt *h) { return h->ninst == 1 && h->cfg.grid > 0; }
+bool tune_fixed_grid(const kdt *h) { return h->ninst == 1 && (h->cfg.grid > 0 || h->qmap); }
 
 int autotune_before(kdt *h)
 {
@@ -931,6 +947,75 @@ int export_range(kdt *h, int s0, int nslots, int idbase, int np, int32_t *out, i
     return KDT_OK;
 }
 
+// The quad-tree of Section III (Data structure) over the current positions of the
+// single instance: the square of side 2^lg (the smallest power of two >= the larger
+// extent) at the points' minimum corner, divided into four recursively until a square
+// holds at most ppp points or has the side of a fine cell (2^lg / 2^D, D = min(11,
+// lg)).  The points per fine cell are counted on the GPU; the division runs on the
+// host over the count pyramid; every fine cell gets its leaf's number (depth-first,
+// children low-x low-y, high-x low-y, low-x high-y, high-x high-y).
+int build_quadtree(kdt *h)
+{
+    cudaStream_t st = h->stream;
+    const int n = (int)h->n;
+    int init_bbox[4] = {INT_MAX, INT_MAX, INT_MIN, INT_MIN};
+    CK(cudaMemsetAsync(h->scal, 0, S_NUM * sizeof(int), st));
+    CK(cudaMemcpyAsync(h->scal + S_MINX, init_bbox, sizeof init_bbox, cudaMemcpyHostToDevice, st));
+    k_range<<<thread_grid(h, n, 256), 256, 0, st>>>(h->xy, n, h->cfg.domain_bits, h->scal + S_STATUS,
+                                                    h->scal + S_MINX);
+    if (sync_scalars(h)) return KDT_ERR_CUDA;
+    const int x0 = h->hscal[S_MINX], y0 = h->hscal[S_MINY];
+    const long long ext = std::max((long long)h->hscal[S_MAXX] - x0, (long long)h->hscal[S_MAXY] - y0) + 1;
+    int lg = 0;
+    while ((1ll << lg) < ext) ++lg;
+    const int D = std::min(11, lg), F = 1 << D;
+    if (grow(h->hist, (size_t)F * F * sizeof(int))) return KDT_ERR_CUDA;
+    CK(cudaMemsetAsync(h->hist.p, 0, (size_t)F * F * sizeof(int), st));
+    k_qt_hist<<<thread_grid(h, n, 256), 256, 0, st>>>(h->xy, n, x0, y0, lg - D, F, (int *)h->hist.p);
+    h->stats.kernel_launches += 2;
+    std::vector<std::vector<long long>> lev(D + 1);
+    {
+        std::vector<int> fine((size_t)F * F);
+        CK(cudaMemcpyAsync(fine.data(), h->hist.p, fine.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        lev[D].assign(fine.begin(), fine.end());
+    }
+    for (int l = D - 1; l >= 0; --l) {
+        const int w = 1 << l, wc = 2 << l;
+        lev[l].assign((size_t)w * w, 0);
+        for (int y = 0; y < w; ++y)
+            for (int x = 0; x < w; ++x)
+                lev[l][(size_t)y * w + x] = lev[l + 1][(size_t)(2 * y) * wc + 2 * x] +
+                                            lev[l + 1][(size_t)(2 * y) * wc + 2 * x + 1] +
+                                            lev[l + 1][(size_t)(2 * y + 1) * wc + 2 * x] +
+                                            lev[l + 1][(size_t)(2 * y + 1) * wc + 2 * x + 1];
+    }
+    std::vector<int> qmap((size_t)F * F, -1);
+    int leaves = 0, largest = D;
+    const long long T = h->ppp;
+    auto divide = [&](auto &&self, int l, int x, int y) -> void {
+        if (lev[l][(size_t)y * (1 << l) + x] <= T || l == D) {
+            const int id = leaves++, span = 1 << (D - l);
+            largest = std::min(largest, l);
+            for (int fy = y * span; fy < (y + 1) * span; ++fy)
+                for (int fx = x * span; fx < (x + 1) * span; ++fx) qmap[(size_t)fy * F + fx] = id;
+            return;
+        }
+        for (int cy = 0; cy < 2; ++cy)
+            for (int cx = 0; cx < 2; ++cx) self(self, l + 1, 2 * x + cx, 2 * y + cy);
+    };
+    divide(divide, 0, 0, 0);
+    if (dalloc(&h->qmap, qmap.size())) return KDT_ERR_CUDA;
+    CK(cudaMemcpy(h->qmap, qmap.data(), qmap.size() * sizeof(int), cudaMemcpyHostToDevice));
+    h->qx0 = x0;
+    h->qy0 = y0;
+    h->qshift = lg - D;
+    h->qF = F;
+    h->qleaves = leaves;
+    h->qleaf_side_lg = lg - largest;  // log2 of the side of the largest leaf
+    return set_partitions(h, h->ppp);
+}
+
 int build_impl(kdt *h, const int32_t *xy, const int64_t *offs, int n_inst)
 {
     CK(cudaSetDevice(h->device));
@@ -942,7 +1027,9 @@ int build_impl(kdt *h, const int32_t *xy, const int64_t *offs, int n_inst)
     }
     CK(cudaMemcpyAsync(h->xy, xy, (size_t)h->n * sizeof(int2),
                        is_device_ptr(xy) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
-    return rebuild_all(h);
+    rc = rebuild_all(h);
+    if (rc == 0 && h->cfg.quadtree && h->ninst == 1) rc = build_quadtree(h);
+    return rc;
 }
 
 }  // namespace
@@ -1003,7 +1090,7 @@ int kdt_create(kdt **out, const kdt_config *cfg, int device, void *cuda_stream)
     else kdt_default_config(&c);
     if (c.domain_bits <= 0 || c.domain_bits > 28 || c.grid < 0 || c.grid > 4096 || c.retry_cap < 0 ||
         c.points_per_partition < 0 || c.warps_per_partition < 0 || c.warps_per_partition > 32 ||
-        c.variant < 0 || c.variant > 1)
+        c.variant < 0 || c.variant > 1 || c.quadtree < 0 || c.quadtree > 1)
         return KDT_ERR_ARG;
     if (c.retry_cap == 0) c.retry_cap = 4096;
     if (cudaSetDevice(device) != cudaSuccess) return KDT_ERR_CUDA;
@@ -1078,6 +1165,7 @@ int kdt_build_batch(kdt *h, const int32_t *xy, const int64_t *offsets, int32_t n
         if (offsets[i + 1] - offsets[i] < 3) return KDT_ERR_DEGENERATE;
     }
     if (offsets[n_inst] > (1ll << 28)) return KDT_ERR_ARG;
+    if (h->cfg.quadtree) return KDT_ERR_ARG;  // quad-tree partitions: one instance
     h->d2_run = INT64_MAX;
     return build_impl(h, xy, offsets, n_inst);
 }
@@ -1212,7 +1300,8 @@ int kdt_d_values(kdt *h, int32_t N, int64_t *dist2, int64_t *cell_min2, kdt_dinf
     info->cells = h->ncells;
     info->spread = 0.0;
     if (h->ninst == 1 && h->d2_run > 0) {
-        const double side = (double)(1ll << h->cfg.domain_bits) / (double)h->igrid[0];
+        const double side = h->qmap ? (double)(1ll << h->qleaf_side_lg)
+                                    : (double)(1ll << h->cfg.domain_bits) / (double)h->igrid[0];
         info->spread = side * std::sqrt(2.0) / std::sqrt((double)h->d2_run);
     }
     return KDT_OK;

@@ -100,10 +100,7 @@ __global__ void k_nth_nn(const int2 *xy, const int *off, const int *nbr, int n, 
         if (dist2) dist2[p] = v;
         if (cell_min) {
             const int inst = I.ninst > 1 ? csr_find(I.pofs, I.ninst + 1, p) : 0;
-            const int G = I.grid[inst];
-            const int cx = (int)(((long long)pp.x * G) >> bits);
-            const int cy = (int)(((long long)pp.y * G) >> bits);
-            atomicMin(cell_min + I.cofs[inst] + cy * G + cx, (unsigned long long)v);
+            atomicMin(cell_min + partition_of(I, inst, bits, pp), (unsigned long long)v);
         }
         best = min(best, v);
     }

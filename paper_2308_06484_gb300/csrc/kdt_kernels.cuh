@@ -29,10 +29,41 @@ struct Inst {
     const int *pofs;
     const int *cofs;
     const int *grid;
+    // quad-tree partitions (one instance): the leaf of every fine cell of side
+    // 2^qshift of the square at (qx0, qy0), qF x qF fine cells; null = the grid
+    const int *qmap;
+    int qx0, qy0, qshift, qF;
     const int *moff;  // per step: the moves of instance i are moff[i] .. moff[i+1]-1
     const int *tofs;  // triangle slots of instance i: tofs[i] .. tofs[i+1]-1
     int ninst;
 };
+
+// Partition of a position of instance `inst`: its grid cell, or the quad-tree leaf of
+// its fine cell (positions outside the square clamped into it).
+__device__ __forceinline__ int partition_of(const Inst &I, int inst, int bits, int2 o)
+{
+    if (I.qmap) {
+        int fx = (int)max(0ll, min((long long)I.qF - 1, ((long long)o.x - I.qx0) >> I.qshift));
+        int fy = (int)max(0ll, min((long long)I.qF - 1, ((long long)o.y - I.qy0) >> I.qshift));
+        return I.qmap[fy * I.qF + fx];
+    }
+    const int G = I.grid[inst];
+    const int cx = (int)(((long long)o.x * G) >> bits);
+    const int cy = (int)(((long long)o.y * G) >> bits);
+    return I.cofs[inst] + cy * G + cx;
+}
+
+// points per fine cell of the quad-tree's square (the division is made on the host)
+__global__ void k_qt_hist(const int2 *xy, int n, int x0, int y0, int shift, int F, int *hist)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int2 p = xy[i];
+        int fx = (int)max(0ll, min((long long)F - 1, ((long long)p.x - x0) >> shift));
+        int fy = (int)max(0ll, min((long long)F - 1, ((long long)p.y - y0) >> shift));
+        atomicAdd(hist + fy * F + fx, 1);
+    }
+}
+
 
 // The warp's handle and its shared state (counters zero, claims none, random state
 // from `seed`, instance = the points [d.rlo, d.rlo + d.rn)).
@@ -209,10 +240,7 @@ __global__ void k_intake_link(Dev d, const int3 *moves, int m, Inst I, int bits,
         int2 o = d.xy[g];
         old_xy[i] = o;
         gmoves[i] = make_int3(g, mv.y, mv.z);
-        int G = I.grid[inst];
-        int cx = (int)(((long long)o.x * G) >> bits);
-        int cy = (int)(((long long)o.y * G) >> bits);
-        next[i] = atomicExch(head + I.cofs[inst] + cy * G + cx, i);
+        next[i] = atomicExch(head + partition_of(I, inst, bits, o), i);
     }
 }
 

@@ -41,7 +41,7 @@ class Config(ctypes.Structure):
                 ("kinetic_warps", ctypes.c_int32), ("debug", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("points_per_partition", ctypes.c_int32),
                 ("warps_per_partition", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("variant", ctypes.c_int32)]
+                ("variant", ctypes.c_int32), ("quadtree", ctypes.c_int32)]
 
 
 _STAT_FIELDS = ["steps", "moves", "rebuilds", "fallbacks", "kernel_launches", "flips", "retries",

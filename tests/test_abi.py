@@ -32,7 +32,7 @@ def test_library_exports_every_declared_symbol():
     for name in declared_functions():
         assert hasattr(L, name), name
     assert set(declared_functions()) <= set(kdt.SYMBOLS)
-    assert L.kdt_version() == 4
+    assert L.kdt_version() == 5
     assert L.kdt_stats_size() == ctypes.sizeof(kdt.Stats)
     assert L.kdt_error_string(-3) == b"duplicate point or repeated move id"
 
