@@ -401,24 +401,34 @@ def run_c3(args):
     torch.cuda.synchronize()
     rebuild_ms = a.elapsed_time(b)
     tri.close()
-    # comparator: the same steps on the paper's quad-tree partitions (threshold 256)
-    tq = kdt.Triangulation(kdt.default_config(domain_bits=24, timing=1, quadtree=1, points_per_partition=256))
-    tq.build(xy0)
-    for i in range(args.warmup):
-        tq.step(moves[i])
-    tq.reset_stats()
-    evq = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    torch.cuda.synchronize()
-    for k, (qa, qb) in enumerate(evq):
-        qa.record()
-        tq.step(moves[args.warmup + k])
-        qb.record()
-    torch.cuda.synchronize()
-    qsec = sum(qa.elapsed_time(qb) for qa, qb in evq) / 1000.0
-    stq = tq.stats()
-    quadtree = {"value": stq["moves"] / qsec, "unit": "updates/s", "ms_per_step": 1000.0 * qsec / args.steps,
-                "leaves": tq.num_cells(), "threshold": 256, "fallbacks": int(stq["fallbacks"])}
-    tq.close()
+
+    def same_steps(cfg):
+        # the same build and steps with another configuration (a comparator)
+        tq = kdt.Triangulation(cfg)
+        tq.build(xy0)
+        for i in range(args.warmup):
+            tq.step(moves[i])
+        tq.reset_stats()
+        evq = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for k, (qa, qb) in enumerate(evq):
+            qa.record()
+            tq.step(moves[args.warmup + k])
+            qb.record()
+        torch.cuda.synchronize()
+        qsec = sum(qa.elapsed_time(qb) for qa, qb in evq) / 1000.0
+        stq = tq.stats()
+        out = {"value": stq["moves"] / qsec, "unit": "updates/s", "ms_per_step": 1000.0 * qsec / args.steps,
+               "fallbacks": int(stq["fallbacks"]), "moved_in_place": (stq["moves"] - stq["deletes"]) / stq["moves"],
+               "cells": tq.num_cells()}
+        tq.close()
+        return out
+
+    # the paper's quad-tree partitions (threshold 256); the two in-place variants
+    quadtree = same_steps(kdt.default_config(domain_bits=24, timing=1, quadtree=1, points_per_partition=256))
+    var1 = same_steps(kdt.default_config(grid=256, domain_bits=24, timing=1, variant=1))
+    var2 = same_steps(kdt.default_config(grid=256, domain_bits=24, timing=1, variant=2))
     m_avg = st["moves"] / args.steps
     peak, peak_kind = measured_peaks()
     kin_ms = st["kinetic_kernel_ms"] / max(1, st["kinetic_kernel_timed"])
@@ -435,7 +445,8 @@ def run_c3(args):
                      "traffic": None, "kernel": "k_kinetic", "kernel_ms": kin_ms, "peak_kind": peak_kind},
         "comparators": {"gpu_full_rebuild": {"value": m_avg / (rebuild_ms / 1000.0), "unit": "updates/s",
                                              "ms_per_rebuild": rebuild_ms},
-                        "gpu_kinetic_quadtree_partitions": quadtree},
+                        "gpu_kinetic_quadtree_partitions": quadtree,
+                        "gpu_kinetic_variant_in_place": var1, "gpu_kinetic_variant_move_flip": var2},
         "gpu_launches": int(st["kernel_launches"]), "fallbacks": int(st["fallbacks"]), "clocks": clk,
         "verify_violations": int(verify_bad), "staged_to_global": int(st["staged_to_global"]),
         "retries": int(st["retries"]),
@@ -662,26 +673,32 @@ def main():
     e2e_sec = sum(a.elapsed_time(b) for a, b in ev2) / 1000.0
     tri2.close()
 
-    # ---- comparator: the same steps with the in-place variant (kdt_config.variant = 1)
-    w3 = W.c2(n=args.n, grid=args.grid, seed=2 + 1000 * rank)
-    tri3 = kdt.Triangulation(kdt.default_config(grid=args.grid, domain_bits=24, variant=1), device=local)
-    tri3.build(torch.from_numpy(w3.positions).to(dev))
-    for i in range(args.warmup):
-        tri3.step(d_moves[i])
-    tri3.reset_stats()
-    ev3 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    torch.cuda.synchronize()
-    for k in range(args.steps):
-        i = args.warmup + k
-        ev3[k][0].record()
-        tri3.step(d_moves[i])
-        ev3[k][1].record()
-        flush.zero_()
-    torch.cuda.synchronize()
-    var_sec = sum(a.elapsed_time(b) for a, b in ev3) / 1000.0
-    st3 = tri3.stats()
-    var_in_place = (st3["moves"] - st3["deletes"]) / max(1, st3["moves"])
-    tri3.close()
+    # ---- comparators: the same steps with the in-place variants (kdt_config.variant
+    # 1: safe-region test, 2: move and flip)
+    variants = {}
+    for var in (1, 2):
+        w3 = W.c2(n=args.n, grid=args.grid, seed=2 + 1000 * rank)
+        tri3 = kdt.Triangulation(kdt.default_config(grid=args.grid, domain_bits=24, variant=var), device=local)
+        tri3.build(torch.from_numpy(w3.positions).to(dev))
+        for i in range(args.warmup):
+            tri3.step(d_moves[i])
+        tri3.reset_stats()
+        ev3 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            i = args.warmup + k
+            ev3[k][0].record()
+            tri3.step(d_moves[i])
+            ev3[k][1].record()
+            flush.zero_()
+        torch.cuda.synchronize()
+        var_sec = sum(a.elapsed_time(b) for a, b in ev3) / 1000.0
+        st3 = tri3.stats()
+        variants[var] = {"value": local_updates / var_sec, "unit": "updates/s",
+                         "moved_in_place": (st3["moves"] - st3["deletes"]) / max(1, st3["moves"]),
+                         "fallbacks": int(st3["fallbacks"])}
+        tri3.close()
 
     # ---- comparator: GPU full rebuild of the same point set per step
     tri.reset_stats()
@@ -739,8 +756,8 @@ def main():
                 "gpu_kinetic_plain": {"value": value, "unit": "updates/s"},
                 "gpu_full_rebuild": {"value": m / (rebuild_ms / 1000.0), "unit": "updates/s",
                                      "ms_per_rebuild": rebuild_ms},
-                "gpu_kinetic_variant_in_place": {"value": local_updates / var_sec, "unit": "updates/s",
-                                                 "moved_in_place": var_in_place},
+                "gpu_kinetic_variant_in_place": variants[1],
+                "gpu_kinetic_variant_move_flip": variants[2],
             },
             "gpu_launches": int(launches),
             "fallbacks": int(fallbacks),

@@ -94,7 +94,12 @@ typedef struct {
                               and every edge of the star stays locally Delaunay at the new
                               position (a safe-region test in the spirit of the paper's
                               related work [6]); if so only the position changes, else
-                              delete + insert.  The triangulation is the same either way.  */
+                              delete + insert.  2: move and flip (the kinetic approach of
+                              the related work [4]): a move that keeps every triangle of
+                              the star counter-clockwise only changes the position, and
+                              the star's edges that stop being locally Delaunay are
+                              flipped by the step's certification and repair; else delete
+                              + insert.  The triangulation is the same in every case.       */
     int32_t quadtree;      /* 1: partitions are the leaves of the paper's quad-tree (Section
                               III, Data structure) instead of the grid: the square of side
                               S (a power of two >= the points' larger extent) at the points'

@@ -1090,7 +1090,7 @@ int kdt_create(kdt **out, const kdt_config *cfg, int device, void *cuda_stream)
     else kdt_default_config(&c);
     if (c.domain_bits <= 0 || c.domain_bits > 28 || c.grid < 0 || c.grid > 4096 || c.retry_cap < 0 ||
         c.points_per_partition < 0 || c.warps_per_partition < 0 || c.warps_per_partition > 32 ||
-        c.variant < 0 || c.variant > 1 || c.quadtree < 0 || c.quadtree > 1)
+        c.variant < 0 || c.variant > 2 || c.quadtree < 0 || c.quadtree > 1)
         return KDT_ERR_ARG;
     if (c.retry_cap == 0) c.retry_cap = 4096;
     if (cudaSetDevice(device) != cudaSuccess) return KDT_ERR_CUDA;

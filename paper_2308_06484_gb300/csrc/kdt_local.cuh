@@ -661,13 +661,17 @@ __device__ int move_point(Warp w, const Dev &d, int p, int2 q, int &s0, int &s1,
                 }
             }
         }
-        // ---- variant 1 (kdt_config.variant): a move that keeps every triangle of the
+        // ---- variants (kdt_config.variant).  1: a move that keeps every triangle of the
         // star counter-clockwise and every edge of the star (spokes p-v_i, link edges
         // v_i-v_{i+1} against the staged ring apex) locally Delaunay at q changes only
         // p's position: every other edge keeps its triangles and their vertices, so the
-        // triangulation stays Delaunay (Delaunay lemma) and nothing is written.
-        if (d.variant == 1 && gpos < 0) {
-            bool stays = true;
+        // triangulation stays Delaunay (Delaunay lemma) and nothing is written.  2 (move
+        // and flip): a move that keeps the star counter-clockwise also changes only p's
+        // position, and the star's triangles go to the dirty list: the certification
+        // that ends the step finds the star edges that stopped being Delaunay and the
+        // repair (general Lawson flips) settles them.
+        if (d.variant >= 1 && gpos < 0) {
+            bool ccw = true, del = true;
             unsigned ex = 0, ti = 0;
             for (int i = w.lane; i < k; i += 32) {
                 int i0 = i == 0 ? k - 1 : i - 1, i1 = i + 1 == k ? 0 : i + 1;
@@ -677,17 +681,22 @@ __device__ int move_point(Warp w, const Dev &d, int p, int2 q, int &s0, int &s1,
                 int o = eo >> 2, f = eo & 3;
                 int r = ic(sh->lv[o], f);
                 int2 pr = sh->lp[o][f];
-                stays = stays && orient2d(q, pb, pc) > 0 &&
-                        !conflict(p, a, b, q, pa, pb, c, pc, d.use_filter, &ex, &ti) &&
-                        !conflict(p, b, c, q, pb, pc, r, pr, d.use_filter, &ex, &ti);
+                const bool turn = orient2d(q, pb, pc) > 0;
+                ccw = ccw && turn;
+                del = del && turn && !conflict(p, a, b, q, pa, pb, c, pc, d.use_filter, &ex, &ti) &&
+                      !conflict(p, b, c, q, pb, pc, r, pr, d.use_filter, &ex, &ti);
             }
             cnt_add(w, C_EXACT, __reduce_add_sync(FULL, ex));
             cnt_add(w, C_TIES, __reduce_add_sync(FULL, ti));
-            if (__all_sync(FULL, stays)) {
+            ccw = __all_sync(FULL, ccw);
+            del = __all_sync(FULL, del);
+            if (del || (ccw && d.variant == 2)) {
                 if (w.lane == 0) {
                     d.xy[p] = q;
                     __threadfence();
                 }
+                if (!del)
+                    for (int i = w.lane; i < k; i += 32) dirty_push(d, sh->S[i]);
                 __syncwarp();
                 release_all(w, d);
                 cnt_add(w, C_CYC_LOCAL, (unsigned)((clock64() - t2) >> 6));

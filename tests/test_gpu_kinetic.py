@@ -228,11 +228,14 @@ def test_fallback_rebuild_and_retry_cap():
 @pytest.mark.parametrize("make", [lambda: W.c1(), lambda: W.c2(n=30000, grid=16, seed=44),
                                   lambda: W.KineticWorkload(W.mixture_lattice_points(30000, 24, 45), 16, 24,
                                                             (1, 16), (1, 8), seed=46, name="mix")])
-def test_variant_in_place_moves(make):
+@pytest.mark.parametrize("variant", [1, 2])
+def test_variant_in_place_moves(make, variant):
     """kdt_config.variant = 1 (move in place when the star stays Delaunay, else delete +
-    insert) gives the oracle's triangulation after every step."""
+    insert) and 2 (move in place when the star stays counter-clockwise, the star's
+    failing edges flipped by the step's repair) give the oracle's triangulation after
+    every step."""
     w = make()
-    t = _setup(w, variant=1)
+    t = _setup(w, variant=variant)
     run_kinetic(t, w, 8, every=1)
     st = t.stats()
     assert st["fallbacks"] == 0
