@@ -291,8 +291,10 @@ const char *kdt_error_string(int code);
 /* ABI version (incremented on any incompatible change). */
 int kdt_version(void);
 
-/* sizeof(kdt_stats) as this library was built (a binding checks its own layout). */
+/* sizeof(kdt_stats) and sizeof(kdt_config) as this library was built (a binding
+ * checks its own layouts against them). */
 int64_t kdt_stats_size(void);
+int64_t kdt_config_size(void);
 
 /* ---- diagnostics ---------------------------------------------------------------- */
 

@@ -1042,6 +1042,8 @@ int kdt_version(void) { return ABI_VERSION; }
 
 int64_t kdt_stats_size(void) { return (int64_t)sizeof(kdt_stats); }
 
+int64_t kdt_config_size(void) { return (int64_t)sizeof(kdt_config); }
+
 const char *kdt_error_string(int code)
 {
     switch (code) {

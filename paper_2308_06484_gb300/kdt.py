@@ -81,7 +81,7 @@ _lib = None
 SYMBOLS = ["kdt_default_config", "kdt_create", "kdt_destroy", "kdt_build", "kdt_step",
            "kdt_rebuild", "kdt_export_triangles", "kdt_export_points", "kdt_verify",
            "kdt_num_points", "kdt_get_stats", "kdt_reset_stats", "kdt_error_string",
-           "kdt_version", "kdt_stats_size", "kdt_eval_predicates", "kdt_export_store",
+           "kdt_version", "kdt_stats_size", "kdt_config_size", "kdt_eval_predicates", "kdt_export_store",
            "kdt_export_triangles_noalloc", "kdt_build_batch", "kdt_step_batch",
            "kdt_export_triangles_inst", "kdt_num_instances", "kdt_set_trace", "kdt_trace_count",
            "kdt_set_proposal", "kdt_mlp_forward", "kdt_mlp_loss_grad", "kdt_mlp_adam", "kdt_d_values",
@@ -122,6 +122,7 @@ def load(build_if_stale: bool = True):
     L.kdt_error_string.restype = ctypes.c_char_p
     L.kdt_version.restype = i32
     L.kdt_stats_size.restype = i64
+    L.kdt_config_size.restype = i64
     L.kdt_eval_predicates.argtypes = [vp, vp, i64, vp, i32, vp]
     L.kdt_export_store.argtypes = [vp, vp, vp, vp, i64]
     L.kdt_export_triangles_noalloc.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
