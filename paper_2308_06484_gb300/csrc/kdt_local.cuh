@@ -555,7 +555,8 @@ __device__ int move_point(Warp w, const Dev &d, int p, int2 q, int &s0, int &s1,
         if (k < 3 || 2 * k + 8 > LM) {
             if (k >= 3) {
                 // a star too large to stage: take the plain global path (or leave the
-                // whole move to the end of the step when its claims keep failing)
+                // whole move for later when its claims keep failing or its degree grew
+                // past the shared arrays)
                 int rc = delete_point(w, d, p, s0, s1, hint, may_give_up && d.big != nullptr);
                 if (rc == DEL_BUSY) return MV_BIG;
                 if (rc == DEL_HUGE) return MV_HUGE;
