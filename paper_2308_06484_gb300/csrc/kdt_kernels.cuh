@@ -68,10 +68,12 @@ __global__ void k_qt_hist(const int2 *xy, int n, int x0, int y0, int shift, int 
 // The warp's handle and its shared state (counters zero, claims none, random state
 // from `seed`, instance = the points [d.rlo, d.rlo + d.rn)).
 static_assert(C_NUM <= 32, "one lane clears each counter");
-// Seven 128-thread blocks of k_kinetic per SM: 7 x (static shared memory, rounded up to
-// 128 bytes, + 1 KB reserved per block) must fit the SM's 228 KB.  Growing the per-warp
-// block past this drops a block per SM (a quarter of the resident moves) at once.
-static_assert(WPB * sizeof(WarpShared) + sizeof(Dev) <= 32256, "k_kinetic must keep 7 blocks per SM");
+// k_kinetic runs six 128-thread blocks per SM, set by its registers (up to 80 a thread:
+// fewer spills of the inlined move path than at 72, which measured 0.1125 against
+// 0.118 ms per launch on the 1e6-point step).  The shared memory would allow seven:
+// 7 x (static shared memory, rounded up to 128 bytes, + 1 KB reserved per block) fits
+// the SM's 228 KB; keeping that bound leaves the choice open.
+static_assert(WPB * sizeof(WarpShared) + sizeof(Dev) <= 32256, "k_kinetic's shared memory must allow 7 blocks per SM");
 
 __device__ __forceinline__ Warp make_warp(WarpShared *sh, int token, unsigned seed, const Dev &d)
 {
@@ -462,7 +464,7 @@ __device__ __noinline__ void drained_done(Warp w, const Dev &d, int rc, bool hug
     }
 }
 
-__global__ void __launch_bounds__(WPB * 32, 7) k_kinetic(Dev dp, const int3 *moves, const int *head, const int *next,
+__global__ void __launch_bounds__(WPB * 32, 6) k_kinetic(Dev dp, const int3 *moves, const int *head, const int *next,
                                                          Inst I, int ncells, int wpp, int4 *deferred,
                                                          int *defer_count, int defer_cap, int *viol, int viol_cap)
 {
