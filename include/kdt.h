@@ -8,7 +8,7 @@
  *     satisfies the Delaunay constraints (Fig. 4, "input");
  *   - at each time step some points move (Section III, movepoint_i) and the
  *     triangulation is repaired by deleting each moved point and inserting it at its
- *      new position (Section IV; the Update, Delete and Insert steps of Fig. 4);
+ *     new position (Section IV; the Update, Delete and Insert steps of Fig. 4);
  *   - output: the Delaunay triangulation after every time step (Fig. 4, "return
  *     dataset(t)").
  * The triangulation is the unique one defined by the empty-circumcircle property
