@@ -5,12 +5,12 @@
  * plane on one GPU.  It follows the problem statement of the paper "A parallel
  * algorithm for Delaunay triangulation of moving points on the plane":
  *   - input: a point set with x and y coordinates (Section I) whose triangulation
- *     satisfies the Delaunay constraints (Fig. 4, "input");
+ *     satisfies the Delaunay constraints (the input of Fig. 4);
  *   - at each time step some points move (Section III, movepoint_i) and the
  *     triangulation is repaired by deleting each moved point and inserting it at its
  *     new position (Section IV; the Update, Delete and Insert steps of Fig. 4);
- *   - output: the Delaunay triangulation after every time step (Fig. 4, "return
- *     dataset(t)").
+ *   - output: the Delaunay triangulation after every time step (the output of Fig. 4
+ *     at the end of each step).
  * The triangulation is the unique one defined by the empty-circumcircle property
  * (Section I); ties between cocircular points are broken by Simulation of Simplicity
  * (a smaller point id gets a larger lifting perturbation), so results are

@@ -7,8 +7,8 @@
  * code, header, table or helper with that path.
  *
  * What it computes (paper, Section I, definition of the DT; Section IV "Insertion
- * and Deletion", Bowyer-Watson insertion; Fig. 4, "return dataset(t)" after every
- * time step): for a set P of distinct integer points, the unique Delaunay
+ * and Deletion", Bowyer-Watson insertion; Fig. 4, the triangulation it outputs after
+ * every time step): for a set P of distinct integer points, the unique Delaunay
  * triangulation, as a canonical sorted list of triangles.  The kinetic method of the
  * paper reaches the same triangulation by deletions and insertions; the oracle does
  * not replay them, it rebuilds from scratch (the DT is a function of the positions
@@ -394,7 +394,7 @@ static int check_points(const int32_t *xy, int64_t n)
     return dup ? ORC_ERR_DUPLICATE : ORC_OK;
 }
 
-/* Canonical form of the output (Fig. 4, "return dataset(t)"): every finite
+/* Canonical form of the output (Fig. 4, the triangulation after a step): every finite
  * triangle counter-clockwise and rotated so its smallest id comes first; the list
  * sorted lexicographically.  It has 2n - 2 - h rows, h = points on the hull
  * boundary (collinear ones included). */

@@ -248,7 +248,7 @@ __global__ void k_intake_link(Dev d, const int3 *moves, int m, Inst I, int bits,
 
 // ------------------------------------------------------------------ step: kinetic
 
-// One warp per partition (Fig. 4 "foreach block i do in parallel"): for each of the
+// One warp per partition (Fig. 4's parallel loop over the blocks): for each of the
 // block's moved points, Delete (Section IV), Update the coordinate, Insert at the
 // new position (walk, split, Lawson flips).  The new block of a point that crosses a
 // partition border follows from its new position; all blocks share one
