@@ -20,8 +20,10 @@
  *   - Return 0 on success or a negative KDT_ERR_* code; kdt_error_string() names it.
  *   - Pointers marked "host or device" may point to host memory (pageable or pinned)
  *     or to device memory of the handle's GPU; the library detects which and copies
- *     as needed.  The caller keeps ownership of every buffer it passes; the library
- *     copies inputs in before returning and never keeps a caller pointer.
+ *     as needed.  Device memory of any other GPU is rejected with KDT_ERR_ARG before
+ *     anything is launched (managed memory is accepted).  The caller keeps ownership
+ *     of every buffer it passes; the library copies inputs in before returning and
+ *     never keeps a caller pointer.
  *   - The library owns all device state of a handle (allocated in kdt_create /
  *     kdt_build, freed in kdt_destroy).  Handles are independent; no global state.
  *   - Coordinates are int32 in [0, 2^domain_bits) with domain_bits <= 28.
@@ -165,8 +167,8 @@ int kdt_destroy(kdt *h);
 /* ---- the method ------------------------------------------------------------------ */
 
 /* Build the Delaunay triangulation of n distinct points xy[2*i], xy[2*i+1]
- * (host or device) from scratch on the GPU (Fig. 4, "input: a dataset ... that
- * satisfies Delaunay constraints"; Section III partition into blocks).  Replaces any
+ * (host or device) from scratch on the GPU: the triangulated point set that Fig. 4
+ * starts from, divided into the blocks of Section III.  Replaces any
  * previous state.  Errors: KDT_ERR_ARG (NULL, n > 2^28), KDT_ERR_RANGE,
  * KDT_ERR_DUPLICATE, KDT_ERR_DEGENERATE (n < 3 or all collinear), KDT_ERR_CUDA. */
 int kdt_build(kdt *h, const int32_t *xy, int64_t n);
@@ -207,7 +209,7 @@ int32_t kdt_num_instances(const kdt *h);
  * full-rebuild comparator; the same code is the fallback of kdt_step). */
 int kdt_rebuild(kdt *h);
 
-/* Export the triangulation (Fig. 4, "return dataset(t)") as the canonical list:
+/* Export the triangulation (what Fig. 4 returns after each time step) as the canonical list:
  * every finite triangle counter-clockwise, rotated so its smallest id comes first,
  * rows sorted lexicographically; 3 int32 per row into out (host or device, capacity
  * `cap` rows).  *n_tri receives the row count (2n - 2 - h, h = hull points) even when
@@ -234,8 +236,10 @@ int kdt_export_points(kdt *h, int32_t *xy, int64_t cap_points);
  * points (nothing is launched); KDT_ERR_CAPACITY, KDT_ERR_ARG, KDT_ERR_STATE,
  * KDT_ERR_CUDA.
  * The first call on a device looks the scratch array's device address up
- * (cudaGetSymbolAddress, with that device current) and caches it; make that first
- * call before any stream capture.  All calls share the one array, so calls that
+ * (cudaGetSymbolAddress, with that device current) and caches it for the life of the
+ * process; make that first call before any stream capture.  A cudaDeviceReset of that
+ * device discards the array with the context, so do not call this entry point after
+ * one.  All calls share the one array, so calls that
  * overlap on the GPU (other handles' streams, other host threads) race; serialise
  * them.  Each call clears what must start at zero. */
 #define KDT_NOALLOC_MAX_POINTS (1 << 20)

@@ -142,15 +142,29 @@ int dev_to_abi(int s)
     }
 }
 
-bool is_device_ptr(const void *p)
+// Where a caller's pointer points: host memory (pageable or pinned), memory the
+// handle's GPU reads directly (its own device memory, or managed memory), or device
+// memory of another GPU, which every entry point rejects with KDT_ERR_ARG before
+// launching anything (without peer access a kernel touching it would fault).
+enum PtrKind { PTR_HOST = 0, PTR_DEV = 1, PTR_FOREIGN = 2 };
+
+PtrKind ptr_kind(const void *p, int device)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return PTR_HOST;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return PTR_DEV;
+    if (a.type == cudaMemoryTypeDevice) return a.device == device ? PTR_DEV : PTR_FOREIGN;
+    return PTR_HOST;
 }
+
+// true iff p is memory the handle's GPU reads directly (see ptr_kind)
+bool on_device(const kdt *h, const void *p) { return ptr_kind(p, h->device) == PTR_DEV; }
+
+// true iff p is device memory of another GPU
+bool foreign(const kdt *h, const void *p) { return p && ptr_kind(p, h->device) == PTR_FOREIGN; }
 
 int grow(Buf &b, size_t bytes)
 {
@@ -778,12 +792,14 @@ int step_impl(kdt *h, const kdt_move *moves, const int64_t *moff, int64_t m)
     if (m == 0) return KDT_OK;
     if (m > h->n) return KDT_ERR_DUPLICATE;  // some id must repeat (or be out of range)
     CK(cudaSetDevice(h->device));
+    const PtrKind mk = ptr_kind(moves, h->device);
+    if (mk == PTR_FOREIGN) return KDT_ERR_ARG;
     int rc = ensure_moves(h, m);
     if (rc) return rc;
     cudaStream_t st = h->stream;
     const int mi = (int)m;
     const int3 *mp = (const int3 *)moves;
-    if (!is_device_ptr(moves)) {
+    if (mk != PTR_DEV) {
         CK(cudaMemcpyAsync(h->moves, moves, (size_t)m * sizeof(int3), cudaMemcpyHostToDevice, st));
         mp = h->moves;
     }
@@ -928,7 +944,7 @@ int export_range(kdt *h, int s0, int nslots, int idbase, int np, int32_t *out, i
     int64_t total = h->hscal[S_TOTAL];
     *n_tri = total;
     if (total > cap) return KDT_ERR_CAPACITY;
-    bool dev_out = total > 0 && is_device_ptr(out);
+    bool dev_out = total > 0 && on_device(h, out);
     int3 *dst;
     if (dev_out) {
         dst = (int3 *)out;
@@ -1019,6 +1035,7 @@ int build_quadtree(kdt *h)
 int build_impl(kdt *h, const int32_t *xy, const int64_t *offs, int n_inst)
 {
     CK(cudaSetDevice(h->device));
+    if (foreign(h, xy)) return KDT_ERR_ARG;
     free_state(h);
     int rc = alloc_state(h, offs, n_inst);
     if (rc) {
@@ -1026,7 +1043,7 @@ int build_impl(kdt *h, const int32_t *xy, const int64_t *offs, int n_inst)
         return rc;
     }
     CK(cudaMemcpyAsync(h->xy, xy, (size_t)h->n * sizeof(int2),
-                       is_device_ptr(xy) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+                       on_device(h, xy) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
     rc = rebuild_all(h);
     if (rc == 0 && h->cfg.quadtree && h->ninst == 1) rc = build_quadtree(h);
     return rc;
@@ -1226,8 +1243,9 @@ int kdt_export_points(kdt *h, int32_t *xy, int64_t cap_points)
     if (!h->built) return KDT_ERR_STATE;
     if (cap_points < h->n) return KDT_ERR_CAPACITY;
     CK(cudaSetDevice(h->device));
+    if (foreign(h, xy)) return KDT_ERR_ARG;
     CK(cudaMemcpyAsync(xy, h->xy, (size_t)h->n * sizeof(int2),
-                       is_device_ptr(xy) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+                       on_device(h, xy) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return KDT_OK;
 }
@@ -1239,6 +1257,7 @@ int kdt_d_values(kdt *h, int32_t N, int64_t *dist2, int64_t *cell_min2, kdt_dinf
     for (int i = 0; i < h->ninst; ++i)
         if (h->pofs[i + 1] - h->pofs[i] <= N) return KDT_ERR_ARG;
     CK(cudaSetDevice(h->device));
+    if (foreign(h, dist2) || foreign(h, cell_min2)) return KDT_ERR_ARG;
     cudaStream_t st = h->stream;
     const int n = (int)h->n;
     // neighbour lists (CSR) from the live triangles
@@ -1256,8 +1275,8 @@ int kdt_d_values(kdt *h, int32_t N, int64_t *dist2, int64_t *cell_min2, kdt_dinf
     CK(cudaMemsetAsync(deg, 0, (size_t)n * sizeof(int), st));  // now the fill positions
     k_nbr_fill<<<thread_grid(h, h->cap, 256), 256, 0, st>>>(h->tv, h->cap, off, deg, (int *)h->nb_list.p);
     // the N-th nearest neighbours and their minima
-    const bool dist_dev = dist2 && is_device_ptr(dist2);
-    const bool cmin_dev = cell_min2 && is_device_ptr(cell_min2);
+    const bool dist_dev = dist2 && on_device(h, dist2);
+    const bool cmin_dev = cell_min2 && on_device(h, cell_min2);
     long long *dd = nullptr;
     unsigned long long *cm = nullptr;
     if (dist2) {
@@ -1412,7 +1431,7 @@ extern "C" int kdt_export_triangles_noalloc(kdt *h, int32_t *out, int64_t cap, i
     if (!h->built) return KDT_ERR_STATE;
     if (h->n > KDT_NOALLOC_MAX_POINTS) return KDT_ERR_TOO_LARGE;
     CK(cudaSetDevice(h->device));
-    if (cap > 0 && !is_device_ptr(out)) return KDT_ERR_ARG;
+    if (cap > 0 && !on_device(h, out)) return KDT_ERR_ARG;
     int *scratch = noalloc_scratch(h->device);
     if (!scratch) return KDT_ERR_CUDA;
     cudaStream_t st = h->stream;
@@ -1427,6 +1446,7 @@ extern "C" int kdt_export_triangles_noalloc(kdt *h, int32_t *out, int64_t cap, i
     k_scan_tile<<<ntiles, SCAN_THREADS, 0, st>>>(cnt, off, n, tiles);
     k_scan_sums<<<1, 1024, 0, st>>>(tiles, ntiles, total);
     k_scan_add<<<ntiles, SCAN_THREADS, 0, st>>>(off, n, tiles);
+    h->stats.kernel_launches += 4;
     CK(cudaGetLastError());
     int tot = 0;
     CK(cudaMemcpyAsync(&tot, total, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1436,6 +1456,7 @@ extern "C" int kdt_export_triangles_noalloc(kdt *h, int32_t *out, int64_t cap, i
     CK(cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(int), st));
     k_exp_place<<<thread_grid(h, h->cap, 256), 256, 0, st>>>(h->tv, h->cap, off, cnt, (int3 *)out, 0);
     k_exp_sortseg<<<thread_grid(h, n, 256), 256, 0, st>>>(n, off, cnt, (int3 *)out);
+    h->stats.kernel_launches += 2;
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));
     return KDT_OK;
@@ -1449,8 +1470,8 @@ extern "C" {
 int kdt_set_trace(kdt *h, float *features, int32_t *labels, int64_t cap)
 {
     if (!h || cap < 0 || (cap > 0 && (!features || !labels)) || cap > INT_MAX) return KDT_ERR_ARG;
-    if (cap > 0 && (!is_device_ptr(features) || !is_device_ptr(labels))) return KDT_ERR_ARG;
     CK(cudaSetDevice(h->device));
+    if (cap > 0 && (!on_device(h, features) || !on_device(h, labels))) return KDT_ERR_ARG;
     if (!h->trace_count && cudaMalloc(&h->trace_count, sizeof(int)) != cudaSuccess) return KDT_ERR_CUDA;
     CK(cudaMemsetAsync(h->trace_count, 0, sizeof(int), h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -1478,6 +1499,7 @@ int kdt_set_proposal(kdt *h, const uint16_t *params_bf16)
 {
     if (!h) return KDT_ERR_ARG;
     CK(cudaSetDevice(h->device));
+    if (foreign(h, params_bf16)) return KDT_ERR_ARG;
     if (!params_bf16) {
         h->prop_on = false;
         h->gen++;
@@ -1485,7 +1507,7 @@ int kdt_set_proposal(kdt *h, const uint16_t *params_bf16)
     }
     if (!h->mlp_w && cudaMalloc(&h->mlp_w, MLP_PARAMS * sizeof(uint16_t)) != cudaSuccess) return KDT_ERR_CUDA;
     CK(cudaMemcpyAsync(h->mlp_w, params_bf16, MLP_PARAMS * sizeof(uint16_t),
-                       is_device_ptr(params_bf16) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+                       on_device(h, params_bf16) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     h->prop_on = true;
     h->gen++;
@@ -1496,9 +1518,9 @@ int kdt_mlp_forward(kdt *h, const uint16_t *params_bf16, const float *x, int64_t
 {
     if (!h || rows < 0 || (rows > 0 && (!params_bf16 || !x || !out))) return KDT_ERR_ARG;
     if (rows == 0) return KDT_OK;
-    if (!is_device_ptr(params_bf16) || !is_device_ptr(x) || !is_device_ptr(out)) return KDT_ERR_ARG;
-    if (((uintptr_t)params_bf16 & 3) != 0) return KDT_ERR_ARG;  // read as BF16 pairs
     CK(cudaSetDevice(h->device));
+    if (!on_device(h, params_bf16) || !on_device(h, x) || !on_device(h, out)) return KDT_ERR_ARG;
+    if (((uintptr_t)params_bf16 & 3) != 0) return KDT_ERR_ARG;  // read as BF16 pairs
     long long warps = rows < (1ll << 22) ? rows : (1ll << 22);
     int blocks = (int)((warps * 32 + 255) / 256);
     k_mlp_forward<<<blocks, 256, 0, h->stream>>>((const unsigned short *)params_bf16, x, rows, out);
@@ -1511,10 +1533,10 @@ int kdt_mlp_loss_grad(kdt *h, const uint16_t *params_bf16, const float *x, const
                       const int64_t *index, int64_t rows, float lam, float *grad, float *loss)
 {
     if (!h || rows <= 0 || !params_bf16 || !x || !labels || !grad) return KDT_ERR_ARG;
-    if (!is_device_ptr(params_bf16) || !is_device_ptr(x) || !is_device_ptr(labels) || !is_device_ptr(grad) ||
-        (loss && !is_device_ptr(loss)) || (index && !is_device_ptr(index)))
-        return KDT_ERR_ARG;
     CK(cudaSetDevice(h->device));
+    if (!on_device(h, params_bf16) || !on_device(h, x) || !on_device(h, labels) || !on_device(h, grad) ||
+        (loss && !on_device(h, loss)) || (index && !on_device(h, index)))
+        return KDT_ERR_ARG;
     int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
     long long tiles = (rows + GT - 1) / GT;
@@ -1542,10 +1564,10 @@ int kdt_mlp_adam(kdt *h, float *master, const float *grad, float *m, float *v, i
                  float beta2, float eps, uint16_t *params_bf16)
 {
     if (!h || !master || !grad || !m || !v || t < 1) return KDT_ERR_ARG;
-    if (!is_device_ptr(master) || !is_device_ptr(grad) || !is_device_ptr(m) || !is_device_ptr(v) ||
-        (params_bf16 && !is_device_ptr(params_bf16)))
-        return KDT_ERR_ARG;
     CK(cudaSetDevice(h->device));
+    if (!on_device(h, master) || !on_device(h, grad) || !on_device(h, m) || !on_device(h, v) ||
+        (params_bf16 && !on_device(h, params_bf16)))
+        return KDT_ERR_ARG;
     double bc1 = 1.0 - std::pow((double)beta1, (double)t), bc2 = 1.0 - std::pow((double)beta2, (double)t);
     k_mlp_adam<<<(MLP_PARAMS + 255) / 256, 256, 0, h->stream>>>(master, grad, m, v, MLP_PARAMS, lr, beta1, beta2, eps,
                                                                 (float)bc1, (float)bc2,

@@ -103,3 +103,33 @@ class Trainer:
         acc = float((pred == y[:, 0].long()).float().mean().item()) if x.shape[0] else 0.0
         mae = float((out[:, MLP_SLOTS] - torch.log2(y[:, 1].float())).abs().mean().item()) if x.shape[0] else 0.0
         return acc, mae
+
+
+def collect_traces(sources, cap: int = 1_000_000, bits: int = 24):
+    """Training rows of the given workloads: for every (workload, steps) pair, a fresh
+    triangulation of the workload's points on its grid records the rows of `steps`
+    kinetic steps.  Returns the rows of all sources concatenated (x, y)."""
+    import torch
+    xs, ys = [], []
+    for w, steps in sources:
+        tri = _kdt.Triangulation(_kdt.default_config(grid=w.grid, domain_bits=bits))
+        tri.build(torch.from_numpy(w.positions).cuda())
+        tr = Trace(cap)
+        tr.attach(tri)
+        for _ in range(steps):
+            tri.step(torch.from_numpy(w.next_moves()).cuda())
+        tr.detach(tri)
+        x, y = tr.view()
+        xs.append(x.clone())
+        ys.append(y.clone())
+        tri.close()
+    return torch.cat(xs), torch.cat(ys)
+
+
+def default_training_sources(c3_n: int = 2_000_000, c3_grid: int = 90, c2_steps: int = 100, c3_steps: int = 4):
+    """The training workloads of the proposal: the 1e6-point uniform workload with its
+    training seed (102) and the mixture + lattice distribution at c3_n points on a
+    c3_grid^2 grid (about 250 points per partition, as the 16e6-point workload) with
+    seed 103.  Evaluation uses the uniform workload's own seed (2)."""
+    from . import workloads as W
+    return [(W.c2(seed=102), c2_steps), (W.c3(n=c3_n, grid=c3_grid, seed=103), c3_steps)]

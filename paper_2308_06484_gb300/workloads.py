@@ -113,6 +113,13 @@ def cell_of(xy, grid: int, bits: int) -> np.ndarray:
     return cy * grid + cx
 
 
+def _stable_order(cells, ncell):
+    """Indices sorting `cells` stably (a radix sort when the cell index fits 16 bits)."""
+    if ncell <= 65536:
+        return np.argsort(cells.astype(np.uint16), kind="stable")
+    return np.argsort(cells, kind="stable")
+
+
 class KineticWorkload:
     """A point set plus a seeded stream of per-step moves.
 
@@ -130,6 +137,7 @@ class KineticWorkload:
         self.rng = np.random.default_rng(seed)
         self.pos = np.ascontiguousarray(np.asarray(xy, dtype=np.int64).reshape(-1, 2))
         self.skeys = np.sort(_key(self.pos))
+        self.cells = cell_of(self.pos, self.grid, self.bits)  # kept current for moved points
         self.step_index = 0
 
     @property
@@ -142,25 +150,36 @@ class KineticWorkload:
 
     def _choose(self):
         G = self.grid
-        cells = cell_of(self.pos, G, self.bits)
+        cells = self.cells
         counts = np.bincount(cells, minlength=G * G)
         starts = np.concatenate([[0], np.cumsum(counts)[:-1]])
         lo, hi = self.mpc
         want = self.rng.integers(lo, hi + 1, size=G * G)
         want = np.minimum(want, counts)
         if hi == 1:
-            order = np.argsort(cells, kind="stable")
+            order = _stable_order(cells, G * G)
             cs = np.nonzero(want)[0]
             off = (self.rng.random(cs.shape[0]) * counts[cs]).astype(np.int64)
             chosen = order[starts[cs] + off]
             return chosen
-        # several points per cell: random keys, take the first `want` of each segment
-        # (order by cell, then key, then id: two stable sorts)
+        # several points per cell: random keys; per cell the `want` points with the
+        # smallest keys (ties by id), in (cell, key, id) order
         rk = self.rng.random(self.n)
-        o1 = np.argsort(rk, kind="stable")
-        order2 = o1[np.argsort(cells[o1], kind="stable")]
-        rank = np.arange(self.n) - starts[cells[order2]]
-        sel = rank < want[cells[order2]]
+        # Only keys below a per-cell threshold can be among the smallest `want` as long
+        # as at least `want` keys of that cell are below it; cells short of that keep
+        # every point.  The selection is the same as sorting every point.
+        thr = (want + 4.0 * np.sqrt(want) + 8.0) / np.maximum(counts, 1)
+        cand = rk < thr[cells]
+        short = np.bincount(cells[cand], minlength=G * G) < want
+        if short.any():
+            cand |= short[cells]
+        idx = np.nonzero(cand)[0]
+        o = np.lexsort((rk[idx], cells[idx]))  # stable: ties keep increasing id
+        order2 = idx[o]
+        c_o = cells[order2]
+        cstart = np.concatenate([[0], np.cumsum(np.bincount(c_o, minlength=G * G))[:-1]])
+        rank = np.arange(order2.shape[0]) - cstart[c_o]
+        sel = rank < want[c_o]
         return order2[sel]
 
     def next_moves(self) -> np.ndarray:
@@ -208,6 +227,7 @@ class KineticWorkload:
         old = _key(self.pos[ids])
         self.pos[ids, 0] = tx[sel]
         self.pos[ids, 1] = ty[sel]
+        self.cells[ids] = cell_of(self.pos[ids], self.grid, self.bits)
         new = _key(self.pos[ids])
         keep = np.ones(self.skeys.size, dtype=bool)
         keep[np.searchsorted(self.skeys, old)] = False

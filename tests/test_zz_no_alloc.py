@@ -30,7 +30,10 @@ def test_noalloc_matches_export_two_calls_in_a_row():
     t.build(w.positions)
     ref = t.export_triangles()
     for _ in range(2):  # the shared scratch keeps the last call's contents
+        before = t.stats()["kernel_launches"]
         got, nt = _export_noalloc(t, ref.shape[0] + 5)
+        # count, three scan passes, place, segment sort
+        assert t.stats()["kernel_launches"] - before == 6
         assert nt == ref.shape[0]
         assert np.array_equal(got, ref)
     # after a time step the triangulation changes; the next call must follow it
