@@ -113,6 +113,29 @@ typedef struct {
                               is the leaf holding its current position (clamped into the
                               square).  Single-instance handles only (kdt_build_batch returns
                               KDT_ERR_ARG).  Scheduling only: the triangulation is the same. */
+    float rebuild_displacement; /* f; 0 = off (default).  The rebuild rule of the paper's
+                              abstract (points that move far are cheaper to triangulate
+                              again) with Section III's d as the yardstick: before a step
+                              changes anything, every move's squared displacement |q - p|^2
+                              is compared with f^2 * d_local^2, where d_local^2 is the
+                              running minimum of the N-th nearest-neighbour squared
+                              distance over the move's partition (the per-partition minima
+                              of kdt_d_values, kept over its calls since the partitions
+                              were last set, N of the last call).  If any move exceeds it
+                              the step is done as a certified GPU rebuild of the final
+                              positions (kdt_stats.far_rebuilds).  With f > 0 a step that
+                              finds no d values computes them first (N = 1, or the N of the
+                              last call).  The triangulation is the same either way.      */
+    int32_t plan;          /* step planner (scheduling only; the triangulation is the same):
+                              0 (default): the kinetic kernel takes the partitions in index
+                              order.  1: before the moves start, every move's star is walked
+                              (its degree k) and each partition's work is estimated as the
+                              sum over its moves of k + 8; the partitions are then handed out
+                              largest estimate first (64 logarithmic classes).  2: as 1, and
+                              with a proposal set (kdt_set_proposal) the network is evaluated
+                              for all moves at once in the planner (instead of inside each
+                              move); its predicted cavity size 2^out17 is added to the
+                              estimate, and its guess is the locate's first candidate.      */
 } kdt_config;
 
 /* Counters since creation (or kdt_reset_stats). */
@@ -148,7 +171,9 @@ typedef struct {
     int64_t span_drained_ns;      /* ... start to the end of the last other drained move    */
     int64_t cycles_drained_max;   /* longest move taken from the list, cycles (debug bit 1) */
     int64_t redeferred;           /* drained moves left for later again (debug bit 1)       */
-    int64_t reserved[8];
+    int64_t far_rebuilds;         /* steps done as a rebuild because a move went farther
+                                     than rebuild_displacement * d_local                  */
+    int64_t reserved[7];
 } kdt_stats;
 
 /* ---- lifecycle ------------------------------------------------------------------ */

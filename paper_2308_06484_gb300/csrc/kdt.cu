@@ -22,12 +22,13 @@
 #include "../../include/kdt.h"
 #include "kdt_kernels.cuh"
 #include "kdt_dcalc.cuh"
+#include "kdt_plan.cuh"
 
 using namespace kd;
 
 namespace {
 
-constexpr int ABI_VERSION = 5;
+constexpr int ABI_VERSION = 6;
 
 struct Buf {
     void *p = nullptr;
@@ -85,6 +86,16 @@ struct kdt {
     Buf nb_deg, nb_off, nb_list, dc_dist, dc_cmin, dc_scal;
     int64_t d2_run = INT64_MAX;
     int d_n = 0;
+    // the displacement rule (kdt_config.rebuild_displacement): running per-partition
+    // d_local^2 (INT64_MAX = unknown), valid since the partitions were last set
+    unsigned long long *dloc2 = nullptr;
+    bool dloc_valid = false;
+    // step planner (kdt_config.plan): per-partition cost estimates, the order of the
+    // partitions, class sizes and cursors, and the network's guess per point
+    float *pcost = nullptr;
+    int *order = nullptr;
+    int *ohist = nullptr;
+    signed char *pguess = nullptr;
     // quad-tree partitions (kdt_config.quadtree): leaf of every fine cell, the square
     int *qmap = nullptr;
     int qx0 = 0, qy0 = 0, qshift = 0, qF = 0, qleaves = 0, qleaf_side_lg = 0;
@@ -224,6 +235,7 @@ Dev make_dev(kdt *h)
     d.rlo = 0;
     d.rn = (int)std::max<int64_t>(h->n, 1);
     d.mlp = h->prop_on ? h->mlp_w : nullptr;
+    d.pguess = h->prop_on && h->cfg.plan == 2 ? h->pguess : nullptr;
     d.trace_x = h->trace_x;
     d.trace_y = h->trace_y;
     d.trace_count = h->trace_count;
@@ -248,6 +260,7 @@ Inst make_inst(kdt *h)
     I.qy0 = h->qy0;
     I.qshift = h->qshift;
     I.qF = h->qF;
+    I.order = h->cfg.plan ? h->order : nullptr;
     return I;
 }
 
@@ -496,8 +509,12 @@ int set_partitions(kdt *h, int ppp)
     if (cells > INT_MAX / 8) return KDT_ERR_ARG;
     h->cofs[h->ninst] = (int)cells;
     h->ncells = (int)cells;
-    if (dalloc(&h->head, (size_t)cells) || dalloc(&h->d_cofs, h->ninst + 1) || dalloc(&h->d_grid, h->ninst))
+    if (dalloc(&h->head, (size_t)cells) || dalloc(&h->d_cofs, h->ninst + 1) || dalloc(&h->d_grid, h->ninst) ||
+        dalloc(&h->dloc2, (size_t)cells) || dalloc(&h->pcost, (size_t)cells) || dalloc(&h->order, (size_t)cells))
         return KDT_ERR_CUDA;
+    k_fill_u64<<<thread_grid(h, cells, 256), 256, 0, h->stream>>>(h->dloc2, cells, (unsigned long long)INT64_MAX);
+    h->stats.kernel_launches++;
+    h->dloc_valid = false;
     CK(cudaMemcpy(h->d_cofs, h->cofs.data(), (h->ninst + 1) * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(h->d_grid, h->igrid.data(), h->ninst * sizeof(int), cudaMemcpyHostToDevice));
     h->gen++;
@@ -519,7 +536,7 @@ void free_state(kdt *h)
     h->gen++;
     void *ps[] = {h->xy, h->pt_tri, h->pt_stamp, h->tv, h->tn, h->viol, h->moves, h->gmoves, h->old_xy,
                   h->next, h->head, h->deferred, h->dirty, h->scan_tmp, h->d_pofs, h->d_cofs, h->d_grid,
-                  h->d_moff, h->d_tofs, h->qmap};
+                  h->d_moff, h->d_tofs, h->qmap, h->dloc2, h->pcost, h->order, h->ohist, h->pguess};
     for (void *p : ps)
         if (p) cudaFree(p);
     if (h->h_moff) cudaFreeHost(h->h_moff);
@@ -529,6 +546,12 @@ void free_state(kdt *h)
     h->d_pofs = nullptr; h->d_cofs = nullptr; h->d_grid = nullptr; h->d_moff = nullptr; h->h_moff = nullptr;
     h->d_tofs = nullptr;
     h->qmap = nullptr;
+    h->dloc2 = nullptr;
+    h->dloc_valid = false;
+    h->pcost = nullptr;
+    h->order = nullptr;
+    h->ohist = nullptr;
+    h->pguess = nullptr;
     h->qleaves = 0;
     h->mcap = 0; h->dirty_cap = 0; h->scan_tmp_cap = 0;
     Buf *bs[] = {&h->key, &h->bord, &h->hist, &h->hoff, &h->exp_cnt, &h->exp_off, &h->exp_fill, &h->exp_out,
@@ -557,7 +580,7 @@ int alloc_state(kdt *h, const int64_t *offs, int n_inst)
     h->built = false;
     if (dalloc(&h->xy, h->n) || dalloc(&h->pt_tri, h->n) || dalloc(&h->pt_stamp, h->n) || dalloc(&h->tv, h->cap) ||
         dalloc(&h->tn, h->cap) || dalloc(&h->d_pofs, n_inst + 1) || dalloc(&h->d_moff, n_inst + 1) ||
-        dalloc(&h->d_tofs, n_inst + 1))
+        dalloc(&h->d_tofs, n_inst + 1) || dalloc(&h->pguess, h->n) || dalloc(&h->ohist, 2 * PLAN_CLASSES))
         return KDT_ERR_CUDA;
     if (cudaMallocHost(&h->h_moff, (n_inst + 1) * sizeof(int)) != cudaSuccess) return KDT_ERR_CUDA;
     CK(cudaMemcpy(h->d_pofs, h->pofs.data(), (n_inst + 1) * sizeof(int), cudaMemcpyHostToDevice));
@@ -679,6 +702,17 @@ int ensure_big(kdt *h)
     return 0;
 }
 
+// kdt_d_values without the argument checks (also run by a step whose displacement rule
+// needs d_local)
+int d_values_impl(kdt *h, int N, int64_t *dist2, int64_t *cell_min2, kdt_dinfo *info);
+
+// f^2 of the displacement rule, 0 when it is off
+double far2(const kdt *h)
+{
+    const double f = h->cfg.rebuild_displacement;
+    return f > 0.0 ? f * f : 0.0;
+}
+
 int enqueue_step(kdt *h, cudaStream_t st, const Dev &d, const int3 *mp, int mi, bool from_ctl)
 {
     int cap = from_ctl ? h->mcap : mi;
@@ -691,7 +725,21 @@ int enqueue_step(kdt *h, cudaStream_t st, const Dev &d, const int3 *mp, int mi, 
     CK(cudaMemsetAsync(h->head, 0xff, (size_t)h->ncells * sizeof(int), st));  // empty lists
     CK(cudaMemsetAsync(h->deferred, 0xff, (size_t)h->mcap * sizeof(int4), st));  // empty entries (-1)
     k_intake_link<<<thread_grid(h, cap, 256), 256, 0, st>>>(d, mp, mi, I, h->cfg.domain_bits, h->head, h->next,
-                                                            h->old_xy, h->gmoves);
+                                                            h->old_xy, h->gmoves, h->dloc2, far2(h));
+    if (h->cfg.plan) {
+        // the planner: estimated work per partition (and the network's guesses), then
+        // the partitions in order of decreasing estimate
+        CK(cudaMemsetAsync(h->pcost, 0, (size_t)h->ncells * sizeof(float), st));
+        CK(cudaMemsetAsync(h->ohist, 0, 2 * PLAN_CLASSES * sizeof(int), st));
+        const bool net = h->prop_on && h->cfg.plan == 2;
+        int pblocks = (int)std::min<long long>(((long long)cap + PLAN_THREADS - 1) / PLAN_THREADS,
+                                               8ll * sm_count(h->device));
+        k_plan<<<std::max(pblocks, 1), PLAN_THREADS, 0, st>>>(d, h->gmoves, h->old_xy, mi, I, h->cfg.domain_bits,
+                                                             net ? h->mlp_w : nullptr, net ? h->pguess : nullptr,
+                                                             h->pcost);
+        k_order<<<thread_grid(h, h->ncells, 256), 256, 0, st>>>(h->pcost, h->ncells, h->ohist, h->order, 0);
+        k_order<<<thread_grid(h, h->ncells, 256), 256, 0, st>>>(h->pcost, h->ncells, h->ohist, h->order, 1);
+    }
     // inside a capture an event record must be an external node to keep its timestamp
     unsigned evflags = from_ctl ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (h->cfg.timing) CK(cudaEventRecordWithFlags(h->ev0, st, evflags));
@@ -814,7 +862,7 @@ int step_impl(kdt *h, const kdt_move *moves, const int64_t *moff, int64_t m)
         CK(cudaMemsetAsync(h->scal, 0, S_NUM * sizeof(int), st));
         CK(cudaMemsetAsync(h->head, 0xff, (size_t)h->ncells * sizeof(int), st));
         k_intake_link<<<thread_grid(h, mi, 256), 256, 0, st>>>(d, mp, mi, make_inst(h), h->cfg.domain_bits, h->head,
-                                                               h->next, h->old_xy, h->gmoves);
+                                                               h->next, h->old_xy, h->gmoves, nullptr, 0.0);
         h->stats.kernel_launches++;
         if (sync_scalars(h)) return KDT_ERR_CUDA;
         if (h->hscal[S_STATUS]) return dev_to_abi(h->hscal[S_STATUS]);
@@ -833,6 +881,12 @@ int step_impl(kdt *h, const kdt_move *moves, const int64_t *moff, int64_t m)
     if (rc) return rc;
     rc = ensure_big(h);
     if (rc) return rc;
+    if (far2(h) > 0.0 && !h->dloc_valid) {
+        // the displacement rule needs d_local: compute it (a failure, e.g. an instance
+        // with too few points, leaves the rule inactive for this step)
+        kdt_dinfo info;
+        if (d_values_impl(h, h->d_n > 0 ? h->d_n : 1, nullptr, nullptr, &info) == KDT_ERR_CUDA) return KDT_ERR_CUDA;
+    }
     d = make_dev(h);
     bool timed = h->cfg.timing || (h->tune_idx >= 0 && !h->tune_done);
     if (h->cfg.use_graph) {
@@ -866,7 +920,7 @@ int step_impl(kdt *h, const kdt_move *moves, const int64_t *moff, int64_t m)
         if (enqueue_step(h, st, d, mp, mi, false)) return KDT_ERR_CUDA;
         if (timed) CK(cudaEventRecord(h->ev3, st));
     }
-    h->stats.kernel_launches += 2;
+    h->stats.kernel_launches += h->cfg.plan ? 5 : 2;
     CK(cudaStreamSynchronize(st));
     if (h->hscal[S_CERTPEND] && !h->hscal[S_STATUS]) {
         // a long dirty list (global-path writes): certify it here, appending to the
@@ -890,6 +944,21 @@ int step_impl(kdt *h, const kdt_move *moves, const int64_t *moff, int64_t m)
     }
     int s = h->hscal[S_STATUS];
     if (s == DEV_ARG || s == DEV_RANGE || s == DEV_DUP_ID) return dev_to_abi(s);  // intake: nothing modified
+    if (s == DEV_FAR) {
+        // a move went farther than the displacement rule allows: the kinetic kernel
+        // stopped before changing anything; triangulate the final positions again
+        h->stats.far_rebuilds++;
+        k_set_positions<<<(mi + 255) / 256, 256, 0, st>>>(h->xy, h->gmoves, mi);
+        h->stats.kernel_launches++;
+        rc = rebuild_all(h);
+        if (rc) {
+            int rr = roll_back(h, mi);
+            return rr ? rr : rc;
+        }
+        h->stats.steps++;
+        h->stats.moves += m;
+        return KDT_OK;
+    }
     if (s == 0) {
         int ds = 0;
         if (repair_step(h, &ds)) return KDT_ERR_CUDA;
@@ -1109,7 +1178,8 @@ int kdt_create(kdt **out, const kdt_config *cfg, int device, void *cuda_stream)
     else kdt_default_config(&c);
     if (c.domain_bits <= 0 || c.domain_bits > 28 || c.grid < 0 || c.grid > 4096 || c.retry_cap < 0 ||
         c.points_per_partition < 0 || c.warps_per_partition < 0 || c.warps_per_partition > 32 ||
-        c.variant < 0 || c.variant > 2 || c.quadtree < 0 || c.quadtree > 1)
+        c.variant < 0 || c.variant > 2 || c.quadtree < 0 || c.quadtree > 1 ||
+        !(c.rebuild_displacement >= 0.0f) || c.rebuild_displacement > 1e9f || c.plan < 0 || c.plan > 2)
         return KDT_ERR_ARG;
     if (c.retry_cap == 0) c.retry_cap = 4096;
     if (cudaSetDevice(device) != cudaSuccess) return KDT_ERR_CUDA;
@@ -1254,10 +1324,19 @@ int kdt_d_values(kdt *h, int32_t N, int64_t *dist2, int64_t *cell_min2, kdt_dinf
 {
     if (!h || !info || N < 1 || N > DC_MAX_N) return KDT_ERR_ARG;
     if (!h->built) return KDT_ERR_STATE;
-    for (int i = 0; i < h->ninst; ++i)
-        if (h->pofs[i + 1] - h->pofs[i] <= N) return KDT_ERR_ARG;
     CK(cudaSetDevice(h->device));
     if (foreign(h, dist2) || foreign(h, cell_min2)) return KDT_ERR_ARG;
+    return d_values_impl(h, N, dist2, cell_min2, info);
+}
+
+}  // extern "C"
+
+namespace {
+
+int d_values_impl(kdt *h, int N, int64_t *dist2, int64_t *cell_min2, kdt_dinfo *info)
+{
+    for (int i = 0; i < h->ninst; ++i)
+        if (h->pofs[i + 1] - h->pofs[i] <= N) return KDT_ERR_ARG;
     cudaStream_t st = h->stream;
     const int n = (int)h->n;
     // neighbour lists (CSR) from the live triangles
@@ -1287,21 +1366,24 @@ int kdt_d_values(kdt *h, int32_t N, int64_t *dist2, int64_t *cell_min2, kdt_dinf
             dd = (long long *)h->dc_dist.p;
         }
     }
-    if (cell_min2) {
-        if (cmin_dev) {
-            cm = (unsigned long long *)cell_min2;
-        } else {
-            if (grow(h->dc_cmin, (size_t)std::max(h->ncells, 1) * sizeof(long long))) return KDT_ERR_CUDA;
-            cm = (unsigned long long *)h->dc_cmin.p;
-        }
-        k_fill_u64<<<thread_grid(h, h->ncells, 256), 256, 0, st>>>(cm, h->ncells, (unsigned long long)INT64_MAX);
+    // per-partition minima: into the caller's device buffer, else the handle's (they
+    // also feed the displacement rule's running d_local^2)
+    if (cmin_dev) {
+        cm = (unsigned long long *)cell_min2;
+    } else {
+        if (grow(h->dc_cmin, (size_t)std::max(h->ncells, 1) * sizeof(long long))) return KDT_ERR_CUDA;
+        cm = (unsigned long long *)h->dc_cmin.p;
     }
+    k_fill_u64<<<thread_grid(h, h->ncells, 256), 256, 0, st>>>(cm, h->ncells, (unsigned long long)INT64_MAX);
     unsigned long long *sc = (unsigned long long *)h->dc_scal.p;  // [0] minimum, [1] largest degree
     unsigned long long init[2] = {(unsigned long long)INT64_MAX, 0ull};
     CK(cudaMemcpyAsync(sc, init, sizeof init, cudaMemcpyHostToDevice, st));
     k_nth_nn<<<thread_grid(h, n, 128), 128, 0, st>>>(h->xy, off, (const int *)h->nb_list.p, n, N, make_inst(h),
                                                     h->cfg.domain_bits, dd, cm, sc, (int *)(sc + 1));
-    h->stats.kernel_launches += 7;
+    const int restart = !h->dloc_valid || h->d_n != N;
+    k_merge_min_u64<<<thread_grid(h, h->ncells, 256), 256, 0, st>>>(h->dloc2, cm, h->ncells, restart);
+    h->dloc_valid = true;
+    h->stats.kernel_launches += 8;
     CK(cudaGetLastError());
     if (dist2 && !dist_dev)
         CK(cudaMemcpyAsync(dist2, dd, (size_t)n * sizeof(long long), cudaMemcpyDeviceToHost, st));
@@ -1327,6 +1409,10 @@ int kdt_d_values(kdt *h, int32_t N, int64_t *dist2, int64_t *cell_min2, kdt_dinf
     }
     return KDT_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 int kdt_verify(kdt *h, int64_t *bad)
 {

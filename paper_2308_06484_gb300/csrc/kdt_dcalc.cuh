@@ -114,6 +114,14 @@ __global__ void k_nth_nn(const int2 *xy, const int *off, const int *nbr, int n, 
     }
 }
 
+// run[c] = min(run[c], cur[c]) (or cur[c] when restart): the running per-partition
+// d_local^2 of the displacement rule
+__global__ void k_merge_min_u64(unsigned long long *run, const unsigned long long *cur, long long n, int restart)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        run[i] = restart ? cur[i] : min(run[i], cur[i]);
+}
+
 __global__ void k_fill_u64(unsigned long long *a, long long n, unsigned long long v)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)

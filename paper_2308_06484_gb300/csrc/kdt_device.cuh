@@ -94,6 +94,8 @@ struct Dev {
     unsigned long long *counters;
     // learned locate proposal (kdt_mlp.cuh) and its training rows; null = off
     const unsigned short *mlp;  // network parameters, BF16
+    const signed char *pguess;  // the step planner's guess per point (0..16, -1 none), or null:
+                                // the move evaluates the network itself
     float *trace_x;             // features, trace_cap x 32
     int *trace_y;               // (slot, cavity size) per row
     int *trace_count;           // rows written (may exceed trace_cap: later rows dropped)

@@ -12,6 +12,8 @@ namespace kd {
 
 constexpr int WPB = 4;  // warps per block of the warp-per-item kernels
 constexpr int DEV_DUP_ID = 10;  // a move id repeated within one step (found at intake)
+constexpr int DEV_FAR = 11;     // a move went farther than the rebuild rule allows (found at intake):
+                                // not an error; the step is done as a rebuild
 
 // small device block of scalars
 enum Slot : int {
@@ -19,7 +21,8 @@ enum Slot : int {
     S_MINX = 6, S_MINY = 7, S_MAXX = 8, S_MAXY = 9, S_TOTAL = 10, S_BAD = 11, S_ALIVE = 12,
     S_WRAPS = 13, S_FAILPT = 14, S_DONE = 15, S_CERTPEND = 16, S_TICKET = 17, S_DNEXT = 18,
     S_DRUN = 19,  // warps running a move taken from the deferred list (kinetic launch)
-    S_NUM = 20
+    S_FAR = 20,   // moves beyond the displacement rule's bound (intake)
+    S_NUM = 21
 };
 
 // Instance tables (one instance for kdt_build; many for kdt_build_batch).  Every
@@ -35,6 +38,8 @@ struct Inst {
     int qx0, qy0, qshift, qF;
     const int *moff;  // per step: the moves of instance i are moff[i] .. moff[i+1]-1
     const int *tofs;  // triangle slots of instance i: tofs[i] .. tofs[i+1]-1
+    const int *order; // the order in which the kinetic kernel takes the partitions (the
+                      // step planner's, longest first), or null: index order
     int ninst;
 };
 
@@ -208,12 +213,23 @@ __device__ __forceinline__ const int3 *step_moves(const Dev &d, const int3 *move
     return reinterpret_cast<const int3 *>(((unsigned long long)hi << 32) | lo);
 }
 
+// An invalid move stops the step; it wins over the displacement rule's DEV_FAR, so
+// the host never rebuilds from an invalid move list.
+__device__ __forceinline__ void intake_fail(int *status, int code)
+{
+    if (atomicCAS(status, 0, code) == DEV_FAR) atomicCAS(status, DEV_FAR, code);
+}
+
 // Intake and per-partition bucketing in one pass: validate each move (A2), stamp the
 // moved id, remember the old position, and push the move onto the list of the
 // partition that owns the point (its cell at the start of the step, Section III
-// blocks): next[i] = previous head of the cell's list.
+// blocks): next[i] = previous head of the cell's list.  With far2 > 0 (the rebuild
+// rule of kdt_config.rebuild_displacement) a move whose squared displacement exceeds
+// far2 x its partition's d_local^2 (dloc2; INT64_MAX = unknown or an empty partition)
+// is counted, and the
+// step becomes a rebuild (DEV_FAR stops the kinetic kernel before it changes anything).
 __global__ void k_intake_link(Dev d, const int3 *moves, int m, Inst I, int bits, int *head, int *next,
-                              int2 *old_xy, int3 *gmoves)
+                              int2 *old_xy, int3 *gmoves, const unsigned long long *dloc2, double far2)
 {
     if (d.ctl) {
         m = __ldcg(d.ctl);
@@ -226,23 +242,32 @@ __global__ void k_intake_link(Dev d, const int3 *moves, int m, Inst I, int bits,
         int p0 = I.pofs[inst], ni = I.pofs[inst + 1] - p0;
         int3 mv = moves[i];
         if (mv.x < 0 || mv.x >= ni) {
-            atomicCAS(d.status, 0, DEV_ARG);
+            intake_fail(d.status, DEV_ARG);
             continue;
         }
         if (mv.y < 0 || mv.z < 0 || mv.y >= lim || mv.z >= lim) {
-            atomicCAS(d.status, 0, DEV_RANGE);
+            intake_fail(d.status, DEV_RANGE);
             continue;
         }
         int g = p0 + mv.x;
         int prev = atomicExch(d.pt_stamp + g, d.stamp);
         if (prev == d.stamp) {
-            atomicCAS(d.status, 0, DEV_DUP_ID);
+            intake_fail(d.status, DEV_DUP_ID);
             continue;
         }
         int2 o = d.xy[g];
         old_xy[i] = o;
         gmoves[i] = make_int3(g, mv.y, mv.z);
-        next[i] = atomicExch(head + partition_of(I, inst, bits, o), i);
+        const int cell = partition_of(I, inst, bits, o);
+        if (far2 > 0.0 && dloc2) {
+            const long long dx = (long long)mv.y - o.x, dy = (long long)mv.z - o.y;
+            const unsigned long long dl = dloc2[cell];
+            if (dl < (unsigned long long)LLONG_MAX && (double)(dx * dx + dy * dy) > far2 * (double)dl) {
+                atomicAdd(d.status + S_FAR, 1);
+                atomicCAS(d.status, 0, DEV_FAR);
+            }
+        }
+        next[i] = atomicExch(head + cell, i);
     }
 }
 
@@ -505,6 +530,7 @@ __global__ void __launch_bounds__(WPB * 32, 6) k_kinetic(Dev dp, const int3 *mov
                 }
                 c = t / wpp;
                 sub = t - c * wpp;
+                if (I.order) c = __ldcg(I.order + c);
                 kk = -1;
                 i = __shfl_sync(FULL, __ldcg(head + c), 0);
                 int inst = I.ninst > 1 ? csr_find(I.cofs, I.ninst + 1, c) : 0;

@@ -712,7 +712,9 @@ __device__ int move_point(Warp w, const Dev &d, int p, int2 q, int &s0, int &s1,
         if (learn) {
             int2 po = sh->lp[0][sh->I[0]];  // p's position before the move
             j0 = move_wedge(sh, k, po, q, w.lane);
-            if (j0 >= 0) feat = move_feature(sh, k, j0, po, q, w.lane);
+            // the features feed a training row, or the network when the planner did not
+            // evaluate it for this step
+            if (j0 >= 0 && (d.trace_x || !d.pguess)) feat = move_feature(sh, k, j0, po, q, w.lane);
             __syncwarp();
             for (int i = w.lane; i < k; i += 32) sh->I[i] = sh->L[i];
             __syncwarp();
@@ -878,7 +880,8 @@ __device__ int move_point(Warp w, const Dev &d, int p, int2 q, int &s0, int &s1,
             for (int off = 16; off; off >>= 1) lab = min(lab, __shfl_xor_sync(FULL, lab, off));
             slot = lab < MLP_BEYOND ? lab : MLP_BEYOND;
             if (d.mlp) {
-                int guess = mlp_argmax_slot(mlp_warp_forward(d.mlp, feat, w.lane), w.lane);
+                int guess = d.pguess ? (int)__ldcg(d.pguess + p)
+                                     : mlp_argmax_slot(mlp_warp_forward(d.mlp, feat, w.lane), w.lane);
                 cnt_add(w, C_PROP_MOVES, 1);
                 unsigned bm = __ballot_sync(FULL, guess < MLP_BEYOND && rank == guess && (r == 0 || r == 1));
                 if (bm) {

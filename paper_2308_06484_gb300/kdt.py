@@ -41,7 +41,8 @@ class Config(ctypes.Structure):
                 ("kinetic_warps", ctypes.c_int32), ("debug", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("points_per_partition", ctypes.c_int32),
                 ("warps_per_partition", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("variant", ctypes.c_int32), ("quadtree", ctypes.c_int32)]
+                ("variant", ctypes.c_int32), ("quadtree", ctypes.c_int32),
+                ("rebuild_displacement", ctypes.c_float), ("plan", ctypes.c_int32)]
 
 
 _STAT_FIELDS = ["steps", "moves", "rebuilds", "fallbacks", "kernel_launches", "flips", "retries",
@@ -56,7 +57,7 @@ _STAT_FIELDS2 = ["staged_to_global", "cycles_move", "cycles_move_max", "cycles_g
 _STAT_FIELDS3 = ["cycles_ear", "cycles_lawson", "cycles_certify", "proposal_moves", "proposal_hits",
                  "trace_rows", "tail_moves", "cycles_tail", "big_moves", "cycles_big", "drain_moves",
                  "span_tickets_ns", "span_drain_ns", "span_kernel_ns", "span_huge_ns", "span_drained_ns",
-                 "cycles_drained_max", "redeferred"]
+                 "cycles_drained_max", "redeferred", "far_rebuilds"]
 
 
 class Stats(ctypes.Structure):
@@ -67,7 +68,7 @@ class Stats(ctypes.Structure):
                 + [("step_graph_ms", ctypes.c_double), ("tuned_points_per_partition", ctypes.c_int64),
                    ("tuned_warps_per_partition", ctypes.c_int64)]
                 + [(f, ctypes.c_int64) for f in _STAT_FIELDS3]
-                + [("reserved", ctypes.c_int64 * 8)])
+                + [("reserved", ctypes.c_int64 * 7)])
 
 
 class DInfo(ctypes.Structure):
