@@ -136,6 +136,9 @@ typedef struct {
                               for all moves at once in the planner (instead of inside each
                               move); its predicted cavity size 2^out17 is added to the
                               estimate, and its guess is the locate's first candidate.      */
+    int32_t batch_build;   /* 1 (default): the instances of a batch are (re)built together,
+                              one set of launches for all of them; 0: one instance after
+                              another.  The triangulations are the same.                    */
 } kdt_config;
 
 /* Counters since creation (or kdt_reset_stats). */

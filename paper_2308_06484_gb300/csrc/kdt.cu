@@ -53,8 +53,8 @@ struct kdt {
     // instances
     int ninst = 0;
     std::vector<int> pofs, tofs, cofs, igrid;  // host copies
-    int *d_pofs = nullptr, *d_cofs = nullptr, *d_grid = nullptr, *d_moff = nullptr, *d_tofs = nullptr;
-    int *h_moff = nullptr;  // pinned
+    int *d_pofs = nullptr, *d_cofs = nullptr, *d_grid = nullptr, *d_tofs = nullptr;
+    int *d_moff = nullptr, *h_moff = nullptr;  // move offsets: ctl + 4 and hctl + 4
     int ncells = 0;          // partitions (all instances)
     int ppp = 256;           // points per partition in use
     int wpp = 1;             // warps per partition in use
@@ -82,6 +82,7 @@ struct kdt {
     int scan_tmp_cap = 0;
     // build / export temporaries (kept between calls)
     Buf key, bord, hist, hoff, exp_cnt, exp_off, exp_fill, exp_out;
+    Buf btab, blev;  // batched build: per-instance tables, per-level item offsets
     // d-calculation: neighbour lists, results, running minimum (per N)
     Buf nb_deg, nb_off, nb_list, dc_dist, dc_cmin, dc_scal;
     int64_t d2_run = INT64_MAX;
@@ -99,7 +100,8 @@ struct kdt {
     // quad-tree partitions (kdt_config.quadtree): leaf of every fine cell, the square
     int *qmap = nullptr;
     int qx0 = 0, qy0 = 0, qshift = 0, qF = 0, qleaves = 0, qleaf_side_lg = 0;
-    // graph-launched step: control words (moves, stamp, moves address) and the graph
+    // graph-launched step: control words (moves, stamp, moves address) followed by the
+    // move offsets of the instances, copied in one piece each step, and the graph
     int *ctl = nullptr;   // device
     int *hctl = nullptr;  // pinned host
     cudaStream_t cstream = nullptr;
@@ -450,13 +452,137 @@ int rebuild_instance(kdt *h, int i)
     return KDT_OK;
 }
 
+// Build the triangulations of every instance of a batch from the positions in h->xy in
+// one set of launches (the steps of rebuild_instance, each over all instances at once;
+// see the batched build kernels).  Returns an ABI code, or BATCH_TOO_WIDE (nothing
+// built) when the instances' Hilbert grids together exceed 2^31 cells.
+constexpr int BATCH_TOO_WIDE = 1;
+
+int rebuild_batch(kdt *h)
+{
+    const int ni = h->ninst, n = (int)h->n;
+    cudaStream_t st = h->stream;
+    Dev d = make_dev(h);
+    d.dirty_cap = 0;
+    if (d.retry_cap < 32768) d.retry_cap = 32768;
+    // per-instance tables: bbox (4), hk, hshift, hbase (ni + 1), third, tri_count
+    const size_t tab_ints = 4 * (size_t)ni + 5 * (size_t)ni + 1;
+    if (grow(h->btab, tab_ints * sizeof(int))) return KDT_ERR_CUDA;
+    int *bbox = (int *)h->btab.p, *hk = bbox + 4 * ni, *hsh = hk + ni, *third = hsh + ni, *tcount = third + ni;
+    unsigned *hbase = (unsigned *)(tcount + ni);
+    std::vector<int> hb(4 * (size_t)ni);
+    for (int i = 0; i < ni; ++i) {
+        hb[4 * i] = INT_MAX;
+        hb[4 * i + 1] = INT_MAX;
+        hb[4 * i + 2] = INT_MIN;
+        hb[4 * i + 3] = INT_MIN;
+    }
+    CK(cudaMemsetAsync(h->scal, 0, S_NUM * sizeof(int), st));
+    CK(cudaMemcpyAsync(bbox, hb.data(), hb.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(h->tv, 0, (size_t)h->cap * sizeof(int4), st));
+    CK(cudaMemsetAsync(h->tn, 0, (size_t)h->cap * sizeof(int4), st));
+    k_fill_int<<<thread_grid(h, n, 256), 256, 0, st>>>(h->pt_tri, n, -1);
+    k_range_batch<<<thread_grid(h, n, 256), 256, 0, st>>>(h->xy, n, h->d_pofs, ni, h->cfg.domain_bits,
+                                                          h->scal + S_STATUS, bbox);
+    h->stats.kernel_launches += 2;
+    CK(cudaMemcpyAsync(hb.data(), bbox, hb.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (sync_scalars(h)) return KDT_ERR_CUDA;
+    if (h->hscal[S_STATUS]) return dev_to_abi(h->hscal[S_STATUS]);
+    // Hilbert grids per instance (as rebuild_instance), laid one after another
+    std::vector<int> kk(ni), sh(ni), th(ni, INT_MAX);
+    std::vector<unsigned> base(ni + 1, 0);
+    int Kmax = 0;
+    for (int i = 0; i < ni; ++i) {
+        const int nn = h->pofs[i + 1] - h->pofs[i];
+        int k = 1;
+        while ((1ll << (2 * k)) < (long long)nn && k < 14) ++k;
+        long long span = (long long)std::max(hb[4 * i + 2] - hb[4 * i], hb[4 * i + 3] - hb[4 * i + 1]) + 1;
+        int shift = 0;
+        while ((span >> shift) > (1ll << k)) ++shift;
+        kk[i] = k;
+        sh[i] = shift;
+        if ((unsigned long long)base[i] + (1ull << (2 * k)) > 0x7fffffffull) return BATCH_TOO_WIDE;
+        base[i + 1] = base[i] + (1u << (2 * k));
+        int K = 0;
+        while ((1ll << (K + 1)) < (long long)nn) ++K;
+        Kmax = std::max(Kmax, K);
+    }
+    const size_t ncell = base[ni];
+    if (grow(h->key, (size_t)n * 4) || grow(h->bord, (size_t)n * 4) || grow(h->hist, ncell * 4) ||
+        grow(h->hoff, ncell * 4))
+        return KDT_ERR_CUDA;
+    unsigned *key = (unsigned *)h->key.p;
+    int *order = (int *)h->bord.p, *hist = (int *)h->hist.p, *hoff = (int *)h->hoff.p;
+    CK(cudaMemcpyAsync(hk, kk.data(), ni * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(hsh, sh.data(), ni * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(hbase, base.data(), (ni + 1) * sizeof(unsigned), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(third, th.data(), ni * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(hist, 0, ncell * 4, st));
+    k_hilbert_batch<<<thread_grid(h, n, 256), 256, 0, st>>>(h->xy, n, h->d_pofs, ni, bbox, hk, hsh, hbase, key, hist);
+    h->stats.kernel_launches++;
+    if (scan(h, hist, hoff, (int)ncell, h->scal + S_TOTAL, st)) return KDT_ERR_CUDA;
+    CK(cudaMemsetAsync(hist, 0, ncell * 4, st));
+    k_place_order<<<(n + 255) / 256, 256, 0, st>>>(n, key, hoff, hist, order, 0);
+    k_third_batch<<<thread_grid(h, n, 256), 256, 0, st>>>(h->xy, n, order, h->d_pofs, ni, third);
+    h->stats.kernel_launches += 2;
+    CK(cudaMemcpyAsync(th.data(), third, ni * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int i = 0; i < ni; ++i)
+        if (th[i] == INT_MAX) return KDT_ERR_DEGENERATE;
+    k_init_batch<<<thread_grid(h, ni, 128), 128, 0, st>>>(d, order, third, h->d_pofs, h->d_tofs, ni, tcount);
+    h->stats.kernel_launches++;
+    // the items of every level: instance i's positions (2j+1) * 2^level below n_i
+    std::vector<int> lv((size_t)(Kmax + 1) * (ni + 1), 0);
+    for (int lev = 0; lev <= Kmax; ++lev) {
+        int *o = lv.data() + (size_t)lev * (ni + 1);
+        for (int i = 0; i < ni; ++i) {
+            const long long nn = h->pofs[i + 1] - h->pofs[i];
+            const long long items = (nn - 1 + (1ll << lev)) >> (lev + 1);
+            o[i + 1] = o[i] + (int)std::max(0ll, items);
+        }
+    }
+    if (grow(h->blev, lv.size() * sizeof(int))) return KDT_ERR_CUDA;
+    CK(cudaMemcpyAsync(h->blev.p, lv.data(), lv.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    std::vector<long long> inserted(ni, 3);
+    for (int lev = Kmax; lev >= 0; --lev) {
+        const int *o = lv.data() + (size_t)lev * (ni + 1);
+        const int items = o[ni];
+        if (items <= 0) continue;
+        // about 16 triangles of room per concurrent insertion in every instance
+        long long conc = 0;
+        for (int i = 0; i < ni; ++i)
+            if (o[i + 1] > o[i]) conc += std::max(8ll, inserted[i] / 8);
+        if (h->cfg.build_warps > 0) conc = h->cfg.build_warps;
+        long long warps = std::min<long long>(items, conc);
+        k_insert_level_batch<<<warp_grid(h, warps, 64), WPB * 32, 0, st>>>(
+            d, order, lev, items, (const int *)h->blev.p + (size_t)lev * (ni + 1), h->d_pofs, h->d_tofs, ni, tcount);
+        h->stats.kernel_launches++;
+        CK(cudaGetLastError());
+        for (int i = 0; i < ni; ++i) inserted[i] += o[i + 1] - o[i];
+    }
+    std::vector<int> tc(ni);
+    CK(cudaMemcpyAsync(tc.data(), tcount, ni * sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (sync_scalars(h)) return KDT_ERR_CUDA;
+    if (h->hscal[S_STATUS]) return dev_to_abi(h->hscal[S_STATUS]);
+    for (int i = 0; i < ni; ++i)
+        if (tc[i] != h->tofs[i + 1]) return KDT_ERR_INTERNAL;
+    int ds = 0;
+    if (certify_and_repair(h, true, 0, h->cap, ni, &ds)) return KDT_ERR_CUDA;
+    if (ds) return dev_to_abi(ds);
+    return KDT_OK;
+}
+
 int rebuild_all(kdt *h)
 {
     h->built = false;
     h->stamp++;
-    for (int i = 0; i < h->ninst; ++i) {
-        int rc = rebuild_instance(h, i);
-        if (rc) return rc;
+    int rc = h->ninst > 1 && h->cfg.batch_build ? rebuild_batch(h) : BATCH_TOO_WIDE;
+    if (rc != BATCH_TOO_WIDE && rc != KDT_OK) return rc;
+    if (rc == BATCH_TOO_WIDE) {
+        for (int i = 0; i < h->ninst; ++i) {
+            const int ri = rebuild_instance(h, i);
+            if (ri) return ri;
+        }
     }
     h->built = true;
     h->stats.rebuilds++;
@@ -536,10 +662,12 @@ void free_state(kdt *h)
     h->gen++;
     void *ps[] = {h->xy, h->pt_tri, h->pt_stamp, h->tv, h->tn, h->viol, h->moves, h->gmoves, h->old_xy,
                   h->next, h->head, h->deferred, h->dirty, h->scan_tmp, h->d_pofs, h->d_cofs, h->d_grid,
-                  h->d_moff, h->d_tofs, h->qmap, h->dloc2, h->pcost, h->order, h->ohist, h->pguess};
+                  h->ctl, h->d_tofs, h->qmap, h->dloc2, h->pcost, h->order, h->ohist, h->pguess};
     for (void *p : ps)
         if (p) cudaFree(p);
-    if (h->h_moff) cudaFreeHost(h->h_moff);
+    if (h->hctl) cudaFreeHost(h->hctl);
+    h->ctl = nullptr;
+    h->hctl = nullptr;
     h->xy = nullptr; h->pt_tri = nullptr; h->pt_stamp = nullptr; h->tv = nullptr; h->tn = nullptr;
     h->viol = nullptr; h->moves = nullptr; h->gmoves = nullptr; h->old_xy = nullptr; h->next = nullptr;
     h->head = nullptr; h->deferred = nullptr; h->dirty = nullptr; h->scan_tmp = nullptr;
@@ -555,6 +683,7 @@ void free_state(kdt *h)
     h->qleaves = 0;
     h->mcap = 0; h->dirty_cap = 0; h->scan_tmp_cap = 0;
     Buf *bs[] = {&h->key, &h->bord, &h->hist, &h->hoff, &h->exp_cnt, &h->exp_off, &h->exp_fill, &h->exp_out,
+                 &h->btab, &h->blev,
                  &h->nb_deg, &h->nb_off, &h->nb_list, &h->dc_dist, &h->dc_cmin, &h->dc_scal};
     for (Buf *b : bs) free_buf(*b);
     h->n = 0;
@@ -579,10 +708,12 @@ int alloc_state(kdt *h, const int64_t *offs, int n_inst)
     h->cap = h->tofs[n_inst];
     h->built = false;
     if (dalloc(&h->xy, h->n) || dalloc(&h->pt_tri, h->n) || dalloc(&h->pt_stamp, h->n) || dalloc(&h->tv, h->cap) ||
-        dalloc(&h->tn, h->cap) || dalloc(&h->d_pofs, n_inst + 1) || dalloc(&h->d_moff, n_inst + 1) ||
+        dalloc(&h->tn, h->cap) || dalloc(&h->d_pofs, n_inst + 1) || dalloc(&h->ctl, 4 + n_inst + 1) ||
         dalloc(&h->d_tofs, n_inst + 1) || dalloc(&h->pguess, h->n) || dalloc(&h->ohist, 2 * PLAN_CLASSES))
         return KDT_ERR_CUDA;
-    if (cudaMallocHost(&h->h_moff, (n_inst + 1) * sizeof(int)) != cudaSuccess) return KDT_ERR_CUDA;
+    if (cudaMallocHost(&h->hctl, (4 + n_inst + 1) * sizeof(int)) != cudaSuccess) return KDT_ERR_CUDA;
+    h->d_moff = h->ctl + 4;
+    h->h_moff = h->hctl + 4;
     CK(cudaMemcpy(h->d_pofs, h->pofs.data(), (n_inst + 1) * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(h->d_tofs, h->tofs.data(), (n_inst + 1) * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMemsetAsync(h->pt_stamp, 0, h->n * sizeof(int), h->stream));
@@ -719,11 +850,10 @@ int enqueue_step(kdt *h, cudaStream_t st, const Dev &d, const int3 *mp, int mi, 
     Inst I = make_inst(h);
     // the step's control words and move offsets, from pinned host memory (a captured
     // copy reads them when the graph runs)
-    if (from_ctl) CK(cudaMemcpyAsync(h->ctl, h->hctl, 4 * sizeof(int), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(h->d_moff, h->h_moff, (h->ninst + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
-    CK(cudaMemsetAsync(h->scal, 0, S_NUM * sizeof(int), st));
-    CK(cudaMemsetAsync(h->head, 0xff, (size_t)h->ncells * sizeof(int), st));  // empty lists
-    CK(cudaMemsetAsync(h->deferred, 0xff, (size_t)h->mcap * sizeof(int4), st));  // empty entries (-1)
+    CK(cudaMemcpyAsync(h->ctl, h->hctl, (4 + h->ninst + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+    // scalars zero, partition lists empty, deferred entries -1: one kernel
+    k_step_clear<<<thread_grid(h, std::max<long long>(h->ncells, 4ll * h->mcap), 256), 256, 0, st>>>(
+        h->scal, S_NUM, h->head, h->ncells, h->deferred, h->mcap);
     k_intake_link<<<thread_grid(h, cap, 256), 256, 0, st>>>(d, mp, mi, I, h->cfg.domain_bits, h->head, h->next,
                                                             h->old_xy, h->gmoves, h->dloc2, far2(h));
     if (h->cfg.plan) {
@@ -858,7 +988,7 @@ int step_impl(kdt *h, const kdt_move *moves, const int64_t *moff, int64_t m)
     if (large) {
         // a step this large is cheaper as a rebuild (Abstract: "if the points move so
         // far, it's better to rebuild the triangulation")
-        CK(cudaMemcpyAsync(h->d_moff, h->h_moff, (h->ninst + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(h->ctl, h->hctl, (4 + h->ninst + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
         CK(cudaMemsetAsync(h->scal, 0, S_NUM * sizeof(int), st));
         CK(cudaMemsetAsync(h->head, 0xff, (size_t)h->ncells * sizeof(int), st));
         k_intake_link<<<thread_grid(h, mi, 256), 256, 0, st>>>(d, mp, mi, make_inst(h), h->cfg.domain_bits, h->head,
@@ -920,7 +1050,7 @@ int step_impl(kdt *h, const kdt_move *moves, const int64_t *moff, int64_t m)
         if (enqueue_step(h, st, d, mp, mi, false)) return KDT_ERR_CUDA;
         if (timed) CK(cudaEventRecord(h->ev3, st));
     }
-    h->stats.kernel_launches += h->cfg.plan ? 5 : 2;
+    h->stats.kernel_launches += h->cfg.plan ? 6 : 3;
     CK(cudaStreamSynchronize(st));
     if (h->hscal[S_CERTPEND] && !h->hscal[S_STATUS]) {
         // a long dirty list (global-path writes): certify it here, appending to the
@@ -1166,6 +1296,7 @@ int kdt_default_config(kdt_config *cfg)
     cfg->warps_per_partition = 0;
     cfg->autotune = 0;
     cfg->variant = 0;
+    cfg->batch_build = 1;
     return KDT_OK;
 }
 
@@ -1179,7 +1310,8 @@ int kdt_create(kdt **out, const kdt_config *cfg, int device, void *cuda_stream)
     if (c.domain_bits <= 0 || c.domain_bits > 28 || c.grid < 0 || c.grid > 4096 || c.retry_cap < 0 ||
         c.points_per_partition < 0 || c.warps_per_partition < 0 || c.warps_per_partition > 32 ||
         c.variant < 0 || c.variant > 2 || c.quadtree < 0 || c.quadtree > 1 ||
-        !(c.rebuild_displacement >= 0.0f) || c.rebuild_displacement > 1e9f || c.plan < 0 || c.plan > 2)
+        !(c.rebuild_displacement >= 0.0f) || c.rebuild_displacement > 1e9f || c.plan < 0 || c.plan > 2 ||
+        c.batch_build < 0 || c.batch_build > 1)
         return KDT_ERR_ARG;
     if (c.retry_cap == 0) c.retry_cap = 4096;
     if (cudaSetDevice(device) != cudaSuccess) return KDT_ERR_CUDA;
@@ -1191,8 +1323,7 @@ int kdt_create(kdt **out, const kdt_config *cfg, int device, void *cuda_stream)
     if (cudaMalloc(&h->scal, S_NUM * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&h->counters, C_SLOTS * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost(&h->hscal, S_NUM * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&h->ctl, 4 * sizeof(int)) != cudaSuccess ||
-        cudaMallocHost(&h->hctl, 4 * sizeof(int)) != cudaSuccess ||
+
         cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
         cudaEventCreate(&h->ev2) != cudaSuccess || cudaEventCreate(&h->ev3) != cudaSuccess) {
@@ -1219,8 +1350,6 @@ int kdt_destroy(kdt *h)
     if (h->mlp_part) cudaFree(h->mlp_part);
     if (h->big) cudaFree(h->big);
     if (h->hscal) cudaFreeHost(h->hscal);
-    if (h->ctl) cudaFree(h->ctl);
-    if (h->hctl) cudaFreeHost(h->hctl);
     if (h->cstream) cudaStreamDestroy(h->cstream);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);

@@ -213,6 +213,18 @@ __device__ __forceinline__ const int3 *step_moves(const Dev &d, const int3 *move
     return reinterpret_cast<const int3 *>(((unsigned long long)hi << 32) | lo);
 }
 
+// Start of a step: the scalars zero, every partition's move list empty, every deferred
+// entry -1 (one launch instead of three copies of memset).
+__global__ void k_step_clear(int *scal, int nscal, int *head, int ncells, int4 *deferred, int ndef)
+{
+    const int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(ncells, ndef); i += stride) {
+        if (i < nscal) scal[i] = 0;
+        if (i < ncells) head[i] = -1;
+        if (i < ndef) deferred[i] = make_int4(-1, -1, -1, -1);
+    }
+}
+
 // An invalid move stops the step; it wins over the displacement rule's DEV_FAR, so
 // the host never rebuilds from an invalid move list.
 __device__ __forceinline__ void intake_fail(int *status, int code)
@@ -897,6 +909,141 @@ __global__ void __launch_bounds__(WPB * 32) k_insert_level(Dev dp, const int *or
         if (w.lane == 0) s = atomicAdd(tri_count, 2);
         s = __shfl_sync(FULL, s, 0);
         if (s + 1 >= slot_end) {
+            set_status(d, DEV_INTERNAL);
+            break;
+        }
+        int2 q = d.xy[v];
+        int rc = insert_staged(w, d, v, q, start, s, s + 1, false);
+        if (rc == INS_GLOBAL) rc = insert_point(w, d, v, q, start, s, s + 1, false);
+        if (rc) {
+            if (rc > 0) set_status(d, rc);
+            break;
+        }
+    }
+    flush_counters(w, d);
+}
+
+// ------------------------------------------------------------------ batched build
+//
+// All instances of a batch built by one set of launches: per-instance bounding boxes,
+// Hilbert keys offset by instance (so one counting sort orders every instance's points
+// inside its own range of `order`), per-instance first triangles, and one launch per
+// insertion level whose items are every instance's points of that level, back to back.
+
+// bounding box of every instance (bbox[4 i .. 4 i + 3]) and the range check
+__global__ void k_range_batch(const int2 *xy, int n, const int *pofs, int ninst, int bits, int *status, int *bbox)
+{
+    const long long lim = 1ll << bits;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int2 p = xy[i];
+        if (p.x < 0 || p.y < 0 || p.x >= lim || p.y >= lim) atomicCAS(status, 0, DEV_RANGE);
+        int *b = bbox + 4 * csr_find(pofs, ninst + 1, i);
+        atomicMin(b + 0, p.x);
+        atomicMin(b + 1, p.y);
+        atomicMax(b + 2, p.x);
+        atomicMax(b + 3, p.y);
+    }
+}
+
+// Hilbert key of every point over its instance's grid (2^hk[i] cells a side, cell side
+// 2^hshift[i] from the instance's minimum corner), offset by hbase[i] (the instances'
+// grids one after another)
+__global__ void k_hilbert_batch(const int2 *xy, int n, const int *pofs, int ninst, const int *bbox, const int *hk,
+                                const int *hshift, const unsigned *hbase, unsigned *key, int *hist)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int inst = csr_find(pofs, ninst + 1, i);
+        const int k = hk[inst], shift = hshift[inst];
+        const int2 p = xy[i];
+        unsigned cx = (unsigned)(p.x - bbox[4 * inst]) >> shift, cy = (unsigned)(p.y - bbox[4 * inst + 1]) >> shift;
+        const unsigned lim = (1u << k) - 1;
+        cx = min(cx, lim);
+        cy = min(cy, lim);
+        const unsigned h = hbase[inst] + hilbert_d(k, cx, cy);
+        key[i] = h;
+        atomicAdd(hist + h, 1);
+    }
+}
+
+// per instance: the first position j >= 2 of its order whose point is not collinear
+// with its first two (third[i], instance-local)
+__global__ void k_third_batch(const int2 *xy, int n, const int *order, const int *pofs, int ninst, int *third)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const int inst = csr_find(pofs, ninst + 1, j);
+        const int p0 = pofs[inst];
+        if (j - p0 < 2) continue;
+        if (orient2d(xy[order[p0]], xy[order[p0 + 1]], xy[order[j]]) != 0) atomicMin(third + inst, j - p0);
+    }
+}
+
+// per instance: its first triangle and three ghosts at its first slots (as k_init)
+__global__ void k_init_batch(Dev d, const int *order, const int *third, const int *pofs, const int *tofs, int ninst,
+                             int *tri_count)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ninst; i += gridDim.x * blockDim.x) {
+        const int p0 = pofs[i], s0 = tofs[i];
+        int a = order[p0], b = order[p0 + 1], c = order[p0 + third[i]];
+        if (orient2d(d.xy[a], d.xy[b], d.xy[c]) < 0) {
+            int t = b;
+            b = c;
+            c = t;
+        }
+        const int G = KDT_GHOST;
+        const int t0 = s0, t1 = s0 + 1, t2 = s0 + 2, t3 = s0 + 3;
+        d.tv[t0] = make_int4(a, b, c, ALIVE);
+        d.tn[t0] = make_int4((t1 << 2) | 2, (t2 << 2) | 2, (t3 << 2) | 2, 0);
+        d.tv[t1] = make_int4(c, b, G, ALIVE);
+        d.tn[t1] = make_int4((t3 << 2) | 1, (t2 << 2) | 0, (t0 << 2) | 0, 0);
+        d.tv[t2] = make_int4(a, c, G, ALIVE);
+        d.tn[t2] = make_int4((t1 << 2) | 1, (t3 << 2) | 0, (t0 << 2) | 1, 0);
+        d.tv[t3] = make_int4(b, a, G, ALIVE);
+        d.tn[t3] = make_int4((t2 << 2) | 1, (t1 << 2) | 0, (t0 << 2) | 2, 0);
+        d.pt_tri[a] = t0;
+        d.pt_tri[b] = t0;
+        d.pt_tri[c] = t0;
+        tri_count[i] = s0 + 4;
+    }
+}
+
+// One insertion level of every instance: items lvoff[i] .. lvoff[i+1]-1 are instance
+// i's points at its sorted positions (2j+1) * 2^level (as k_insert_level); each warp
+// takes a contiguous run of the items, so its insertions are far apart along their
+// instance's Hilbert curve.
+__global__ void __launch_bounds__(WPB * 32) k_insert_level_batch(Dev dp, const int *order, int level, int items,
+                                                                 const int *lvoff, const int *pofs, const int *tofs,
+                                                                 int ninst, int *tri_count)
+{
+    KD_BLOCK_DEV(dp);
+    __shared__ WarpShared shs[WPB];
+    int wib = threadIdx.x >> 5;
+    int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+    int nw = gridDim.x * (blockDim.x >> 5);
+    Warp w = make_warp(&shs[wib], gw + 1, gw * 7 + level * 1315423911u, d);
+    const int per = (items + nw - 1) / nw;
+    const int gend = min(items, (gw + 1) * per);
+    int cur = -1, p0 = 0, nloc = 0;
+    for (int g = gw * per; g < gend; ++g) {
+        if (read_status(d)) break;
+        const int inst = csr_find(lvoff, ninst + 1, g);
+        if (inst != cur) {
+            cur = inst;
+            p0 = pofs[inst];
+            nloc = pofs[inst + 1] - p0;
+            set_instance(w, p0, nloc);
+        }
+        const int j = g - lvoff[inst];
+        long long i = ((long long)(2 * j + 1)) << level;
+        if (i >= nloc) continue;
+        int v = order[p0 + i];
+        if (__shfl_sync(FULL, __ldcg(d.pt_tri + v), 0) >= 0) continue;  // one of the first three
+        int parent = order[p0 + i - (1ll << level)];
+        int start = __shfl_sync(FULL, __ldcg(d.pt_tri + parent), 0);
+        if (start < 0) start = tofs[inst];
+        int s = 0;
+        if (w.lane == 0) s = atomicAdd(tri_count + inst, 2);
+        s = __shfl_sync(FULL, s, 0);
+        if (s + 1 >= tofs[inst + 1]) {
             set_status(d, DEV_INTERNAL);
             break;
         }

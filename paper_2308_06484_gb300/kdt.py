@@ -42,7 +42,8 @@ class Config(ctypes.Structure):
                 ("use_graph", ctypes.c_int32), ("points_per_partition", ctypes.c_int32),
                 ("warps_per_partition", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("variant", ctypes.c_int32), ("quadtree", ctypes.c_int32),
-                ("rebuild_displacement", ctypes.c_float), ("plan", ctypes.c_int32)]
+                ("rebuild_displacement", ctypes.c_float), ("plan", ctypes.c_int32),
+                ("batch_build", ctypes.c_int32)]
 
 
 _STAT_FIELDS = ["steps", "moves", "rebuilds", "fallbacks", "kernel_launches", "flips", "retries",

@@ -107,3 +107,39 @@ def test_batch_full_size_sampled():
     for i in sample:
         assert_same(t.export_triangles_inst(i), ws[i].positions, "step instance %d" % i)
     assert t.stats()["fallbacks"] == 0
+
+
+def test_batched_build_equals_one_instance_at_a_time():
+    """kdt_config.batch_build: every instance built in one set of launches gives the same
+    triangulations as building them one after another, and as the oracle; including
+    3-point instances, an instance whose first points are collinear, a lattice and
+    repeated rebuilds after steps."""
+    import torch
+    from paper_2308_06484_gb300 import kdt
+    ws = _batch(20, 3, 5000, seed=71)
+    rng = np.random.default_rng(72)
+    line = np.stack([np.arange(40) * 3 + 5, np.full(40, 77)], axis=1)
+    line = np.concatenate([line, [[60, 500], [61, 9]]]).astype(np.int32)  # collinear first, then two off the line
+    g = np.arange(12)
+    lat = (np.stack(np.meshgrid(g, g), -1).reshape(-1, 2) * 64 + 1000).astype(np.int32)
+    xys = [w.positions for w in ws] + [line, lat, np.array([[1, 1], [9, 2], [4, 8]], dtype=np.int32)]
+    ts = {}
+    for bb in (0, 1):
+        t = kdt.Triangulation(kdt.default_config(domain_bits=20, batch_build=bb))
+        t.build_batch(xys)
+        ts[bb] = t
+    for i, xy in enumerate(xys):
+        a = ts[1].export_triangles_inst(i)
+        assert np.array_equal(a, ts[0].export_triangles_inst(i)), i
+        assert_same(a, xy, "batched build instance %d" % i)
+    assert ts[1].verify() == 0
+    for s in range(3):
+        mv, offs = _step_moves(ws)
+        offs = np.concatenate([offs, [offs[-1]] * 3])
+        ts[1].step_batch(torch.from_numpy(mv).cuda(), offs)
+        ts[1].rebuild()
+    for i, w in enumerate(ws):
+        assert_same(ts[1].export_triangles_inst(i), w.positions, "rebuilt instance %d" % i)
+    assert ts[1].verify() == 0
+    for t in ts.values():
+        t.close()
