@@ -111,8 +111,15 @@ typedef struct {
                               low-x low-y, high-x low-y, low-x high-y, high-x high-y).  Built
                               by kdt_build from the initial positions; a moved point's block
                               is the leaf holding its current position (clamped into the
-                              square).  Single-instance handles only (kdt_build_batch returns
-                              KDT_ERR_ARG).  Scheduling only: the triangulation is the same. */
+                              square).  2: as 1, and the division is made again at the start
+                              of every step from the current positions (Fig. 4 runs the
+                              division inside its time loop), on the GPU, within the square
+                              of the build (positions outside it are clamped into it); the
+                              number of partitions then changes from step to step
+                              (kdt_num_cells gives the last step's), and the displacement rule
+                              below is inactive.  Single-instance handles only
+                              (kdt_build_batch returns KDT_ERR_ARG).  Scheduling only: the
+                              triangulation is the same.                                     */
     float rebuild_displacement; /* f; 0 = off (default).  The rebuild rule of the paper's
                               abstract (points that move far are cheaper to triangulate
                               again) with Section III's d as the yardstick: before a step

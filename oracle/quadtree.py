@@ -31,10 +31,17 @@ def layout(xy):
     return x0, y0, lg, min(MAX_DEPTH, lg)
 
 
-def leaves(xy, T):
-    """Leaf squares as (x, y, side) in their depth-first order (the block ids)."""
+def leaves(xy, T, lay=None):
+    """Leaf squares as (x, y, side) in their depth-first order (the block ids).  With
+    `lay` (a layout from an earlier division) the division is made again inside that
+    square, positions outside it clamped into it (a division repeated during the time
+    loop keeps the square of the build)."""
     P = np.asarray(xy, dtype=np.int64)
-    x0, y0, lg, D = layout(P)
+    if lay is None:
+        x0, y0, lg, D = layout(P)
+    else:
+        x0, y0, lg, D = lay
+        P = np.stack([np.clip(P[:, 0], x0, x0 + (1 << lg) - 1), np.clip(P[:, 1], y0, y0 + (1 << lg) - 1)], axis=1)
     out = []
 
     def divide(x, y, side, idx, depth):

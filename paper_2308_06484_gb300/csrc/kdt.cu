@@ -56,6 +56,8 @@ struct kdt {
     int *d_pofs = nullptr, *d_cofs = nullptr, *d_grid = nullptr, *d_tofs = nullptr;
     int *d_moff = nullptr, *h_moff = nullptr;  // move offsets: ctl + 4 and hctl + 4
     int ncells = 0;          // partitions (all instances)
+    int ncells_cap = 0;      // entries of the per-partition arrays (more than ncells when the
+                             // quad-tree is re-divided at every step: one per fine cell)
     int ppp = 256;           // points per partition in use
     int wpp = 1;             // warps per partition in use
     // state
@@ -99,7 +101,12 @@ struct kdt {
     signed char *pguess = nullptr;
     // quad-tree partitions (kdt_config.quadtree): leaf of every fine cell, the square
     int *qmap = nullptr;
-    int qx0 = 0, qy0 = 0, qshift = 0, qF = 0, qleaves = 0, qleaf_side_lg = 0;
+    int qx0 = 0, qy0 = 0, qshift = 0, qF = 0, qleaves = 0, qleaf_side_lg = 0, qD = 0;
+    // re-divided at every step (kdt_config.quadtree = 2): points per fine cell, the count
+    // pyramid above it, and per fine cell (Morton order) the leaf-start flags, their
+    // prefix counts and the leaf levels
+    int *qhist = nullptr, *qpyr = nullptr, *qflag = nullptr, *qpre = nullptr;
+    unsigned char *qlev = nullptr;
     // graph-launched step: control words (moves, stamp, moves address) followed by the
     // move offsets of the instances, copied in one piece each step, and the graph
     int *ctl = nullptr;   // device
@@ -263,6 +270,8 @@ Inst make_inst(kdt *h)
     I.qshift = h->qshift;
     I.qF = h->qF;
     I.order = h->cfg.plan ? h->order : nullptr;
+    I.qhist = h->qhist;
+    I.ncells_dyn = h->qhist ? h->scal + S_NCELLS : nullptr;
     return I;
 }
 
@@ -635,10 +644,13 @@ int set_partitions(kdt *h, int ppp)
     if (cells > INT_MAX / 8) return KDT_ERR_ARG;
     h->cofs[h->ninst] = (int)cells;
     h->ncells = (int)cells;
-    if (dalloc(&h->head, (size_t)cells) || dalloc(&h->d_cofs, h->ninst + 1) || dalloc(&h->d_grid, h->ninst) ||
-        dalloc(&h->dloc2, (size_t)cells) || dalloc(&h->pcost, (size_t)cells) || dalloc(&h->order, (size_t)cells))
+    // a quad-tree re-divided at every step has at most one leaf per fine cell
+    const long long cap = h->qhist ? (long long)h->qF * h->qF : cells;
+    h->ncells_cap = (int)cap;
+    if (dalloc(&h->head, (size_t)cap) || dalloc(&h->d_cofs, h->ninst + 1) || dalloc(&h->d_grid, h->ninst) ||
+        dalloc(&h->dloc2, (size_t)cap) || dalloc(&h->pcost, (size_t)cap) || dalloc(&h->order, (size_t)cap))
         return KDT_ERR_CUDA;
-    k_fill_u64<<<thread_grid(h, cells, 256), 256, 0, h->stream>>>(h->dloc2, cells, (unsigned long long)INT64_MAX);
+    k_fill_u64<<<thread_grid(h, cap, 256), 256, 0, h->stream>>>(h->dloc2, cap, (unsigned long long)INT64_MAX);
     h->stats.kernel_launches++;
     h->dloc_valid = false;
     CK(cudaMemcpy(h->d_cofs, h->cofs.data(), (h->ninst + 1) * sizeof(int), cudaMemcpyHostToDevice));
@@ -662,7 +674,8 @@ void free_state(kdt *h)
     h->gen++;
     void *ps[] = {h->xy, h->pt_tri, h->pt_stamp, h->tv, h->tn, h->viol, h->moves, h->gmoves, h->old_xy,
                   h->next, h->head, h->deferred, h->dirty, h->scan_tmp, h->d_pofs, h->d_cofs, h->d_grid,
-                  h->ctl, h->d_tofs, h->qmap, h->dloc2, h->pcost, h->order, h->ohist, h->pguess};
+                  h->ctl, h->d_tofs, h->qmap, h->dloc2, h->pcost, h->order, h->ohist, h->pguess,
+                  h->qhist, h->qpyr, h->qflag, h->qpre, h->qlev};
     for (void *p : ps)
         if (p) cudaFree(p);
     if (h->hctl) cudaFreeHost(h->hctl);
@@ -674,6 +687,11 @@ void free_state(kdt *h)
     h->d_pofs = nullptr; h->d_cofs = nullptr; h->d_grid = nullptr; h->d_moff = nullptr; h->h_moff = nullptr;
     h->d_tofs = nullptr;
     h->qmap = nullptr;
+    h->qhist = nullptr;
+    h->qpyr = nullptr;
+    h->qflag = nullptr;
+    h->qpre = nullptr;
+    h->qlev = nullptr;
     h->dloc2 = nullptr;
     h->dloc_valid = false;
     h->pcost = nullptr;
@@ -841,7 +859,7 @@ int d_values_impl(kdt *h, int N, int64_t *dist2, int64_t *cell_min2, kdt_dinfo *
 double far2(const kdt *h)
 {
     const double f = h->cfg.rebuild_displacement;
-    return f > 0.0 ? f * f : 0.0;
+    return f > 0.0 && !h->qhist ? f * f : 0.0;  // (partitions that change every step keep no d_local)
 }
 
 int enqueue_step(kdt *h, cudaStream_t st, const Dev &d, const int3 *mp, int mi, bool from_ctl)
@@ -852,14 +870,28 @@ int enqueue_step(kdt *h, cudaStream_t st, const Dev &d, const int3 *mp, int mi, 
     // copy reads them when the graph runs)
     CK(cudaMemcpyAsync(h->ctl, h->hctl, (4 + h->ninst + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
     // scalars zero, partition lists empty, deferred entries -1: one kernel
-    k_step_clear<<<thread_grid(h, std::max<long long>(h->ncells, 4ll * h->mcap), 256), 256, 0, st>>>(
-        h->scal, S_NUM, h->head, h->ncells, h->deferred, h->mcap);
+    k_step_clear<<<thread_grid(h, std::max<long long>(h->ncells_cap, 4ll * h->mcap), 256), 256, 0, st>>>(
+        h->scal, S_NUM, h->head, h->ncells_cap, h->deferred, h->mcap);
+    if (h->qhist) {
+        // Fig. 4's Quad-treeDvision at the start of the step, from the points per fine
+        // cell the intakes keep current: count pyramid, every fine cell's leaf, leaves
+        // numbered depth-first (a scan in Morton order); their number goes to S_NCELLS
+        const int D = h->qD, F = 1 << D;
+        for (int l = D - 1; l >= 0; --l) {
+            const int *src = l == D - 1 ? h->qhist : h->qpyr + ((1 << (2 * (l + 1))) - 1) / 3;
+            k_qt_level<<<thread_grid(h, 1ll << (2 * l), 256), 256, 0, st>>>(src, h->qpyr + ((1 << (2 * l)) - 1) / 3,
+                                                                         1 << l);
+        }
+        k_qt_leaf<<<thread_grid(h, (long long)F * F, 256), 256, 0, st>>>(h->qpyr, D, h->ppp, h->qflag, h->qlev);
+        if (scan(h, h->qflag, h->qpre, F * F, h->scal + S_NCELLS, st)) return KDT_ERR_CUDA;
+        k_qt_map<<<thread_grid(h, (long long)F * F, 256), 256, 0, st>>>(h->qpre, h->qlev, D, h->qmap);
+    }
     k_intake_link<<<thread_grid(h, cap, 256), 256, 0, st>>>(d, mp, mi, I, h->cfg.domain_bits, h->head, h->next,
                                                             h->old_xy, h->gmoves, h->dloc2, far2(h));
     if (h->cfg.plan) {
         // the planner: estimated work per partition (and the network's guesses), then
         // the partitions in order of decreasing estimate
-        CK(cudaMemsetAsync(h->pcost, 0, (size_t)h->ncells * sizeof(float), st));
+        CK(cudaMemsetAsync(h->pcost, 0, (size_t)h->ncells_cap * sizeof(float), st));
         CK(cudaMemsetAsync(h->ohist, 0, 2 * PLAN_CLASSES * sizeof(int), st));
         const bool net = h->prop_on && h->cfg.plan == 2;
         int pblocks = (int)std::min<long long>(((long long)cap + PLAN_THREADS - 1) / PLAN_THREADS,
@@ -867,8 +899,8 @@ int enqueue_step(kdt *h, cudaStream_t st, const Dev &d, const int3 *mp, int mi, 
         k_plan<<<std::max(pblocks, 1), PLAN_THREADS, 0, st>>>(d, h->gmoves, h->old_xy, mi, I, h->cfg.domain_bits,
                                                              net ? h->mlp_w : nullptr, net ? h->pguess : nullptr,
                                                              h->pcost);
-        k_order<<<thread_grid(h, h->ncells, 256), 256, 0, st>>>(h->pcost, h->ncells, h->ohist, h->order, 0);
-        k_order<<<thread_grid(h, h->ncells, 256), 256, 0, st>>>(h->pcost, h->ncells, h->ohist, h->order, 1);
+        k_order<<<thread_grid(h, h->ncells_cap, 256), 256, 0, st>>>(h->pcost, h->ncells_cap, h->ohist, h->order, 0);
+        k_order<<<thread_grid(h, h->ncells_cap, 256), 256, 0, st>>>(h->pcost, h->ncells_cap, h->ohist, h->order, 1);
     }
     // inside a capture an event record must be an external node to keep its timestamp
     unsigned evflags = from_ctl ? cudaEventRecordExternal : cudaEventRecordDefault;
@@ -880,6 +912,7 @@ int enqueue_step(kdt *h, cudaStream_t st, const Dev &d, const int3 *mp, int mi, 
     k_kinetic<<<kblocks, kthreads, 0, st>>>(dk, h->gmoves, h->head, h->next, I, h->ncells, h->wpp, h->deferred,
                                             h->scal + S_DEFER, h->mcap, h->viol, h->viol_cap);
     if (h->cfg.timing) CK(cudaEventRecordWithFlags(h->ev1, st, evflags));
+    k_certify_step<<<thread_grid(h, 4096, 256), 256, 0, st>>>(d, h->viol, h->scal + S_VIOL, h->viol_cap);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->hscal, h->scal, S_NUM * sizeof(int), cudaMemcpyDeviceToHost, st));
     return 0;
@@ -965,7 +998,23 @@ int autotune_after(kdt *h, float ms, int64_t m)
 
 // One step of every instance: moves (instance-local ids, host or device) with CSR
 // offsets moff (host, ninst + 1 entries).
+int step_core(kdt *h, const kdt_move *moves, const int64_t *moff, int64_t m);
+int qt_recount(kdt *h);
+
+// One step; with the quad-tree re-divided at every step, a step that did not finish on the
+// kinetic path (an error, a rebuild) has the points per fine cell counted again.
 int step_impl(kdt *h, const kdt_move *moves, const int64_t *moff, int64_t m)
+{
+    const int64_t rebuilds = h->stats.rebuilds;
+    const int rc = step_core(h, moves, moff, m);
+    if (h->qhist && (rc != KDT_OK || h->stats.rebuilds != rebuilds)) {
+        const int rr = qt_recount(h);
+        if (rr) return rr;
+    }
+    return rc;
+}
+
+int step_core(kdt *h, const kdt_move *moves, const int64_t *moff, int64_t m)
 {
     if (m == 0) return KDT_OK;
     if (m > h->n) return KDT_ERR_DUPLICATE;  // some id must repeat (or be out of range)
@@ -990,7 +1039,7 @@ int step_impl(kdt *h, const kdt_move *moves, const int64_t *moff, int64_t m)
         // far, it's better to rebuild the triangulation")
         CK(cudaMemcpyAsync(h->ctl, h->hctl, (4 + h->ninst + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
         CK(cudaMemsetAsync(h->scal, 0, S_NUM * sizeof(int), st));
-        CK(cudaMemsetAsync(h->head, 0xff, (size_t)h->ncells * sizeof(int), st));
+        CK(cudaMemsetAsync(h->head, 0xff, (size_t)h->ncells_cap * sizeof(int), st));
         k_intake_link<<<thread_grid(h, mi, 256), 256, 0, st>>>(d, mp, mi, make_inst(h), h->cfg.domain_bits, h->head,
                                                                h->next, h->old_xy, h->gmoves, nullptr, 0.0);
         h->stats.kernel_launches++;
@@ -1011,6 +1060,13 @@ int step_impl(kdt *h, const kdt_move *moves, const int64_t *moff, int64_t m)
     if (rc) return rc;
     rc = ensure_big(h);
     if (rc) return rc;
+    if (h->qhist && h->scan_tmp_cap < (h->qF * h->qF + SCAN_TILE - 1) / SCAN_TILE + 1) {
+        // the step graph scans every fine cell: its scan scratch must exist before capture
+        const int c = (h->qF * h->qF + SCAN_TILE - 1) / SCAN_TILE + 1024;
+        if (dalloc(&h->scan_tmp, (size_t)c)) return KDT_ERR_CUDA;
+        h->scan_tmp_cap = c;
+        h->gen++;
+    }
     if (far2(h) > 0.0 && !h->dloc_valid) {
         // the displacement rule needs d_local: compute it (a failure, e.g. an instance
         // with too few points, leaves the rule inactive for this step)
@@ -1050,16 +1106,9 @@ int step_impl(kdt *h, const kdt_move *moves, const int64_t *moff, int64_t m)
         if (enqueue_step(h, st, d, mp, mi, false)) return KDT_ERR_CUDA;
         if (timed) CK(cudaEventRecord(h->ev3, st));
     }
-    h->stats.kernel_launches += h->cfg.plan ? 6 : 3;
+    h->stats.kernel_launches += (h->cfg.plan ? 7 : 4) + (h->qhist ? h->qD + 5 : 0);
     CK(cudaStreamSynchronize(st));
-    if (h->hscal[S_CERTPEND] && !h->hscal[S_STATUS]) {
-        // a long dirty list (global-path writes): certify it here, appending to the
-        // violations the kinetic kernel already recorded
-        k_certify<<<thread_grid(h, h->hscal[S_DIRTY], 256), 256, 0, st>>>(d, 0, h->viol, h->scal + S_VIOL,
-                                                                          h->viol_cap);
-        h->stats.kernel_launches++;
-        if (sync_scalars(h)) return KDT_ERR_CUDA;
-    }
+    if (h->qhist) h->ncells = h->qleaves = h->hscal[S_NCELLS];
     if (timed) {
         float ms = 0.f;
         if (h->cfg.timing && cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) {
@@ -1228,7 +1277,31 @@ int build_quadtree(kdt *h)
     h->qF = F;
     h->qleaves = leaves;
     h->qleaf_side_lg = lg - largest;  // log2 of the side of the largest leaf
+    h->qD = D;
+    if (h->cfg.quadtree == 2) {
+        // re-divided at every step: keep the points per fine cell, and the scratch of the
+        // division on the GPU
+        const size_t f2 = (size_t)F * F;
+        if (dalloc(&h->qhist, f2) || dalloc(&h->qpyr, std::max<size_t>(1, (f2 - 1) / 3)) ||
+            dalloc(&h->qflag, f2) || dalloc(&h->qpre, f2) || dalloc(&h->qlev, f2))
+            return KDT_ERR_CUDA;
+        CK(cudaMemcpyAsync(h->qhist, h->hist.p, f2 * sizeof(int), cudaMemcpyDeviceToDevice, st));
+        CK(cudaStreamSynchronize(st));
+    }
     return set_partitions(h, h->ppp);
+}
+
+// Points per fine cell of the re-divided quad-tree counted again from the positions
+// (after a step that did not finish on the kinetic path).
+int qt_recount(kdt *h)
+{
+    const size_t f2 = (size_t)h->qF * h->qF;
+    CK(cudaMemsetAsync(h->qhist, 0, f2 * sizeof(int), h->stream));
+    k_qt_hist<<<thread_grid(h, h->n, 256), 256, 0, h->stream>>>(h->xy, (int)h->n, h->qx0, h->qy0, h->qshift, h->qF,
+                                                               h->qhist);
+    h->stats.kernel_launches++;
+    CK(cudaStreamSynchronize(h->stream));
+    return 0;
 }
 
 int build_impl(kdt *h, const int32_t *xy, const int64_t *offs, int n_inst)
@@ -1309,7 +1382,7 @@ int kdt_create(kdt **out, const kdt_config *cfg, int device, void *cuda_stream)
     else kdt_default_config(&c);
     if (c.domain_bits <= 0 || c.domain_bits > 28 || c.grid < 0 || c.grid > 4096 || c.retry_cap < 0 ||
         c.points_per_partition < 0 || c.warps_per_partition < 0 || c.warps_per_partition > 32 ||
-        c.variant < 0 || c.variant > 2 || c.quadtree < 0 || c.quadtree > 1 ||
+        c.variant < 0 || c.variant > 2 || c.quadtree < 0 || c.quadtree > 2 ||
         !(c.rebuild_displacement >= 0.0f) || c.rebuild_displacement > 1e9f || c.plan < 0 || c.plan > 2 ||
         c.batch_build < 0 || c.batch_build > 1)
         return KDT_ERR_ARG;

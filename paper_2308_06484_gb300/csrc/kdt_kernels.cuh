@@ -22,7 +22,8 @@ enum Slot : int {
     S_WRAPS = 13, S_FAILPT = 14, S_DONE = 15, S_CERTPEND = 16, S_TICKET = 17, S_DNEXT = 18,
     S_DRUN = 19,  // warps running a move taken from the deferred list (kinetic launch)
     S_FAR = 20,   // moves beyond the displacement rule's bound (intake)
-    S_NUM = 21
+    S_NCELLS = 21, // partitions of this step (quad-tree re-divided at every step)
+    S_NUM = 22
 };
 
 // Instance tables (one instance for kdt_build; many for kdt_build_batch).  Every
@@ -40,6 +41,9 @@ struct Inst {
     const int *tofs;  // triangle slots of instance i: tofs[i] .. tofs[i+1]-1
     const int *order; // the order in which the kinetic kernel takes the partitions (the
                       // step planner's, longest first), or null: index order
+    int *qhist;       // quad-tree re-divided at every step: points per fine cell, kept
+                      // current by the intake; null otherwise
+    const int *ncells_dyn;  // ... and this step's number of leaves (else the launch's count)
     int ninst;
 };
 
@@ -58,7 +62,69 @@ __device__ __forceinline__ int partition_of(const Inst &I, int inst, int bits, i
     return I.cofs[inst] + cy * G + cx;
 }
 
-// points per fine cell of the quad-tree's square (the division is made on the host)
+// fine cell (row-major) of a position in the quad-tree's square, clamped into it
+__device__ __forceinline__ int qt_fine(const Inst &I, int2 o)
+{
+    int fx = (int)max(0ll, min((long long)I.qF - 1, ((long long)o.x - I.qx0) >> I.qshift));
+    int fy = (int)max(0ll, min((long long)I.qF - 1, ((long long)o.y - I.qy0) >> I.qshift));
+    return fy * I.qF + fx;
+}
+
+// ---- the quad-tree re-divided at every step (kdt_config.quadtree = 2), on the GPU.
+// Depth-first order of the leaves with children (low x, low y), (high x, low y), (low x,
+// high y), (high x, high y) is the order of their first fine cell's Morton index with x
+// in the low bit of every two-bit digit.
+__device__ __forceinline__ unsigned qt_morton(unsigned x, unsigned y)
+{
+    unsigned m = 0;
+    for (int b = 0; b < 16; ++b) m |= (((x >> b) & 1u) << (2 * b)) | (((y >> b) & 1u) << (2 * b + 1));
+    return m;
+}
+
+// one level of the count pyramid: dst (w x w, row-major) from src (2w x 2w)
+__global__ void k_qt_level(const int *src, int *dst, int w)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < w * w; i += gridDim.x * blockDim.x) {
+        const int y = i / w, x = i - y * w, s = 2 * w;
+        dst[i] = src[(2 * y) * s + 2 * x] + src[(2 * y) * s + 2 * x + 1] + src[(2 * y + 1) * s + 2 * x] +
+                 src[(2 * y + 1) * s + 2 * x + 1];
+    }
+}
+
+// every fine cell: the level of its leaf (the first level from the whole square down
+// whose square holds at most T points, or the floor D) into lev[morton], and
+// flag[morton] = 1 iff the cell is the first of its leaf.  Level l of the pyramid
+// (2^l x 2^l) starts at pyr + (4^l - 1) / 3; level D is qhist.
+__global__ void k_qt_leaf(const int *pyr, int D, int T, int *flag, unsigned char *lev)
+{
+    const int F = 1 << D;
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < F * F; f += gridDim.x * blockDim.x) {
+        const int fy = f >> D, fx = f & (F - 1);
+        int l = 0;
+        for (; l < D; ++l) {
+            const int c = pyr[((1 << (2 * l)) - 1) / 3 + ((fy >> (D - l)) << l) + (fx >> (D - l))];
+            if (c <= T) break;
+        }
+        const unsigned m = qt_morton((unsigned)fx, (unsigned)fy);
+        lev[m] = (unsigned char)l;
+        flag[m] = (m & ((1u << (2 * (D - l))) - 1u)) == 0u ? 1 : 0;
+    }
+}
+
+// qmap (row-major) = the depth-first number of each fine cell's leaf: the exclusive
+// prefix count of leaf starts at its leaf's first cell
+__global__ void k_qt_map(const int *pre, const unsigned char *lev, int D, int *qmap)
+{
+    const int F = 1 << D;
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < F * F; f += gridDim.x * blockDim.x) {
+        const int fy = f >> D, fx = f & (F - 1);
+        const unsigned m = qt_morton((unsigned)fx, (unsigned)fy);
+        const int l = lev[m];
+        qmap[f] = pre[m & ~((1u << (2 * (D - l))) - 1u)];
+    }
+}
+
+// points per fine cell of the quad-tree's square (the first division is made on the host)
 __global__ void k_qt_hist(const int2 *xy, int n, int x0, int y0, int shift, int F, int *hist)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -271,6 +337,11 @@ __global__ void k_intake_link(Dev d, const int3 *moves, int m, Inst I, int bits,
         old_xy[i] = o;
         gmoves[i] = make_int3(g, mv.y, mv.z);
         const int cell = partition_of(I, inst, bits, o);
+        if (I.qhist) {
+            // the re-divided quad-tree counts points at their positions after the step
+            atomicSub(I.qhist + qt_fine(I, o), 1);
+            atomicAdd(I.qhist + qt_fine(I, make_int2(mv.y, mv.z)), 1);
+        }
         if (far2 > 0.0 && dloc2) {
             const long long dx = (long long)mv.y - o.x, dy = (long long)mv.z - o.y;
             const unsigned long long dl = dloc2[cell];
@@ -302,6 +373,9 @@ __device__ __noinline__ void step_tail(Warp w, const Dev &d, Inst I, int4 *defer
 // above KMAX, for the first warp that runs out of partitions; DQ_DONE once a warp has
 // taken it.
 constexpr int DQ_MOVE = -2, DQ_HUGE = -50, DQ_DONE = -100, DQ_PASSES = 3;
+
+// Global-path writes the last warp certifies itself; a longer list goes to the whole GPU.
+constexpr int TAIL_CERTIFY = 64;
 
 // Append an entry.  The list is cleared to -1 before every step and the point id is
 // written last (after a fence), so a warp that takes a reserved but unwritten entry
@@ -513,7 +587,7 @@ __global__ void __launch_bounds__(WPB * 32, 6) k_kinetic(Dev dp, const int3 *mov
     Warp w = make_warp(&shs[wib], gw + 1, gw + 17 * d.stamp, d);
     const bool tl = d.timeline && d.counters;
     if (tl && gw == 0 && w.lane == 0) d.counters[C_T0] = global_ns();
-    const int items = ncells * wpp;
+    const int items = (I.ncells_dyn ? __ldcg(I.ncells_dyn) : ncells) * wpp;
     // One loop, one move per iteration: first the moves of the (partition, share) work
     // items the warp takes from a ticket; when those are gone, the whole moves left
     // so far (drained in parallel with the warps still busy; each may be left again,
@@ -724,7 +798,8 @@ __device__ __noinline__ void step_tail(Warp w, const Dev &d, Inst I, int4 *defer
     dev_count(w, d, C_CYC_TAIL, (unsigned long long)(clock64() - c0));
     __threadfence();
     int hi = __shfl_sync(FULL, __ldcg(d.dirty_count), 0);
-    if (hi > 4096) {
+    if (hi > TAIL_CERTIFY) {
+        // a longer list is certified by the whole GPU (k_certify_step, the next node)
         if (w.lane == 0) d.status[S_CERTPEND] = 1;
         return;
     }
@@ -734,6 +809,18 @@ __device__ __noinline__ void step_tail(Warp w, const Dev &d, Inst I, int4 *defer
 }
 
 // certify the dirty slots [lo, *dirty_count) (the slots written in this step)
+// The step's certification of the triangles written on the global-memory path when the
+// last warp left the list to the whole GPU (S_CERTPEND); a no-op otherwise.
+__global__ void k_certify_step(Dev d, int *viol, int *viol_count, int viol_cap)
+{
+    if (__ldcg(d.status + S_CERTPEND) == 0 || __ldcg(d.status) != 0) return;
+    int hi = __ldcg(d.dirty_count);
+    if (hi > d.dirty_cap) return;  // overflowed: the host certifies every slot
+    unsigned ex = 0, ti = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += gridDim.x * blockDim.x)
+        certify_one(d, d.dirty[i], viol, viol_count, viol_cap, &ex, &ti);
+}
+
 __global__ void k_certify(Dev d, int lo, int *viol, int *viol_count, int viol_cap)
 {
     int hi = *d.dirty_count;

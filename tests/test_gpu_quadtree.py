@@ -15,7 +15,8 @@ pytestmark = pytest.mark.gpu
 
 def _tri(**kw):
     from paper_2308_06484_gb300 import kdt
-    return kdt.Triangulation(kdt.default_config(quadtree=1, **kw))
+    kw.setdefault("quadtree", 1)
+    return kdt.Triangulation(kdt.default_config(**kw))
 
 
 def _leaf_minima(t, xy, sq, lay, N=2):
@@ -67,3 +68,28 @@ def test_batch_rejected():
     t = _tri(domain_bits=20)
     with pytest.raises(kdt.KDTError):
         t.build_batch([W.uniform_points(100, 20, 1), W.uniform_points(100, 20, 2)])
+
+
+def test_redivided_at_every_step():
+    """kdt_config.quadtree = 2: the division is made again on the GPU at the start of
+    every step (Fig. 4), inside the build's square; after each step the leaves in use
+    are the reference's division of the positions the step started from, every point's
+    leaf follows through the per-leaf minima, and the triangulation equals the oracle's."""
+    import torch
+    w = W.KineticWorkload(W.mixture_lattice_points(20000, 20, 27), 16, 20, (1, 4), (500, 40000), seed=28,
+                          name="qt-every-step")
+    t = _tri(domain_bits=20, points_per_partition=48, quadtree=2)
+    t.build(w.positions)
+    sq0, lay = Q.leaves(w.positions, 48)
+    assert t.num_cells() == len(sq0)
+    counts = set()
+    for s in range(6):
+        before = w.positions
+        t.step(torch.from_numpy(w.next_moves()).cuda())
+        assert_same(t.export_triangles(), w.positions, "re-divided quadtree step %d" % s)
+        sq, _ = Q.leaves(before, 48, lay=lay)
+        assert t.num_cells() == len(sq), (s, t.num_cells(), len(sq))
+        _leaf_minima(t, w.positions, sq, lay)
+        counts.add(len(sq))
+    assert len(counts) > 1  # the division changed over the steps
+    assert t.verify() == 0

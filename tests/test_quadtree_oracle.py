@@ -101,3 +101,28 @@ def test_plants_are_caught():
             finally:
                 g["Q"] = old
         assert (failed == 0) if plant is None else (failed > 0), name
+
+
+def test_redivision_in_a_given_square():
+    """A division repeated with the build's layout clamps positions into its square and
+    equals a fresh division when every position is inside it."""
+    import numpy as np
+    from oracle import quadtree as Q
+    rng = np.random.default_rng(5)
+    xy = rng.integers(100, 900, size=(400, 2))
+    sq, lay = Q.leaves(xy, 8)
+    assert Q.leaves(xy, 8, lay=lay)[0] == sq
+    moved = xy.copy()
+    moved[:40] = [[-50, 5000]] * 40  # outside: clamped to the top-left corner's leaf
+    sq2, _ = Q.leaves(moved, 8, lay=lay)
+    cl = np.stack([np.clip(moved[:, 0], lay[0], lay[0] + (1 << lay[2]) - 1),
+                   np.clip(moved[:, 1], lay[1], lay[1] + (1 << lay[2]) - 1)], axis=1)
+    assert sq2 == Q.leaves(cl, 8, lay=lay)[0]
+    assert sq2 != sq  # 40 points piled into one corner divide it further
+    blocks = Q.block_of(moved, sq2, lay)
+    assert (blocks >= 0).all()
+    counts = np.bincount(blocks, minlength=len(sq2))
+    side0 = 1 << lay[2]
+    assert sum(s * s for _, _, s in sq2) == side0 * side0  # the leaves tile the square
+    for (x, y, side), c in zip(sq2, counts):
+        assert c <= 8 or side == side0 >> lay[3]  # above the threshold only at the floor
