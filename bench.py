@@ -439,7 +439,7 @@ def run_c3(args, rank=0, ws=1, local=0, comparators=True):
     if comparators:
         def same_steps(**kw):
             tq = mk(**kw) if "quadtree" not in kw else kdt.Triangulation(
-                kdt.default_config(domain_bits=24, quadtree=1, points_per_partition=256), device=local)
+                kdt.default_config(domain_bits=24, quadtree=kw["quadtree"], points_per_partition=256), device=local)
             tq.build(xy0)
             qms = timed_steps(tq, moves, args.warmup)
             stq = tq.stats()
@@ -455,7 +455,9 @@ def run_c3(args, rank=0, ws=1, local=0, comparators=True):
             "gpu_full_rebuild": {"value": m_avg / (rebuild_ms / 1000.0), "unit": "updates/s",
                                  "ms_per_rebuild": rebuild_ms},
             "gpu_kinetic_quadtree_partitions": same_steps(quadtree=1),
+            "gpu_kinetic_quadtree_redivided_every_step": same_steps(quadtree=2),
             "gpu_kinetic_planned_order": same_steps(plan=1),
+            "gpu_kinetic_seven_blocks_per_sm": same_steps(kinetic_blocks_per_sm=7),
             "gpu_kinetic_variant_in_place": same_steps(variant=1),
             "gpu_kinetic_variant_move_flip": same_steps(variant=2),
         }

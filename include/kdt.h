@@ -146,6 +146,10 @@ typedef struct {
     int32_t batch_build;   /* 1 (default): the instances of a batch are (re)built together,
                               one set of launches for all of them; 0: one instance after
                               another.  The triangulations are the same.                    */
+    int32_t kinetic_blocks_per_sm; /* 0 or 6 (default): the kinetic kernel compiled for six
+                              128-thread blocks per SM (up to 80 registers a thread); 7: for
+                              seven (up to 72 registers, more warps in flight).  Scheduling
+                              only.                                                          */
 } kdt_config;
 
 /* Counters since creation (or kdt_reset_stats). */

@@ -323,7 +323,9 @@ int thread_grid(kdt *h, long long items, int threads)
 int kinetic_blocks(kdt *h)
 {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_kinetic, WPB * 32, 0) != cudaSuccess ||
+    const bool seven = h->cfg.kinetic_blocks_per_sm == 7;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, seven ? k_kinetic<7> : k_kinetic<6>, WPB * 32, 0) !=
+            cudaSuccess ||
         per_sm < 1)
         per_sm = 4;
     return sm_count(h->device) * per_sm;
@@ -909,7 +911,8 @@ int enqueue_step(kdt *h, cudaStream_t st, const Dev &d, const int3 *mp, int mi, 
     kinetic_shape(h, &kblocks, &kthreads);
     Dev dk = d;
     dk.big = h->big;
-    k_kinetic<<<kblocks, kthreads, 0, st>>>(dk, h->gmoves, h->head, h->next, I, h->ncells, h->wpp, h->deferred,
+    auto kin = h->cfg.kinetic_blocks_per_sm == 7 ? k_kinetic<7> : k_kinetic<6>;
+    kin<<<kblocks, kthreads, 0, st>>>(dk, h->gmoves, h->head, h->next, I, h->ncells, h->wpp, h->deferred,
                                             h->scal + S_DEFER, h->mcap, h->viol, h->viol_cap);
     if (h->cfg.timing) CK(cudaEventRecordWithFlags(h->ev1, st, evflags));
     k_certify_step<<<thread_grid(h, 4096, 256), 256, 0, st>>>(d, h->viol, h->scal + S_VIOL, h->viol_cap);
@@ -1384,7 +1387,8 @@ int kdt_create(kdt **out, const kdt_config *cfg, int device, void *cuda_stream)
         c.points_per_partition < 0 || c.warps_per_partition < 0 || c.warps_per_partition > 32 ||
         c.variant < 0 || c.variant > 2 || c.quadtree < 0 || c.quadtree > 2 ||
         !(c.rebuild_displacement >= 0.0f) || c.rebuild_displacement > 1e9f || c.plan < 0 || c.plan > 2 ||
-        c.batch_build < 0 || c.batch_build > 1)
+        c.batch_build < 0 || c.batch_build > 1 ||
+        (c.kinetic_blocks_per_sm != 0 && c.kinetic_blocks_per_sm != 6 && c.kinetic_blocks_per_sm != 7))
         return KDT_ERR_ARG;
     if (c.retry_cap == 0) c.retry_cap = 4096;
     if (cudaSetDevice(device) != cudaSuccess) return KDT_ERR_CUDA;

@@ -575,9 +575,14 @@ __device__ __noinline__ void drained_done(Warp w, const Dev &d, int rc, bool hug
     }
 }
 
-__global__ void __launch_bounds__(WPB * 32, 6) k_kinetic(Dev dp, const int3 *moves, const int *head, const int *next,
-                                                         Inst I, int ncells, int wpp, int4 *deferred,
-                                                         int *defer_count, int defer_cap, int *viol, int viol_cap)
+// The kinetic kernel, compiled for two occupancies: MINB = 6 blocks per SM (up to 80
+// registers a thread, the default) or 7 (up to 72: more warps in flight, more spills of
+// the inlined move path); kdt_config.kinetic_blocks_per_sm chooses.
+template <int MINB>
+__global__ void __launch_bounds__(WPB * 32, MINB) k_kinetic(Dev dp, const int3 *moves, const int *head,
+                                                            const int *next, Inst I, int ncells, int wpp,
+                                                            int4 *deferred, int *defer_count, int defer_cap,
+                                                            int *viol, int viol_cap)
 {
     KD_BLOCK_DEV(dp);
     __shared__ WarpShared shs[WPB];

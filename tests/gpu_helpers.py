@@ -27,18 +27,32 @@ def run_kinetic(tri, w, steps, every=1, check_points=True):
 
 
 def hull_count(xy):
-    """Points on the convex hull boundary, collinear ones included (monotone chain)."""
-    pts = np.unique(np.asarray(xy, dtype=np.int64), axis=0)
+    """Points on the convex hull boundary of distinct points, collinear ones included
+    (monotone chain, exact integers).  Points strictly inside the polygon of the extreme
+    points in 16 directions cannot be on the boundary and are dropped first."""
+    pts = np.asarray(xy, dtype=np.int64).reshape(-1, 2)
     if pts.shape[0] < 3:
         return pts.shape[0]
+    if pts.shape[0] > 64:
+        ang = np.arange(16) * (2 * np.pi / 16)
+        dirs = np.stack([np.round(1024 * np.cos(ang)), np.round(1024 * np.sin(ang))], axis=1).astype(np.int64)
+        ext = np.array([np.argmax(pts[:, 0] * dx + pts[:, 1] * dy) for dx, dy in dirs])
+        poly = [pts[i] for k, i in enumerate(ext) if k == 0 or i != ext[k - 1]]
+        if len(poly) >= 3 and not np.array_equal(poly[0], poly[-1]):
+            inside = np.ones(pts.shape[0], dtype=bool)
+            for k in range(len(poly)):
+                a, b = poly[k], poly[(k + 1) % len(poly)]
+                inside &= (b[0] - a[0]) * (pts[:, 1] - a[1]) - (b[1] - a[1]) * (pts[:, 0] - a[0]) > 0
+            pts = pts[~inside]
 
     def chain(P):
         h = []
-        for p in P:
+        for p in P.tolist():
             while len(h) >= 2 and (h[-1][0] - h[-2][0]) * (p[1] - h[-2][1]) - (h[-1][1] - h[-2][1]) * (p[0] - h[-2][0]) < 0:
                 h.pop()
-            h.append((int(p[0]), int(p[1])))
+            h.append((p[0], p[1]))
         return h
+    pts = pts[np.lexsort((pts[:, 1], pts[:, 0]))]
     lower, upper = chain(pts), chain(pts[::-1])
     return len(set(lower) | set(upper))
 
@@ -57,7 +71,7 @@ def assert_same_tiled(got, xy, bits, tiles=8, overlap=0.5, threads=None, what=""
     triangulation, row for row."""
     import os
     from concurrent.futures import ThreadPoolExecutor
-    from paper_2308_06484_gb300.shard import _x_extent_circle, _canonical
+    from paper_2308_06484_gb300.shard import _x_extent_circle
     xy = np.ascontiguousarray(xy, dtype=np.int32)
     n = xy.shape[0]
     L = 1 << bits
@@ -85,25 +99,54 @@ def assert_same_tiled(got, xy, bits, tiles=8, overlap=0.5, threads=None, what=""
     threads = threads or max(1, min(32, len(os.sched_getaffinity(0))))
     with ThreadPoolExecutor(threads) as pool:
         parts = list(pool.map(one, range(tiles * tiles)))
-    acc = _canonical(np.unique(_canonical(np.concatenate(parts)), axis=0))
+    # (the oracle's rows are canonical, and so are they in global ids: a tile's ids are
+    # increasing; overlapping tiles give some rows more than once)
+    acc = np.concatenate(parts).astype(np.int64)
     h = hull_count(xy)
     assert got.shape[0] == 2 * n - 2 - h, "%s: %d rows, Euler wants %d" % (what, got.shape[0], 2 * n - 2 - h)
-    key = lambda t: (t[:, 0].astype(np.int64) * n + t[:, 1]) * n + t[:, 2]
-    kg, ka = key(got.astype(np.int64)), key(acc.astype(np.int64))
-    missing = ~np.isin(ka, kg)
+    g64 = np.asarray(got, dtype=np.int64)
+    missing = ~_members(acc, g64)
     assert not missing.any(), "%s: %d certified oracle triangles missing, e.g. %s" % (
         what, int(missing.sum()), acc[missing][:3].tolist())
-    rest = got[~np.isin(kg, ka)]
-    for tri in rest:
-        a, b, c = (int(v) for v in tri)
-        P = x64[[a, b, c]].astype(np.float64)
-        d = 2.0 * (P[0, 0] * (P[1, 1] - P[2, 1]) + P[1, 0] * (P[2, 1] - P[0, 1]) + P[2, 0] * (P[0, 1] - P[1, 1]))
-        s = (P ** 2).sum(axis=1)
-        ux = (s[0] * (P[1, 1] - P[2, 1]) + s[1] * (P[2, 1] - P[0, 1]) + s[2] * (P[0, 1] - P[1, 1])) / d
-        uy = (s[0] * (P[2, 0] - P[1, 0]) + s[1] * (P[0, 0] - P[2, 0]) + s[2] * (P[1, 0] - P[0, 0])) / d
-        r = np.hypot(P[0, 0] - ux, P[0, 1] - uy) * (1 + 1e-9) + 2.0
-        cand = np.nonzero((x64[:, 0] >= ux - r) & (x64[:, 0] <= ux + r) & (x64[:, 1] >= uy - r) &
-                          (x64[:, 1] <= uy + r))[0]
-        bad = [int(q) for q in cand if q not in (a, b, c) and oracle.incircle_sos(xy, a, b, c, int(q)) > 0]
-        assert not bad, "%s: triangle %s has points %s in its circle" % (what, tri.tolist(), bad[:3])
+    rest = got[~_members(g64, acc)]
+    if rest.shape[0]:
+        # the exact empty-circle test against every point near the circle (points sorted
+        # by x; a float64 box around the circle with a margin selects the candidates)
+        by_x = np.argsort(x64[:, 0], kind="stable")
+        xs = x64[by_x, 0]
+        P = x64[rest].astype(np.float64)
+        ax, ay, bx, byy, cx, cy = P[:, 0, 0], P[:, 0, 1], P[:, 1, 0], P[:, 1, 1], P[:, 2, 0], P[:, 2, 1]
+        d = 2.0 * (ax * (byy - cy) + bx * (cy - ay) + cx * (ay - byy))
+        a2, b2, c2 = ax * ax + ay * ay, bx * bx + byy * byy, cx * cx + cy * cy
+        ux = (a2 * (byy - cy) + b2 * (cy - ay) + c2 * (ay - byy)) / d
+        uy = (a2 * (cx - bx) + b2 * (ax - cx) + c2 * (bx - ax)) / d
+        r = np.hypot(ax - ux, ay - uy) * (1 + 1e-9) + 2.0
+        for k, tri in enumerate(rest):
+            a, b, c = (int(v) for v in tri)
+            lo = np.searchsorted(xs, np.int64(np.floor(max(ux[k] - r[k], -2.0 ** 62))), "left")
+            hi = np.searchsorted(xs, np.int64(np.ceil(min(ux[k] + r[k], 2.0 ** 62))), "right")
+            cand = by_x[lo:hi]
+            cand = cand[(x64[cand, 1] >= uy[k] - r[k]) & (x64[cand, 1] <= uy[k] + r[k])]
+            dd = (x64[cand, 0] - ux[k]) ** 2 + (x64[cand, 1] - uy[k]) ** 2
+            cand = cand[dd <= r[k] * r[k]]  # (r has a margin above the float64 rounding)
+            bad = [int(q) for q in cand if q not in (a, b, c) and oracle.incircle_sos(xy, a, b, c, int(q)) > 0]
+            assert not bad, "%s: triangle %s has points %s in its circle" % (what, tri.tolist(), bad[:3])
     return acc.shape[0], rest.shape[0]
+
+
+def _members(A, B):
+    """For each row of A (int64, 3 columns): is it a row of B?  Rows are hashed
+    (multiply-xor, wrapping 64-bit), B's hashes sorted, and every hash hit is confirmed
+    by comparing the rows themselves."""
+    def hsh(T):
+        T = T.astype(np.uint64)
+        return (T[:, 0] * np.uint64(0x9E3779B97F4A7C15)) ^ (T[:, 1] * np.uint64(0xC2B2AE3D27D4EB4F)) ^ \
+               (T[:, 2] * np.uint64(0x165667B19E3779F9))
+    if B.shape[0] == 0:
+        return np.zeros(A.shape[0], dtype=bool)
+    hb = hsh(B)
+    o = np.argsort(hb, kind="stable")
+    hb = hb[o]
+    ha = hsh(A)
+    pos = np.minimum(np.searchsorted(hb, ha), hb.shape[0] - 1)
+    return (hb[pos] == ha) & (B[o[pos]] == A).all(axis=1)
