@@ -456,6 +456,7 @@ def run_c3(args, rank=0, ws=1, local=0, comparators=True):
                                  "ms_per_rebuild": rebuild_ms},
             "gpu_kinetic_quadtree_partitions": same_steps(quadtree=1),
             "gpu_kinetic_quadtree_redivided_every_step": same_steps(quadtree=2),
+            "gpu_kinetic_index_order": same_steps(partition_order=1),
             "gpu_kinetic_planned_order": same_steps(plan=1),
             "gpu_kinetic_seven_blocks_per_sm": same_steps(kinetic_blocks_per_sm=7),
             "gpu_kinetic_variant_in_place": same_steps(variant=1),
@@ -708,7 +709,8 @@ def run_c4(args, tn=None):
     torch.cuda.synchronize()
     rebuild_ms = a.elapsed_time(b)
     tri.close()
-    tk, stk = batched(timing=1)
+    tk, _ = batched(timing=1)
+    stk = tk.stats()
     kin_ms = stk["kinetic_kernel_ms"] / max(1, stk["kinetic_kernel_timed"])
     tk.close()
     m_avg = st["moves"] / args.steps

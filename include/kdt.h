@@ -150,6 +150,12 @@ typedef struct {
                               128-thread blocks per SM (up to 80 registers a thread); 7: for
                               seven (up to 72 registers, more warps in flight).  Scheduling
                               only.                                                          */
+    int32_t partition_order; /* 0 (default): without a planned order the kinetic kernel takes
+                              the partitions scattered, ticket k -> partition k * s mod the
+                              count (s coprime with the count, near 0.618 of it), so that
+                              partitions worked on at the same time are rarely neighbours
+                              (fewer claim conflicts on the triangles they share); 1: index
+                              order.  Scheduling only.                                       */
 } kdt_config;
 
 /* Counters since creation (or kdt_reset_stats). */

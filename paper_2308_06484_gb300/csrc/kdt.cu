@@ -16,6 +16,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <numeric>
 #include <new>
 #include <vector>
 
@@ -56,6 +57,7 @@ struct kdt {
     int *d_pofs = nullptr, *d_cofs = nullptr, *d_grid = nullptr, *d_tofs = nullptr;
     int *d_moff = nullptr, *h_moff = nullptr;  // move offsets: ctl + 4 and hctl + 4
     int ncells = 0;          // partitions (all instances)
+    int stride = 1;          // the scattering stride of the partitions (Inst.stride)
     int ncells_cap = 0;      // entries of the per-partition arrays (more than ncells when the
                              // quad-tree is re-divided at every step: one per fine cell)
     int ppp = 256;           // points per partition in use
@@ -271,6 +273,7 @@ Inst make_inst(kdt *h)
     I.qF = h->qF;
     I.order = h->cfg.plan ? h->order : nullptr;
     I.qhist = h->qhist;
+    I.stride = h->cfg.partition_order == 0 && !h->qhist ? h->stride : 1;
     I.ncells_dyn = h->qhist ? h->scal + S_NCELLS : nullptr;
     return I;
 }
@@ -646,6 +649,10 @@ int set_partitions(kdt *h, int ppp)
     if (cells > INT_MAX / 8) return KDT_ERR_ARG;
     h->cofs[h->ninst] = (int)cells;
     h->ncells = (int)cells;
+    // a stride near the golden ratio of the partition count, coprime with it
+    long long stride = std::max(1ll, std::llround(0.6180339887498949 * (double)cells));
+    while (std::gcd(stride, cells) != 1) ++stride;
+    h->stride = (int)stride;
     // a quad-tree re-divided at every step has at most one leaf per fine cell
     const long long cap = h->qhist ? (long long)h->qF * h->qF : cells;
     h->ncells_cap = (int)cap;
@@ -901,8 +908,11 @@ int enqueue_step(kdt *h, cudaStream_t st, const Dev &d, const int3 *mp, int mi, 
         k_plan<<<std::max(pblocks, 1), PLAN_THREADS, 0, st>>>(d, h->gmoves, h->old_xy, mi, I, h->cfg.domain_bits,
                                                              net ? h->mlp_w : nullptr, net ? h->pguess : nullptr,
                                                              h->pcost);
-        k_order<<<thread_grid(h, h->ncells_cap, 256), 256, 0, st>>>(h->pcost, h->ncells_cap, h->ohist, h->order, 0);
-        k_order<<<thread_grid(h, h->ncells_cap, 256), 256, 0, st>>>(h->pcost, h->ncells_cap, h->ohist, h->order, 1);
+        const int ostride = h->qhist || h->cfg.partition_order ? 1 : h->stride;
+        k_order<<<thread_grid(h, h->ncells_cap, 256), 256, 0, st>>>(h->pcost, h->ncells_cap, h->ohist, h->order, 0,
+                                                                    ostride);
+        k_order<<<thread_grid(h, h->ncells_cap, 256), 256, 0, st>>>(h->pcost, h->ncells_cap, h->ohist, h->order, 1,
+                                                                    ostride);
     }
     // inside a capture an event record must be an external node to keep its timestamp
     unsigned evflags = from_ctl ? cudaEventRecordExternal : cudaEventRecordDefault;
@@ -1388,7 +1398,8 @@ int kdt_create(kdt **out, const kdt_config *cfg, int device, void *cuda_stream)
         c.variant < 0 || c.variant > 2 || c.quadtree < 0 || c.quadtree > 2 ||
         !(c.rebuild_displacement >= 0.0f) || c.rebuild_displacement > 1e9f || c.plan < 0 || c.plan > 2 ||
         c.batch_build < 0 || c.batch_build > 1 ||
-        (c.kinetic_blocks_per_sm != 0 && c.kinetic_blocks_per_sm != 6 && c.kinetic_blocks_per_sm != 7))
+        (c.kinetic_blocks_per_sm != 0 && c.kinetic_blocks_per_sm != 6 && c.kinetic_blocks_per_sm != 7) ||
+        c.partition_order < 0 || c.partition_order > 1)
         return KDT_ERR_ARG;
     if (c.retry_cap == 0) c.retry_cap = 4096;
     if (cudaSetDevice(device) != cudaSuccess) return KDT_ERR_CUDA;

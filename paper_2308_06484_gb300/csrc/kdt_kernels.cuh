@@ -44,6 +44,10 @@ struct Inst {
     int *qhist;       // quad-tree re-divided at every step: points per fine cell, kept
                       // current by the intake; null otherwise
     const int *ncells_dyn;  // ... and this step's number of leaves (else the launch's count)
+    int stride;       // without a planned order: ticket k takes partition k * stride mod the
+                      // partition count (a stride coprime with it, near the golden ratio of
+                      // it), so partitions taken at the same time lie far apart; 0 or 1:
+                      // index order
     int ninst;
 };
 
@@ -622,6 +626,7 @@ __global__ void __launch_bounds__(WPB * 32, MINB) k_kinetic(Dev dp, const int3 *
                 c = t / wpp;
                 sub = t - c * wpp;
                 if (I.order) c = __ldcg(I.order + c);
+                else if (I.stride > 1) c = (int)(((long long)c * I.stride) % ncells);
                 kk = -1;
                 i = __shfl_sync(FULL, __ldcg(head + c), 0);
                 int inst = I.ninst > 1 ? csr_find(I.cofs, I.ninst + 1, c) : 0;

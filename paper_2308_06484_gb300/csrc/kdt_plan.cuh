@@ -182,8 +182,10 @@ __device__ __forceinline__ int plan_class(float c)
 }
 
 // phase 0: classes' sizes into hist[0 .. 63]; phase 1: order[] = partitions by class,
-// largest class first (cursor = hist[64 .. 127], zero before phase 0).
-__global__ void k_order(const float *pcost, int ncells, int *hist, int *order, int phase)
+// largest class first (cursor = hist[64 .. 127], zero before phase 0).  Partitions are
+// visited with the scattering stride (Inst.stride), so that inside a class neighbouring
+// partitions are rarely next to each other.
+__global__ void k_order(const float *pcost, int ncells, int *hist, int *order, int phase, int stride)
 {
     __shared__ int start[PLAN_CLASSES];
     if (phase == 1) {
@@ -196,7 +198,8 @@ __global__ void k_order(const float *pcost, int ncells, int *hist, int *order, i
         }
         __syncthreads();
     }
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncells; i += gridDim.x * blockDim.x) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < ncells; j += gridDim.x * blockDim.x) {
+        const int i = stride > 1 ? (int)(((long long)j * stride) % ncells) : j;
         const int c = plan_class(pcost[i]);
         if (phase == 0) {
             atomicAdd(hist + c, 1);

@@ -43,7 +43,8 @@ class Config(ctypes.Structure):
                 ("warps_per_partition", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("variant", ctypes.c_int32), ("quadtree", ctypes.c_int32),
                 ("rebuild_displacement", ctypes.c_float), ("plan", ctypes.c_int32),
-                ("batch_build", ctypes.c_int32), ("kinetic_blocks_per_sm", ctypes.c_int32)]
+                ("batch_build", ctypes.c_int32), ("kinetic_blocks_per_sm", ctypes.c_int32),
+                ("partition_order", ctypes.c_int32)]
 
 
 _STAT_FIELDS = ["steps", "moves", "rebuilds", "fallbacks", "kernel_launches", "flips", "retries",

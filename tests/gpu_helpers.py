@@ -110,10 +110,9 @@ def assert_same_tiled(got, xy, bits, tiles=8, overlap=0.5, threads=None, what=""
         what, int(missing.sum()), acc[missing][:3].tolist())
     rest = got[~_members(g64, acc)]
     if rest.shape[0]:
-        # the exact empty-circle test against every point near the circle (points sorted
-        # by x; a float64 box around the circle with a margin selects the candidates)
-        by_x = np.argsort(x64[:, 0], kind="stable")
-        xs = x64[by_x, 0]
+        # the exact empty-circle test against every point near the circle: a float64
+        # circumcircle widened by a margin above its rounding selects the candidates
+        # (a k-d tree when SciPy is there), the exact SoS predicate decides
         P = x64[rest].astype(np.float64)
         ax, ay, bx, byy, cx, cy = P[:, 0, 0], P[:, 0, 1], P[:, 1, 0], P[:, 1, 1], P[:, 2, 0], P[:, 2, 1]
         d = 2.0 * (ax * (byy - cy) + bx * (cy - ay) + cx * (ay - byy))
@@ -121,15 +120,23 @@ def assert_same_tiled(got, xy, bits, tiles=8, overlap=0.5, threads=None, what=""
         ux = (a2 * (byy - cy) + b2 * (cy - ay) + c2 * (ay - byy)) / d
         uy = (a2 * (cx - bx) + b2 * (ax - cx) + c2 * (bx - ax)) / d
         r = np.hypot(ax - ux, ay - uy) * (1 + 1e-9) + 2.0
+        try:
+            from scipy.spatial import cKDTree
+            tree = cKDTree(x64.astype(np.float64))
+            cands = tree.query_ball_point(np.stack([ux, uy], axis=1), r)
+        except ImportError:
+            by_x = np.argsort(x64[:, 0], kind="stable")
+            xs = x64[by_x, 0]
+            cands = []
+            for k in range(rest.shape[0]):
+                lo = np.searchsorted(xs, np.int64(np.floor(max(ux[k] - r[k], -2.0 ** 62))), "left")
+                hi = np.searchsorted(xs, np.int64(np.ceil(min(ux[k] + r[k], 2.0 ** 62))), "right")
+                c = by_x[lo:hi]
+                c = c[(x64[c, 1] >= uy[k] - r[k]) & (x64[c, 1] <= uy[k] + r[k])]
+                cands.append(c[(x64[c, 0] - ux[k]) ** 2 + (x64[c, 1] - uy[k]) ** 2 <= r[k] * r[k]])
         for k, tri in enumerate(rest):
             a, b, c = (int(v) for v in tri)
-            lo = np.searchsorted(xs, np.int64(np.floor(max(ux[k] - r[k], -2.0 ** 62))), "left")
-            hi = np.searchsorted(xs, np.int64(np.ceil(min(ux[k] + r[k], 2.0 ** 62))), "right")
-            cand = by_x[lo:hi]
-            cand = cand[(x64[cand, 1] >= uy[k] - r[k]) & (x64[cand, 1] <= uy[k] + r[k])]
-            dd = (x64[cand, 0] - ux[k]) ** 2 + (x64[cand, 1] - uy[k]) ** 2
-            cand = cand[dd <= r[k] * r[k]]  # (r has a margin above the float64 rounding)
-            bad = [int(q) for q in cand if q not in (a, b, c) and oracle.incircle_sos(xy, a, b, c, int(q)) > 0]
+            bad = [int(q) for q in cands[k] if q not in (a, b, c) and oracle.incircle_sos(xy, a, b, c, int(q)) > 0]
             assert not bad, "%s: triangle %s has points %s in its circle" % (what, tri.tolist(), bad[:3])
     return acc.shape[0], rest.shape[0]
 
