@@ -728,7 +728,7 @@ def run_c4(args, tn=None):
                                                  "ms_per_step": sum(qms) / len(qms), "verify_violations": tq.verify()}
     tq.close()
     if tn is not None:
-        tp, pms = batched(proposal=True, plan=2)
+        tp, pms = batched(proposal=True, plan=2)  # the network evaluated for all moves at once
         stp = tp.stats()
         comp["gpu_kinetic_batched_learned"] = {
             "value": stp["moves"] / (sum(pms) / 1000.0), "unit": "updates/s", "ms_per_step": sum(pms) / len(pms),

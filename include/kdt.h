@@ -133,16 +133,16 @@ typedef struct {
                               positions (kdt_stats.far_rebuilds).  With f > 0 a step that
                               finds no d values computes them first (N = 1, or the N of the
                               last call).  The triangulation is the same either way.      */
-    int32_t plan;          /* step planner (scheduling only; the triangulation is the same):
-                              0 (default): the kinetic kernel takes the partitions in index
-                              order.  1: before the moves start, every move's star is walked
-                              (its degree k) and each partition's work is estimated as the
-                              sum over its moves of k + 8; the partitions are then handed out
-                              largest estimate first (64 logarithmic classes).  2: as 1, and
-                              with a proposal set (kdt_set_proposal) the network is evaluated
-                              for all moves at once in the planner (instead of inside each
-                              move); its predicted cavity size 2^out17 is added to the
-                              estimate, and its guess is the locate's first candidate.      */
+    int32_t plan;          /* step planner, two bits (scheduling only; the triangulation is the
+                              same).  Bit 0 (1): before the moves start, every move's star is
+                              walked (its degree k), each partition's work is estimated as
+                              the sum over its moves of k + 8 (plus the network's predicted
+                              cavity size 2^out17 with bit 1 and a proposal), and the
+                              partitions are handed out largest estimate first (64
+                              logarithmic classes).  Bit 1 (2): with a proposal set
+                              (kdt_set_proposal) the network is evaluated for all moves at
+                              once by the planner instead of inside each move; its guess is
+                              the locate's first candidate.  0 (default): neither.          */
     int32_t batch_build;   /* 1 (default): the instances of a batch are (re)built together,
                               one set of launches for all of them; 0: one instance after
                               another.  The triangulations are the same.                    */

@@ -246,7 +246,7 @@ Dev make_dev(kdt *h)
     d.rlo = 0;
     d.rn = (int)std::max<int64_t>(h->n, 1);
     d.mlp = h->prop_on ? h->mlp_w : nullptr;
-    d.pguess = h->prop_on && h->cfg.plan == 2 ? h->pguess : nullptr;
+    d.pguess = h->prop_on && (h->cfg.plan & PLAN_NETWORK) ? h->pguess : nullptr;
     d.trace_x = h->trace_x;
     d.trace_y = h->trace_y;
     d.trace_count = h->trace_count;
@@ -271,7 +271,7 @@ Inst make_inst(kdt *h)
     I.qy0 = h->qy0;
     I.qshift = h->qshift;
     I.qF = h->qF;
-    I.order = h->cfg.plan ? h->order : nullptr;
+    I.order = (h->cfg.plan & PLAN_ORDER) ? h->order : nullptr;
     I.qhist = h->qhist;
     I.stride = h->cfg.partition_order == 0 && !h->qhist ? h->stride : 1;
     I.ncells_dyn = h->qhist ? h->scal + S_NCELLS : nullptr;
@@ -897,17 +897,21 @@ int enqueue_step(kdt *h, cudaStream_t st, const Dev &d, const int3 *mp, int mi, 
     }
     k_intake_link<<<thread_grid(h, cap, 256), 256, 0, st>>>(d, mp, mi, I, h->cfg.domain_bits, h->head, h->next,
                                                             h->old_xy, h->gmoves, h->dloc2, far2(h));
-    if (h->cfg.plan) {
-        // the planner: estimated work per partition (and the network's guesses), then
-        // the partitions in order of decreasing estimate
-        CK(cudaMemsetAsync(h->pcost, 0, (size_t)h->ncells_cap * sizeof(float), st));
-        CK(cudaMemsetAsync(h->ohist, 0, 2 * PLAN_CLASSES * sizeof(int), st));
-        const bool net = h->prop_on && h->cfg.plan == 2;
+    const bool net = h->prop_on && (h->cfg.plan & PLAN_NETWORK), ordered = (h->cfg.plan & PLAN_ORDER) != 0;
+    if (net || ordered) {
+        // the planner: estimated work per partition and / or the network's guesses,
+        // then (ordered) the partitions in order of decreasing estimate
+        if (ordered) {
+            CK(cudaMemsetAsync(h->pcost, 0, (size_t)h->ncells_cap * sizeof(float), st));
+            CK(cudaMemsetAsync(h->ohist, 0, 2 * PLAN_CLASSES * sizeof(int), st));
+        }
         int pblocks = (int)std::min<long long>(((long long)cap + PLAN_THREADS - 1) / PLAN_THREADS,
                                                8ll * sm_count(h->device));
         k_plan<<<std::max(pblocks, 1), PLAN_THREADS, 0, st>>>(d, h->gmoves, h->old_xy, mi, I, h->cfg.domain_bits,
                                                              net ? h->mlp_w : nullptr, net ? h->pguess : nullptr,
-                                                             h->pcost);
+                                                             ordered ? h->pcost : nullptr);
+    }
+    if (ordered) {
         const int ostride = h->qhist || h->cfg.partition_order ? 1 : h->stride;
         k_order<<<thread_grid(h, h->ncells_cap, 256), 256, 0, st>>>(h->pcost, h->ncells_cap, h->ohist, h->order, 0,
                                                                     ostride);
@@ -1119,7 +1123,9 @@ int step_core(kdt *h, const kdt_move *moves, const int64_t *moff, int64_t m)
         if (enqueue_step(h, st, d, mp, mi, false)) return KDT_ERR_CUDA;
         if (timed) CK(cudaEventRecord(h->ev3, st));
     }
-    h->stats.kernel_launches += (h->cfg.plan ? 7 : 4) + (h->qhist ? h->qD + 5 : 0);
+    h->stats.kernel_launches += 4 + ((h->cfg.plan & PLAN_ORDER) ? 2 : 0) +
+                                ((h->cfg.plan & PLAN_ORDER) || (h->prop_on && (h->cfg.plan & PLAN_NETWORK)) ? 1 : 0) +
+                                (h->qhist ? h->qD + 5 : 0);
     CK(cudaStreamSynchronize(st));
     if (h->qhist) h->ncells = h->qleaves = h->hscal[S_NCELLS];
     if (timed) {
@@ -1396,7 +1402,7 @@ int kdt_create(kdt **out, const kdt_config *cfg, int device, void *cuda_stream)
     if (c.domain_bits <= 0 || c.domain_bits > 28 || c.grid < 0 || c.grid > 4096 || c.retry_cap < 0 ||
         c.points_per_partition < 0 || c.warps_per_partition < 0 || c.warps_per_partition > 32 ||
         c.variant < 0 || c.variant > 2 || c.quadtree < 0 || c.quadtree > 2 ||
-        !(c.rebuild_displacement >= 0.0f) || c.rebuild_displacement > 1e9f || c.plan < 0 || c.plan > 2 ||
+        !(c.rebuild_displacement >= 0.0f) || c.rebuild_displacement > 1e9f || c.plan < 0 || c.plan > 3 ||
         c.batch_build < 0 || c.batch_build > 1 ||
         (c.kinetic_blocks_per_sm != 0 && c.kinetic_blocks_per_sm != 6 && c.kinetic_blocks_per_sm != 7) ||
         c.partition_order < 0 || c.partition_order > 1)

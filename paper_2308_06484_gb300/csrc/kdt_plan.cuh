@@ -22,6 +22,8 @@
 
 namespace kd {
 
+constexpr int PLAN_ORDER = 1;    // kdt_config.plan bit: hand out partitions by estimated work
+constexpr int PLAN_NETWORK = 2;  // ... bit: evaluate the proposal for all moves in the planner
 constexpr int PLAN_THREADS = 256;
 constexpr int PLAN_CLASSES = 64;
 
@@ -140,7 +142,7 @@ __device__ __forceinline__ bool plan_features(const Dev &d, const int *L, int k,
 
 // One thread per move i < m (m from the step's control words in a graph launch):
 // pguess[p] = the network's guess (0 .. 16, -1 = none) when mlp is set; pcost[cell of
-// the move's partition] += its estimated cost.
+// the move's partition] += its estimated cost when pcost is set.
 __global__ void __launch_bounds__(PLAN_THREADS) k_plan(Dev d, const int3 *gmoves, const int2 *old_xy, int m, Inst I,
                                                        int bits, const unsigned short *mlp, signed char *pguess,
                                                        float *pcost)
@@ -170,8 +172,10 @@ __global__ void __launch_bounds__(PLAN_THREADS) k_plan(Dev d, const int3 *gmoves
             }
         }
         if (pguess) pguess[p] = (signed char)guess;
-        const int inst = I.ninst > 1 ? csr_find(I.moff, I.ninst + 1, i) : 0;
-        atomicAdd(pcost + partition_of(I, inst, bits, po), cost);
+        if (pcost) {
+            const int inst = I.ninst > 1 ? csr_find(I.moff, I.ninst + 1, i) : 0;
+            atomicAdd(pcost + partition_of(I, inst, bits, po), cost);
+        }
     }
 }
 
