@@ -71,14 +71,23 @@ __device__ __forceinline__ int plan_network(const float *W, const float *x, floa
     float out[MLP_OUT];
 #pragma unroll
     for (int o = 0; o < MLP_OUT; ++o) out[o] = W[OFF_B3 + o];
-    for (int u = 0; u < MLP_H; ++u) {
-        float c = W[OFF_B2 + u];
-        const float *r = W + OFF_W2 + u * MLP_H;
+    // eight hidden units at a time: eight independent sums in flight (each unit's sum
+    // and the outputs' sums over the units keep their order)
+    constexpr int UB = 8;
+    for (int u0 = 0; u0 < MLP_H; u0 += UB) {
+        float c[UB];
 #pragma unroll
-        for (int k = 0; k < MLP_H; ++k) c = fmaf(r[k], h1[k], c);
-        const float g = fmaxf(c, 0.f);
+        for (int j = 0; j < UB; ++j) c[j] = W[OFF_B2 + u0 + j];
 #pragma unroll
-        for (int o = 0; o < MLP_OUT; ++o) out[o] = fmaf(W[OFF_W3 + o * MLP_H + u], g, out[o]);
+        for (int k = 0; k < MLP_H; ++k)
+#pragma unroll
+            for (int j = 0; j < UB; ++j) c[j] = fmaf(W[OFF_W2 + (u0 + j) * MLP_H + k], h1[k], c[j]);
+#pragma unroll
+        for (int j = 0; j < UB; ++j) {
+            const float g = fmaxf(c[j], 0.f);
+#pragma unroll
+            for (int o = 0; o < MLP_OUT; ++o) out[o] = fmaf(W[OFF_W3 + o * MLP_H + u0 + j], g, out[o]);
+        }
     }
     int best = 0;
     float bv = out[0];
