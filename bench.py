@@ -69,9 +69,17 @@ def bytes_per_update(k_old, k_new):
 BYTES_K6 = bytes_per_update(6, 6)
 
 # DRAM bytes (read + write) per moved point of one k_kinetic launch, from ncu's
-# dram__bytes_read.sum + dram__bytes_write.sum, valid only for the kernel sources it was
-# taken on (their SHA-256 prefix) and the workload it was taken on; null otherwise.
-KINETIC_TRAFFIC = {}
+# dram__bytes_read.sum + dram__bytes_write.sum (profiles/), valid only for the kernel
+# sources it was taken on (their SHA-256 prefix) and the workload it was taken on; the
+# bench line reports it scaled to the launch's moves, null otherwise.
+KINETIC_TRAFFIC = {
+    # 16e6-point workload, 3 launches of about 165,000 moves: 648.2, 647.6, 649.3 MB
+    "c3": {"sources": "6b0e3b47254213b2", "bytes_per_move": 3928.0},
+    # 1e6-point workload, 2 launches of 4,096 moves: 15.633, 15.658 MB
+    "c2": {"sources": "6b0e3b47254213b2", "bytes_per_move": 3820.0},
+    # 512-instance batch at 256 points per partition, 1 launch of 212,368 moves: 1,098 MB
+    "c4": {"sources": "6b0e3b47254213b2", "bytes_per_move": 5170.0},
+}
 
 
 def kernel_sources_hash():
