@@ -455,6 +455,9 @@ def run_c3(args, rank=0, ws=1, local=0, comparators=True):
                    "ms_per_step": sum(qms) / len(qms), "fallbacks": int(stq["fallbacks"]),
                    "moved_in_place": (stq["moves"] - stq["deletes"]) / max(1, stq["moves"]),
                    "cells": tq.num_cells()}
+            if kw.get("rebuild_displacement"):
+                out["far_rebuilds"] = int(stq["far_rebuilds"])
+                out["steps"] = int(stq["steps"])
             tq.close()
             return out
 
@@ -467,6 +470,7 @@ def run_c3(args, rank=0, ws=1, local=0, comparators=True):
             "gpu_kinetic_index_order": same_steps(partition_order=1),
             "gpu_kinetic_planned_order": same_steps(plan=1),
             "gpu_kinetic_seven_blocks_per_sm": same_steps(kinetic_blocks_per_sm=7),
+            "gpu_kinetic_displacement_rule_f1": same_steps(rebuild_displacement=1.0),
             "gpu_kinetic_variant_in_place": same_steps(variant=1),
             "gpu_kinetic_variant_move_flip": same_steps(variant=2),
         }
@@ -550,14 +554,19 @@ def run_c2(args, comparators=True):
             "gpu_full_rebuild": {"value": m / (rebuild_ms / 1000.0), "unit": "updates/s",
                                  "ms_per_rebuild": rebuild_ms}}
     if comparators:
-        for var, name in ((1, "gpu_kinetic_variant_in_place"), (2, "gpu_kinetic_variant_move_flip")):
-            t3 = mk(variant=var)
+        for kw, name in (({"variant": 1}, "gpu_kinetic_variant_in_place"),
+                         ({"variant": 2}, "gpu_kinetic_variant_move_flip"),
+                         ({"rebuild_displacement": 1.0}, "gpu_kinetic_displacement_rule_f1")):
+            t3 = mk(**kw)
             t3.build(xy0)
             vms = timed_steps(t3, moves, args.warmup, flush)
             st3 = t3.stats()
             comp[name] = {"value": st3["moves"] / (sum(vms) / 1000.0), "unit": "updates/s",
                           "moved_in_place": (st3["moves"] - st3["deletes"]) / max(1, st3["moves"]),
                           "fallbacks": int(st3["fallbacks"])}
+            if "rebuild_displacement" in kw:
+                comp[name]["far_rebuilds"] = int(st3["far_rebuilds"])
+                comp[name]["steps"] = int(st3["steps"])
             t3.close()
     line["comparators"] = comp
     if fut is not None:
