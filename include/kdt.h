@@ -193,7 +193,13 @@ typedef struct {
     int64_t redeferred;           /* drained moves left for later again (debug bit 1)       */
     int64_t far_rebuilds;         /* steps done as a rebuild because a move went farther
                                      than rebuild_displacement * d_local                  */
-    int64_t reserved[7];
+    int64_t big_in_place;         /* moves of points of degree above 64 done in place      */
+    int64_t cycles_big_in_place;  /* SM cycles of their in-place attempts                  */
+    int64_t cycles_big_delete;    /* ... of their deletions (when not in place)            */
+    int64_t cycles_big_insert;    /* ... of the insertions that followed those deletions   */
+    int64_t cycles_unyielding_max; /* longest move run without giving up (a high-degree
+                                     move, or a move taken again from the list), cycles   */
+    int64_t reserved[2];
 } kdt_stats;
 
 /* ---- lifecycle ------------------------------------------------------------------ */

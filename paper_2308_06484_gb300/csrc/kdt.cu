@@ -800,6 +800,11 @@ void add_counters(kdt *h)
     s.span_drained_ns += (int64_t)c[C_SPAN_DRAINED];
     if ((int64_t)c[C_DRAINED_MAX] > s.cycles_drained_max) s.cycles_drained_max = (int64_t)c[C_DRAINED_MAX];
     s.redeferred += (int64_t)c[C_REDEFER];
+    s.big_in_place += (int64_t)c[C_BIG_INPLACE];
+    s.cycles_big_in_place += (int64_t)c[C_CYC_BIG_INPLACE];
+    s.cycles_big_delete += (int64_t)c[C_CYC_BIG_DELETE];
+    s.cycles_big_insert += (int64_t)c[C_CYC_BIG] - (int64_t)c[C_CYC_BIG_INPLACE] - (int64_t)c[C_CYC_BIG_DELETE];
+    if ((int64_t)c[C_BIG_MAX] > s.cycles_unyielding_max) s.cycles_unyielding_max = (int64_t)c[C_BIG_MAX];
 }
 
 // Undo a step that failed after it started: restore the old positions and rebuild.

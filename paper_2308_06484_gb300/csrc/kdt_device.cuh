@@ -69,6 +69,10 @@ enum Counter : int {
     C_CYC_MAX = C_NUM,  // a second device slot, updated with atomicMax
     // device-only slots for rare events, added straight to global memory (dev_count)
     C_TAIL_MOVES, C_CYC_TAIL, C_BIG_MOVES, C_CYC_BIG, C_DRAIN_MOVES,
+    // high-degree moves: done in place, and the cycles of the in-place attempts and of
+    // the deletions (C_CYC_BIG is their whole time, insertion included); the longest move
+    // run without giving up (atomicMax)
+    C_BIG_INPLACE, C_CYC_BIG_INPLACE, C_CYC_BIG_DELETE, C_BIG_MAX,
     // timeline of a kinetic launch (global timer, ns): its start, the latest end of a
     // warp's partitions and of its drain; summed spans from the start
     C_T0, C_TT, C_TD, C_SPAN_TICKETS, C_SPAN_DRAIN, C_SPAN_ALL,

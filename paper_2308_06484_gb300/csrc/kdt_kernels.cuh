@@ -437,7 +437,8 @@ __device__ __forceinline__ MoveOut run_move(Warp w, const Dev &d, int p, int2 q,
     int s0 = -1, s1 = -1, hint = -1;
     long long c0 = clock64();
     int rc = move_point(w, d, p, q, s0, s1, hint, may_give_up);
-    if ((rc == MV_BIG || rc == MV_HUGE) && !may_give_up) {
+    const bool big = (rc == MV_BIG || rc == MV_HUGE) && !may_give_up;
+    if (big) {
         // a degree above KMAX: the star goes to the warp's global scratch.  A short
         // move that keeps every triangle of the star valid changes p's position (and
         // flips the star's edges that stop being Delaunay); otherwise p is deleted and
@@ -446,14 +447,17 @@ __device__ __forceinline__ MoveOut run_move(Warp w, const Dev &d, int p, int2 q,
         Warp wb = w;
         wb.token |= TOK_PATIENT;
         rc = move_in_place_big(wb, d, p, q);
+        const long long ci = clock64();
+        dev_count(w, d, C_CYC_BIG_INPLACE, (unsigned long long)(ci - cb));
         if (rc == 1) {
             rc = 0;
+            dev_count(w, d, C_BIG_INPLACE, 1);
         } else if (rc == 0) {
             rc = delete_point_big(wb, d, p, s0, s1, hint);
+            dev_count(w, d, C_CYC_BIG_DELETE, (unsigned long long)(clock64() - ci));
             if (rc == 0) rc = MV_GLOBAL;
         }
         dev_count(w, d, C_BIG_MOVES, 1);
-        dev_count(w, d, C_CYC_BIG, (unsigned long long)(clock64() - cb));
     }
     if (rc == MV_GLOBAL) {
         cnt_add(w, C_MV_GLOBAL, 1);
@@ -466,6 +470,12 @@ __device__ __forceinline__ MoveOut run_move(Warp w, const Dev &d, int p, int2 q,
         if (rc == INS_GLOBAL) rc = insert_point(w, d, p, q, hint, s0, s1, true);
     }
     unsigned cy = (unsigned)((clock64() - c0) >> 6);
+    if (!may_give_up) {
+        // a move run without giving up: the high-degree ones' whole time (in place,
+        // or deletion + insertion), and the longest of all such moves
+        if (w.lane == 0 && d.counters) atomicMax(d.counters + C_BIG_MAX, (unsigned long long)cy << 6);
+        if (big) dev_count(w, d, C_CYC_BIG, (unsigned long long)cy << 6);
+    }
     cnt_add(w, C_CYC_MOVE, cy);
     if (w.lane == 0 && cy > w.sh->cyc_max) w.sh->cyc_max = cy;
     o.rc = rc;
