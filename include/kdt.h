@@ -199,7 +199,9 @@ typedef struct {
     int64_t cycles_big_insert;    /* ... of the insertions that followed those deletions   */
     int64_t cycles_unyielding_max; /* longest move run without giving up (a high-degree
                                      move, or a move taken again from the list), cycles   */
-    int64_t reserved[2];
+    int64_t cycles_global_insert; /* SM cycles of insertions finished on the global-memory path
+                                     after a deletion (moves that left the staged region)  */
+    int64_t cycles_global_insert_max; /* the longest of those, cycles                       */
 } kdt_stats;
 
 /* ---- lifecycle ------------------------------------------------------------------ */

@@ -805,6 +805,9 @@ void add_counters(kdt *h)
     s.cycles_big_delete += (int64_t)c[C_CYC_BIG_DELETE];
     s.cycles_big_insert += (int64_t)c[C_CYC_BIG] - (int64_t)c[C_CYC_BIG_INPLACE] - (int64_t)c[C_CYC_BIG_DELETE];
     if ((int64_t)c[C_BIG_MAX] > s.cycles_unyielding_max) s.cycles_unyielding_max = (int64_t)c[C_BIG_MAX];
+    s.cycles_global_insert += (int64_t)c[C_CYC_GLOBAL_INS];
+    if ((int64_t)c[C_GLOBAL_INS_MAX] > s.cycles_global_insert_max)
+        s.cycles_global_insert_max = (int64_t)c[C_GLOBAL_INS_MAX];
 }
 
 // Undo a step that failed after it started: restore the old positions and rebuild.

@@ -73,6 +73,8 @@ enum Counter : int {
     // the deletions (C_CYC_BIG is their whole time, insertion included); the longest move
     // run without giving up (atomicMax)
     C_BIG_INPLACE, C_CYC_BIG_INPLACE, C_CYC_BIG_DELETE, C_BIG_MAX,
+    // insertions on the global-memory path after a deletion: cycles, and the longest one
+    C_CYC_GLOBAL_INS, C_GLOBAL_INS_MAX,
     // timeline of a kinetic launch (global timer, ns): its start, the latest end of a
     // warp's partitions and of its drain; summed spans from the start
     C_T0, C_TT, C_TD, C_SPAN_TICKETS, C_SPAN_DRAIN, C_SPAN_ALL,
@@ -443,10 +445,17 @@ __device__ __forceinline__ bool claim_list(Warp w, const Dev &d, const int *list
 }
 
 // claim_list, patient when the warp's token says so (the global-memory deletions and
-// in-place moves of a high-degree point's star)
+// in-place moves of a high-degree point's star, the insertions that finish a move on the
+// global-memory path)
 __device__ __forceinline__ bool claim_star_list(Warp w, const Dev &d, const int *list, int m)
 {
     return (w.token & TOK_PATIENT) ? claim_list<true>(w, d, list, m) : claim_list<false>(w, d, list, m);
+}
+
+// claim_lanes, patient when the warp's token says so
+__device__ __forceinline__ bool claim_lanes_tok(Warp w, const Dev &d, int mine, int m)
+{
+    return (w.token & TOK_PATIENT) ? claim_lanes<true>(w, d, mine, m) : claim_lanes<false>(w, d, mine, m);
 }
 
 __device__ __forceinline__ void release_all(Warp w, const Dev &d)
@@ -661,7 +670,7 @@ __device__ __noinline__ int lawson(Warp w, const Dev &d, int top, int p, bool in
         else if (w.lane == 3) mine = comp(nb, (e + 2) % 3) >> 2;
         else if (w.lane == 4) mine = comp(un, (f + 1) % 3) >> 2;
         else if (w.lane == 5) mine = comp(un, (f + 2) % 3) >> 2;
-        bool ok = claim_lanes(w, d, mine, 6);
+        bool ok = claim_lanes_tok(w, d, mine, 6);
         if (ok) {
             int4 v2, nb2, uv2, un2;
             load_tri(w, d, T, v2, nb2);
@@ -788,7 +797,7 @@ __device__ __noinline__ int insert_outside(Warp w, const Dev &d, int p, int2 q, 
         cand[2 * k + 3] = spare1;
     }
     __syncwarp();
-    bool ok = claim_list(w, d, cand, 2 * k + 4);
+    bool ok = claim_star_list(w, d, cand, 2 * k + 4);
     if (ok) {
         // re-check the chain under the claims
         bool good = true;
@@ -915,7 +924,7 @@ __device__ __noinline__ int insert_point(Warp w, const Dev &d, int p, int2 q, in
         case 7: mine = where == W_EDGE ? comp(un, (f + 2) % 3) >> 2 : -1; break;
         default: break;
         }
-        bool ok = claim_lanes(w, d, mine, 8);
+        bool ok = claim_lanes_tok(w, d, mine, 8);
         if (ok) {
             // re-read under the claims and re-classify
             int4 v2, nb2;

@@ -466,8 +466,16 @@ __device__ __forceinline__ MoveOut run_move(Warp w, const Dev &d, int p, int2 q,
             __threadfence();
         }
         __syncwarp();
-        rc = insert_staged(w, d, p, q, hint, s0, s1, true);
-        if (rc == INS_GLOBAL) rc = insert_point(w, d, p, q, hint, s0, s1, true);
+        const long long cg = clock64();
+        // p is deleted and must be inserted: its claims are patient (they wait, bounded,
+        // for slots other warps hold instead of releasing everything and walking again)
+        Warp wi = w;
+        wi.token |= TOK_PATIENT;
+        rc = insert_staged(wi, d, p, q, hint, s0, s1, true);
+        if (rc == INS_GLOBAL) rc = insert_point(wi, d, p, q, hint, s0, s1, true);
+        const unsigned long long gc = (unsigned long long)(clock64() - cg);
+        dev_count(w, d, C_CYC_GLOBAL_INS, gc);
+        if (w.lane == 0 && d.counters) atomicMax(d.counters + C_GLOBAL_INS_MAX, gc);
     }
     unsigned cy = (unsigned)((clock64() - c0) >> 6);
     if (!may_give_up) {

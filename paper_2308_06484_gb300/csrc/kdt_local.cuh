@@ -83,7 +83,7 @@ __device__ __noinline__ int ensure_local(Warp w, const Dev &d, int cnt, int slot
     if (j >= 0) return j;
     if (cnt >= LM || w.sh->ncl >= claim_cap(w) || slot < 0 || slot >= d.cap) return -1;
     int mine = w.lane == 0 ? slot : -1;
-    if (!claim_lanes(w, d, mine, 1)) return -1;
+    if (!claim_lanes_tok(w, d, mine, 1)) return -1;
     int4 v, nb;
     load_tri(w, d, slot, v, nb);
     if (!(v.w & ALIVE)) return -1;
@@ -269,7 +269,7 @@ __device__ __forceinline__ int bw_grow(Warp w, const Dev &d, Region &R, int p, i
         if (keep) need[__popc(k1 & ((1u << w.lane) - 1u))] = mine;
         if (keep2) need[__popc(k1) + __popc(k2 & ((1u << w.lane) - 1u))] = mine2;
         __syncwarp();
-        if (!claim_list(w, d, need, nu)) return BW_CLAIM;
+        if (!claim_star_list(w, d, need, nu)) return BW_CLAIM;
         // read the new triangles under their claims, then their vertices' coordinates
         const int base0 = R.cnt, cnt1 = R.cnt + nu;
         for (int i = w.lane; i < nu; i += 32) {
@@ -999,7 +999,7 @@ __device__ __noinline__ int insert_staged(Warp w, const Dev &d, int p, int2 q, i
             sh->tmp[2] = spare1;
         }
         __syncwarp();
-        bool ok = claim_list(w, d, sh->tmp, 3);
+        bool ok = claim_star_list(w, d, sh->tmp, 3);
         Region R;
         R.cnt = 3;
         R.dirty = (1ull << 1) | (1ull << 2);

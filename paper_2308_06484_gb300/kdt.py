@@ -60,7 +60,8 @@ _STAT_FIELDS3 = ["cycles_ear", "cycles_lawson", "cycles_certify", "proposal_move
                  "trace_rows", "tail_moves", "cycles_tail", "big_moves", "cycles_big", "drain_moves",
                  "span_tickets_ns", "span_drain_ns", "span_kernel_ns", "span_huge_ns", "span_drained_ns",
                  "cycles_drained_max", "redeferred", "far_rebuilds", "big_in_place", "cycles_big_in_place",
-                 "cycles_big_delete", "cycles_big_insert", "cycles_unyielding_max"]
+                 "cycles_big_delete", "cycles_big_insert", "cycles_unyielding_max", "cycles_global_insert",
+                 "cycles_global_insert_max"]
 
 
 class Stats(ctypes.Structure):
@@ -71,7 +72,7 @@ class Stats(ctypes.Structure):
                 + [("step_graph_ms", ctypes.c_double), ("tuned_points_per_partition", ctypes.c_int64),
                    ("tuned_warps_per_partition", ctypes.c_int64)]
                 + [(f, ctypes.c_int64) for f in _STAT_FIELDS3]
-                + [("reserved", ctypes.c_int64 * 2)])
+                )
 
 
 class DInfo(ctypes.Structure):
