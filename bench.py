@@ -73,12 +73,10 @@ BYTES_K6 = bytes_per_update(6, 6)
 # sources it was taken on (their SHA-256 prefix) and the workload it was taken on; the
 # bench line reports it scaled to the launch's moves, null otherwise.
 KINETIC_TRAFFIC = {
-    # 16e6-point workload, 3 launches of about 165,000 moves: 648.2, 647.6, 649.3 MB
-    "c3": {"sources": "6b0e3b47254213b2", "bytes_per_move": 3928.0},
-    # 1e6-point workload, 2 launches of 4,096 moves: 15.633, 15.658 MB
-    "c2": {"sources": "6b0e3b47254213b2", "bytes_per_move": 3820.0},
-    # 512-instance batch at 256 points per partition, 1 launch of 212,368 moves: 1,098 MB
-    "c4": {"sources": "6b0e3b47254213b2", "bytes_per_move": 5170.0},
+    # 16e6-point workload, 3 launches of 165,068 moves: 647.4, 647.3, 646.2 MB
+    "c3": {"sources": "d3a6f917f5892715", "bytes_per_move": 3919.0},
+    # 1e6-point workload, 2 launches of 4,096 moves: 15.61, 15.70 MB
+    "c2": {"sources": "d3a6f917f5892715", "bytes_per_move": 3821.0},
 }
 
 
