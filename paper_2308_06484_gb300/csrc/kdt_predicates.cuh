@@ -96,17 +96,15 @@ __device__ __forceinline__ int incircle_raw(int2 a, int2 b, int2 c, int2 d, bool
     return incircle_exact(a, b, c, d);
 }
 
-// Simulation-of-Simplicity incircle: rows a, b, c, d with ids ia..id.  When the
-// determinant is zero the answer is the sign of the first non-zero z-cofactor in
-// increasing id order:  row a: +orient(b,c,d)   row b: -orient(a,c,d)
-//                       row c: +orient(a,b,d)   row d: -orient(a,b,c)
-__device__ __forceinline__ int incircle_sos(int ia, int ib, int ic, int id, int2 a, int2 b,
-                                            int2 c, int2 d, bool use_filter, unsigned *exact_calls,
-                                            unsigned *ties)
+// The exact sign, and when it is zero the Simulation-of-Simplicity answer: the sign of
+// the first non-zero z-cofactor in increasing id order (row a: +orient(b,c,d), row b:
+// -orient(a,c,d), row c: +orient(a,b,d), row d: -orient(a,b,c)).  Out of line: the
+// filter decides most tests, and one copy of this slow path keeps the inlined code of
+// every caller small.  Returns the sign, plus 8 when the tie-break decided.
+__device__ __noinline__ int incircle_sos_exact(int ia, int ib, int ic, int id, int2 a, int2 b, int2 c, int2 d)
 {
-    int s = incircle_raw(a, b, c, d, use_filter, exact_calls);
+    int s = incircle_exact(a, b, c, d);
     if (s) return s;
-    ++*ties;
     int ids[4] = {ia, ib, ic, id};
     int done = 0;
     for (int k = 0; k < 4; ++k) {
@@ -122,9 +120,28 @@ __device__ __forceinline__ int incircle_sos(int ia, int ib, int ic, int id, int2
         case 2: cof = orient2d(a, b, d); break;
         default: cof = -orient2d(a, b, c); break;
         }
-        if (cof) return cof;
+        if (cof) return cof + 8;
     }
-    return 0;
+    return 8;
+}
+
+// Simulation-of-Simplicity incircle: rows a, b, c, d with ids ia..id (the filter, then
+// incircle_sos_exact).
+__device__ __forceinline__ int incircle_sos(int ia, int ib, int ic, int id, int2 a, int2 b,
+                                            int2 c, int2 d, bool use_filter, unsigned *exact_calls,
+                                            unsigned *ties)
+{
+    if (use_filter) {
+        int f = incircle_filter(a, b, c, d);
+        if (f) return f;
+    }
+    ++*exact_calls;
+    int r = incircle_sos_exact(ia, ib, ic, id, a, b, c, d);
+    if (r >= 7) {
+        ++*ties;
+        return r - 8;
+    }
+    return r;
 }
 
 // Conflict of a ghost triangle (u, v, inf), stored counter-clockwise: the outside of
