@@ -579,6 +579,24 @@ def run_c2(args, comparators=True):
 MLP_FLOPS_PER_ROW = 2 * 7424 * 3 + 2 * 18 * 64 + 2 * 64 * 64  # forward, backward to inputs of layers 2-3, grads
 
 
+def _tc_grad_flops_per_tile():
+    """BF16 tensor-core FLOPs k_mlp_grad_tc issues per 128-row tile: the row products
+    (three parts each: layers 1-3 forward, dOut W3, dZ2 W2, N and K as issued) and the
+    weight-gradient products over the 128 rows (G_a 128 x 112, three products; G_b
+    128 x 32, two)."""
+    row = lambda n, k: 3 * 2 * 128 * n * k
+    return (row(64, 32) + row(64, 64) + row(32, 64) + row(64, 32) + row(64, 64)
+            + 3 * 2 * 128 * 112 * 128 + 2 * 2 * 128 * 32 * 128)
+
+
+def bf16_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f).get("bf16_tflops", 1900.0)), "measured"
+    return 1900.0, "fallback"
+
+
 def train_proposal(args):
     """Train the proposal on traces of its training workloads; returns (trainer,
     holder handle, info)."""
@@ -591,26 +609,29 @@ def train_proposal(args):
                                    cap=args.c5_trace_cap)
     gen_s = time.time() - t0
     holder = kdt.Triangulation(kdt.default_config())
-    tn = proposal.Trainer(holder, seed=0, lr=args.c5_lr)
+    tn = proposal.Trainer(holder, seed=0, lr=args.c5_lr, tensor_cores=bool(args.c5_train_tc))
     torch.cuda.synchronize()
     t1 = time.time()
     loss = tn.fit(x, y, epochs=args.c5_epochs, batch=args.c5_batch, seed=0)
     train_s = time.time() - t1
     rows_big = min(x.shape[0], 1 << 18)
-    for _ in range(3):
-        holder.mlp_loss_grad(tn.params, x[:rows_big], y[:rows_big], tn.grad, tn.loss)
-    a, b = _events(1)[0]
-    a.record()
-    reps = 10
-    for _ in range(reps):
-        holder.mlp_loss_grad(tn.params, x[:rows_big], y[:rows_big], tn.grad, tn.loss)
-    b.record()
-    torch.cuda.synchronize()
-    grad_ms = a.elapsed_time(b) / reps
+    grad_ms = {}
+    for tc in (False, True):  # the gradient on the CUDA cores and on the tensor cores
+        for _ in range(3):
+            holder.mlp_loss_grad(tn.params, x[:rows_big], y[:rows_big], tn.grad, tn.loss, tensor_cores=tc)
+        a, b = _events(1)[0]
+        a.record()
+        reps = 10
+        for _ in range(reps):
+            holder.mlp_loss_grad(tn.params, x[:rows_big], y[:rows_big], tn.grad, tn.loss, tensor_cores=tc)
+        b.record()
+        torch.cuda.synchronize()
+        grad_ms[tc] = a.elapsed_time(b) / reps
     acc, mae = tn.evaluate(x, y)
     info = {"rows": int(x.shape[0]), "epochs": args.c5_epochs, "batch": args.c5_batch, "lr": args.c5_lr,
-            "train_top1": acc, "train_log2_cavity_mae": mae, "train_loss": loss, "trace_s": gen_s,
-            "train_s": train_s, "grad_ms": grad_ms, "grad_rows": rows_big}
+            "on_tensor_cores": bool(args.c5_train_tc), "train_top1": acc, "train_log2_cavity_mae": mae,
+            "train_loss": loss, "trace_s": gen_s, "train_s": train_s, "grad_ms": grad_ms[False],
+            "grad_tc_ms": grad_ms[True], "grad_rows": rows_big, "tensor_timeouts": int(holder.stats()["tensor_timeouts"])}
     return tn, holder, info
 
 
@@ -627,10 +648,12 @@ def run_c5(args, tn, holder, tinfo):
     xy0 = torch.from_numpy(w.positions).to(dev)
     moves = [torch.from_numpy(w.next_moves()).to(dev) for _ in range(nsteps)]
     res = {}
-    for mode in ("off", "in_move", "on"):
-        # on: the network evaluated for all moves by the step planner (plan = 2);
-        # in_move: evaluated inside each move
-        tri = kdt.Triangulation(kdt.default_config(grid=64, domain_bits=24, plan=2 if mode == "on" else 0))
+    plans = {"off": 0, "in_move": 0, "on": 6, "cuda_cores": 2}
+    for mode in ("off", "in_move", "on", "cuda_cores"):
+        # on: the network evaluated for all moves by the step planner on the tensor
+        # cores (plan = 2 | 4); cuda_cores: by the planner, one thread per move
+        # (plan = 2); in_move: evaluated inside each move
+        tri = kdt.Triangulation(kdt.default_config(grid=64, domain_bits=24, plan=plans[mode]))
         tri.build(xy0)
         if mode != "off":
             tri.set_proposal(tn.params)
@@ -650,6 +673,8 @@ def run_c5(args, tn, holder, tinfo):
     v_on, v_off = ston["moves"] / on_s, res["off"]["st"]["moves"] / off_s
     stin = res["in_move"]["st"]
     v_in = stin["moves"] / (sum(res["in_move"]["ms"]) / 1000.0)
+    stcc = res["cuda_cores"]["st"]
+    v_cc = stcc["moves"] / (sum(res["cuda_cores"]["ms"]) / 1000.0)
     peak_fp32 = 152 * 128 * 2 * 2.07e9 / 1e12
     achieved = MLP_FLOPS_PER_ROW * tinfo["grad_rows"] / (tinfo["grad_ms"] / 1000.0) / 1e12
     line = base_line(v_on, steps, args.warmup, on_s, "c5",
@@ -661,11 +686,26 @@ def run_c5(args, tn, holder, tinfo):
                         "eval_top1": eval_acc, "eval_majority_class": majority, "eval_log2_cavity_mae": eval_mae,
                         "eval_rows": int(ex.shape[0]), "gain": v_on / v_off - 1.0,
                         "in_move_evaluation": {"value": v_in, "gain": v_in / v_off - 1.0,
-                                               "hit_rate": stin["proposal_hits"] / max(1, stin["proposal_moves"])}}
+                                               "hit_rate": stin["proposal_hits"] / max(1, stin["proposal_moves"])},
+                        "tensor_timeouts": int(ston["tensor_timeouts"]),
+                        "planner_on_cuda_cores": {"value": v_cc, "gain": v_cc / v_off - 1.0,
+                                                  "hit_rate": stcc["proposal_hits"] / max(1, stcc["proposal_moves"]),
+                                                  "ms_per_step": sum(res["cuda_cores"]["ms"]) / steps}}
     line["training_kernel"] = {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
                                "frac": achieved / peak_fp32, "kernel": "k_mlp_grad", "kernel_ms": tinfo["grad_ms"],
                                "rows": tinfo["grad_rows"],
                                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+    # the tensor-core form: BF16 tensor FLOPs as issued (splits and padding included)
+    # against the measured dense BF16 peak, and the network's own FLOPs per second
+    tiles = (tinfo["grad_rows"] + 127) // 128
+    tc_tflops = _tc_grad_flops_per_tile() * tiles / (tinfo["grad_tc_ms"] / 1000.0) / 1e12
+    pk, pk_kind = bf16_peak()
+    line["training_kernel_tensor_cores"] = {
+        "bound": "tensor", "achieved": tc_tflops, "peak": pk, "unit": "TFLOP/s", "frac": tc_tflops / pk,
+        "kernel": "k_mlp_grad_tc", "kernel_ms": tinfo["grad_tc_ms"], "rows": tinfo["grad_rows"],
+        "peak_kind": pk_kind + " dense BF16 (burst)", "bf16_flops_per_tile": _tc_grad_flops_per_tile(),
+        "network_tflops": MLP_FLOPS_PER_ROW * tinfo["grad_rows"] / (tinfo["grad_tc_ms"] / 1000.0) / 1e12,
+        "speedup_vs_cuda_cores": tinfo["grad_ms"] / tinfo["grad_tc_ms"]}
     line["comparators"] = {"gpu_kinetic_plain": {"value": v_off, "unit": "updates/s",
                                                  "ms_per_step": 1000.0 * off_s / steps}}
     line["gpu_launches"] = int(ston["kernel_launches"])
@@ -743,15 +783,18 @@ def run_c4(args, tn=None):
                                                  "ms_per_step": sum(qms) / len(qms), "verify_violations": tq.verify()}
     tq.close()
     if tn is not None:
-        tp, pms = batched(proposal=True, plan=2)  # the network evaluated for all moves at once
-        stp = tp.stats()
-        comp["gpu_kinetic_batched_learned"] = {
-            "value": stp["moves"] / (sum(pms) / 1000.0), "unit": "updates/s", "ms_per_step": sum(pms) / len(pms),
-            "hit_rate": stp["proposal_hits"] / max(1, stp["proposal_moves"]),
-            "proposals_per_step": stp["proposal_moves"] / args.steps, "verify_violations": tp.verify()}
-        comp["gpu_kinetic_batched_learned"]["gain_vs_batched_plain"] = \
-            comp["gpu_kinetic_batched_learned"]["value"] / line["value"] - 1.0
-        tp.close()
+        # the network evaluated for all moves at once, on the CUDA cores and on the
+        # tensor cores
+        for key, plan in (("gpu_kinetic_batched_learned", 2), ("gpu_kinetic_batched_learned_tensor_cores", 6)):
+            tp, pms = batched(proposal=True, plan=plan)
+            stp = tp.stats()
+            comp[key] = {
+                "value": stp["moves"] / (sum(pms) / 1000.0), "unit": "updates/s", "ms_per_step": sum(pms) / len(pms),
+                "hit_rate": stp["proposal_hits"] / max(1, stp["proposal_moves"]),
+                "proposals_per_step": stp["proposal_moves"] / args.steps, "verify_violations": tp.verify(),
+                "tensor_timeouts": int(stp["tensor_timeouts"])}
+            comp[key]["gain_vs_batched_plain"] = comp[key]["value"] / line["value"] - 1.0
+            tp.close()
     if args.c4_plain_steps > 0:
         hs = []
         for x in start:
@@ -906,6 +949,7 @@ def main():
     ap.add_argument("--c5-epochs", type=int, default=4)
     ap.add_argument("--c5-batch", type=int, default=8192)
     ap.add_argument("--c5-lr", type=float, default=2e-3)
+    ap.add_argument("--c5-train-tc", type=int, default=1, help="train the proposal with the tensor-core gradient")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 

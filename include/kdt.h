@@ -142,7 +142,10 @@ typedef struct {
                               logarithmic classes).  Bit 1 (2): with a proposal set
                               (kdt_set_proposal) the network is evaluated for all moves at
                               once by the planner instead of inside each move; its guess is
-                              the locate's first candidate.  0 (default): neither.          */
+                              the locate's first candidate.  Bit 2 (4), with bit 1: the
+                              planner evaluates the network on the tensor cores (as
+                              kdt_mlp_forward_tc does) instead of one thread per move.
+                              0 (default): none.                                            */
     int32_t batch_build;   /* 1 (default): the instances of a batch are (re)built together,
                               one set of launches for all of them; 0: one instance after
                               another.  The triangulations are the same.                    */
@@ -202,6 +205,10 @@ typedef struct {
     int64_t cycles_global_insert; /* SM cycles of insertions finished on the global-memory path
                                      after a deletion (moves that left the staged region)  */
     int64_t cycles_global_insert_max; /* the longest of those, cycles                       */
+    int64_t tensor_timeouts;      /* CTAs of the tensor-core network kernels that gave up
+                                     waiting for their products (after about a second):
+                                     planner guesses left out (the step stays exact),
+                                     kdt_mlp_*_tc results NaN                              */
 } kdt_stats;
 
 /* ---- lifecycle ------------------------------------------------------------------ */
@@ -420,12 +427,36 @@ int kdt_set_proposal(kdt *h, const uint16_t *params_bf16);
  * needs no triangulation for the kdt_mlp_* calls). */
 int kdt_mlp_forward(kdt *h, const uint16_t *params_bf16, const float *x, int64_t rows, float *out);
 
+/* The same outputs computed on the tensor cores (tcgen05, 128 rows per tile): every
+ * activation is split into two BF16 parts (x = hi + lo to 2^-16 of |x|) and each layer
+ * is the two BF16 products with the BF16 weights, accumulated in FP32, so an output is
+ * within about 3 * 2^-15 of the magnitude sum_k |w_k| |x_k| propagated through the
+ * layers of kdt_mlp_forward's value (not bit-identical: the accumulation order is the
+ * hardware's).  Same arguments as kdt_mlp_forward; asynchronous.  Rows of a CTA whose
+ * products did not complete within about a second are NaN (counted in
+ * kdt_stats.tensor_timeouts). */
+int kdt_mlp_forward_tc(kdt *h, const uint16_t *params_bf16, const float *x, int64_t rows, float *out);
+
 /* Mean loss (device scalar, may be NULL) and its gradient with respect to the BF16
  * parameters' values (device, KDT_MLP_PARAMS FP32) over a batch: batch row r is input
  * row index[r] (device int64) or r when index is NULL; labels as kdt_set_trace writes
  * them.  Summation order is fixed, so results repeat exactly.  Asynchronous. */
 int kdt_mlp_loss_grad(kdt *h, const uint16_t *params_bf16, const float *x, const int32_t *labels,
                       const int64_t *index, int64_t rows, float lam, float *grad, float *loss);
+
+/* The same loss and gradient computed on the tensor cores (tcgen05, 128 rows per
+ * tile): in the forward and backward products every activation is split into three
+ * BF16 parts (to 2^-24 of its value) against the BF16 weights, and the weight
+ * gradients are products over the batch rows whose FP32 operands are split into two
+ * parts (three BF16 products per pair), all accumulated in FP32.  Not bit-identical
+ * to kdt_mlp_loss_grad (the hardware's accumulation order); within the tolerance its
+ * test uses (1e-3 of each tensor's largest entry, and of every entry above 5 % of it).
+ * The summation order is fixed, so results repeat exactly.  Same arguments as
+ * kdt_mlp_loss_grad (params_bf16 4-byte aligned); asynchronous.  If a CTA's products
+ * did not complete within about a second the gradient and loss are NaN (counted in
+ * kdt_stats.tensor_timeouts). */
+int kdt_mlp_loss_grad_tc(kdt *h, const uint16_t *params_bf16, const float *x, const int32_t *labels,
+                         const int64_t *index, int64_t rows, float lam, float *grad, float *loss);
 
 /* One Adam step t >= 1 (Kingma and Ba, 2015) on FP32 master parameters with moments m
  * and v (device, KDT_MLP_PARAMS each, updated in place); params_bf16 (device, may be

@@ -24,12 +24,13 @@
 #include "kdt_kernels.cuh"
 #include "kdt_dcalc.cuh"
 #include "kdt_plan.cuh"
+#include "kdt_tc.cuh"
 
 using namespace kd;
 
 namespace {
 
-constexpr int ABI_VERSION = 6;
+constexpr int ABI_VERSION = 7;
 
 struct Buf {
     void *p = nullptr;
@@ -101,6 +102,10 @@ struct kdt {
     int *order = nullptr;
     int *ohist = nullptr;
     signed char *pguess = nullptr;
+    // the network on the tensor cores (kdt_config.plan bit 2): every move's features and
+    // its partition (-1: no features), written by the planner
+    float *pfeat = nullptr;
+    int *ppart = nullptr;
     // quad-tree partitions (kdt_config.quadtree): leaf of every fine cell, the square
     int *qmap = nullptr;
     int qx0 = 0, qy0 = 0, qshift = 0, qF = 0, qleaves = 0, qleaf_side_lg = 0, qD = 0;
@@ -610,6 +615,8 @@ int ensure_moves(kdt *h, int64_t m)
     if (dalloc(&h->moves, c) || dalloc(&h->gmoves, c) || dalloc(&h->old_xy, c) || dalloc(&h->next, c) ||
         dalloc(&h->deferred, c))
         return KDT_ERR_CUDA;
+    if ((h->cfg.plan & PLAN_TENSOR) && (dalloc(&h->pfeat, (size_t)c * MLP_IN) || dalloc(&h->ppart, c)))
+        return KDT_ERR_CUDA;
     h->mcap = c;
     long long dc = 64ll * c + 4096;
     if (dc > (1ll << 30)) dc = 1ll << 30;
@@ -684,7 +691,7 @@ void free_state(kdt *h)
     void *ps[] = {h->xy, h->pt_tri, h->pt_stamp, h->tv, h->tn, h->viol, h->moves, h->gmoves, h->old_xy,
                   h->next, h->head, h->deferred, h->dirty, h->scan_tmp, h->d_pofs, h->d_cofs, h->d_grid,
                   h->ctl, h->d_tofs, h->qmap, h->dloc2, h->pcost, h->order, h->ohist, h->pguess,
-                  h->qhist, h->qpyr, h->qflag, h->qpre, h->qlev};
+                  h->qhist, h->qpyr, h->qflag, h->qpre, h->qlev, h->pfeat, h->ppart};
     for (void *p : ps)
         if (p) cudaFree(p);
     if (h->hctl) cudaFreeHost(h->hctl);
@@ -707,6 +714,8 @@ void free_state(kdt *h)
     h->order = nullptr;
     h->ohist = nullptr;
     h->pguess = nullptr;
+    h->pfeat = nullptr;
+    h->ppart = nullptr;
     h->qleaves = 0;
     h->mcap = 0; h->dirty_cap = 0; h->scan_tmp_cap = 0;
     Buf *bs[] = {&h->key, &h->bord, &h->hist, &h->hoff, &h->exp_cnt, &h->exp_off, &h->exp_fill, &h->exp_out,
@@ -786,6 +795,7 @@ void add_counters(kdt *h)
     s.cycles_lawson += (int64_t)c[C_CYC_LAWSON] << 6;
     s.cycles_certify += (int64_t)c[C_CYC_CERT] << 6;
     s.proposal_moves += c[C_PROP_MOVES];
+    s.tensor_timeouts += (int64_t)c[C_TC_FAIL];
     s.proposal_hits += c[C_PROP_HITS];
     s.trace_rows += c[C_TRACE_ROWS];
     s.tail_moves += c[C_TAIL_MOVES];
@@ -879,6 +889,14 @@ double far2(const kdt *h)
     return f > 0.0 && !h->qhist ? f * f : 0.0;  // (partitions that change every step keep no d_local)
 }
 
+// CTAs of the tensor-core network for `rows` rows: one per 128-row tile, at most three
+// per SM (66 KB of shared memory and 128 TMEM columns each)
+int tc_grid(const kdt *h, long long rows)
+{
+    const long long tiles = std::max(1ll, (rows + TC_M - 1) / TC_M);
+    return (int)std::min<long long>(tiles, 3ll * sm_count(h->device));
+}
+
 int enqueue_step(kdt *h, cudaStream_t st, const Dev &d, const int3 *mp, int mi, bool from_ctl)
 {
     int cap = from_ctl ? h->mcap : mi;
@@ -906,6 +924,7 @@ int enqueue_step(kdt *h, cudaStream_t st, const Dev &d, const int3 *mp, int mi, 
     k_intake_link<<<thread_grid(h, cap, 256), 256, 0, st>>>(d, mp, mi, I, h->cfg.domain_bits, h->head, h->next,
                                                             h->old_xy, h->gmoves, h->dloc2, far2(h));
     const bool net = h->prop_on && (h->cfg.plan & PLAN_NETWORK), ordered = (h->cfg.plan & PLAN_ORDER) != 0;
+    const bool tensor = net && (h->cfg.plan & PLAN_TENSOR);
     if (net || ordered) {
         // the planner: estimated work per partition and / or the network's guesses,
         // then (ordered) the partitions in order of decreasing estimate
@@ -916,8 +935,14 @@ int enqueue_step(kdt *h, cudaStream_t st, const Dev &d, const int3 *mp, int mi, 
         int pblocks = (int)std::min<long long>(((long long)cap + PLAN_THREADS - 1) / PLAN_THREADS,
                                                8ll * sm_count(h->device));
         k_plan<<<std::max(pblocks, 1), PLAN_THREADS, 0, st>>>(d, h->gmoves, h->old_xy, mi, I, h->cfg.domain_bits,
-                                                             net ? h->mlp_w : nullptr, net ? h->pguess : nullptr,
-                                                             ordered ? h->pcost : nullptr);
+                                                             net && !tensor ? h->mlp_w : nullptr,
+                                                             net ? h->pguess : nullptr, ordered ? h->pcost : nullptr,
+                                                             tensor ? h->pfeat : nullptr, tensor ? h->ppart : nullptr);
+        if (tensor)
+            k_mlp_tc<1><<<tc_grid(h, cap), TC_M, TCS_BYTES, st>>>(h->mlp_w, h->pfeat, mi, from_ctl ? h->ctl : nullptr,
+                                                                  nullptr, h->ppart, h->gmoves, h->pguess,
+                                                                  ordered ? h->pcost : nullptr,
+                                                                  h->counters + C_TC_FAIL);
     }
     if (ordered) {
         const int ostride = h->qhist || h->cfg.partition_order ? 1 : h->stride;
@@ -1133,6 +1158,7 @@ int step_core(kdt *h, const kdt_move *moves, const int64_t *moff, int64_t m)
     }
     h->stats.kernel_launches += 4 + ((h->cfg.plan & PLAN_ORDER) ? 2 : 0) +
                                 ((h->cfg.plan & PLAN_ORDER) || (h->prop_on && (h->cfg.plan & PLAN_NETWORK)) ? 1 : 0) +
+                                (h->prop_on && (h->cfg.plan & PLAN_NETWORK) && (h->cfg.plan & PLAN_TENSOR) ? 1 : 0) +
                                 (h->qhist ? h->qD + 5 : 0);
     CK(cudaStreamSynchronize(st));
     if (h->qhist) h->ncells = h->qleaves = h->hscal[S_NCELLS];
@@ -1410,7 +1436,7 @@ int kdt_create(kdt **out, const kdt_config *cfg, int device, void *cuda_stream)
     if (c.domain_bits <= 0 || c.domain_bits > 28 || c.grid < 0 || c.grid > 4096 || c.retry_cap < 0 ||
         c.points_per_partition < 0 || c.warps_per_partition < 0 || c.warps_per_partition > 32 ||
         c.variant < 0 || c.variant > 2 || c.quadtree < 0 || c.quadtree > 2 ||
-        !(c.rebuild_displacement >= 0.0f) || c.rebuild_displacement > 1e9f || c.plan < 0 || c.plan > 3 ||
+        !(c.rebuild_displacement >= 0.0f) || c.rebuild_displacement > 1e9f || c.plan < 0 || c.plan > 7 ||
         c.batch_build < 0 || c.batch_build > 1 ||
         (c.kinetic_blocks_per_sm != 0 && c.kinetic_blocks_per_sm != 6 && c.kinetic_blocks_per_sm != 7) ||
         c.partition_order < 0 || c.partition_order > 1)
@@ -1434,6 +1460,12 @@ int kdt_create(kdt **out, const kdt_config *cfg, int device, void *cuda_stream)
     }
     cudaMemset(h->scal, 0, S_NUM * sizeof(int));
     cudaMemset(h->counters, 0, C_SLOTS * sizeof(unsigned long long));
+    if (cudaFuncSetAttribute(k_mlp_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TCS_BYTES) != cudaSuccess ||
+        cudaFuncSetAttribute(k_mlp_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TCS_BYTES) != cudaSuccess ||
+        cudaFuncSetAttribute(k_mlp_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TG_BYTES) != cudaSuccess) {
+        kdt_destroy(h);
+        return KDT_ERR_CUDA;
+    }
     *out = h;
     return KDT_OK;
 }
@@ -1846,18 +1878,24 @@ int kdt_mlp_forward(kdt *h, const uint16_t *params_bf16, const float *x, int64_t
     return KDT_OK;
 }
 
-int kdt_mlp_loss_grad(kdt *h, const uint16_t *params_bf16, const float *x, const int32_t *labels,
-                      const int64_t *index, int64_t rows, float lam, float *grad, float *loss)
+int kdt_mlp_forward_tc(kdt *h, const uint16_t *params_bf16, const float *x, int64_t rows, float *out)
 {
-    if (!h || rows <= 0 || !params_bf16 || !x || !labels || !grad) return KDT_ERR_ARG;
+    if (!h || rows < 0 || (rows > 0 && (!params_bf16 || !x || !out))) return KDT_ERR_ARG;
+    if (rows == 0) return KDT_OK;
     CK(cudaSetDevice(h->device));
-    if (!on_device(h, params_bf16) || !on_device(h, x) || !on_device(h, labels) || !on_device(h, grad) ||
-        (loss && !on_device(h, loss)) || (index && !on_device(h, index)))
-        return KDT_ERR_ARG;
-    int sms = 0;
-    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
-    long long tiles = (rows + GT - 1) / GT;
-    int blocks = (int)std::min<long long>(tiles, 2ll * sms);
+    if (!on_device(h, params_bf16) || !on_device(h, x) || !on_device(h, out)) return KDT_ERR_ARG;
+    if (((uintptr_t)params_bf16 & 3) != 0) return KDT_ERR_ARG;  // weight rows read as BF16 pairs
+    k_mlp_tc<0><<<tc_grid(h, rows), TC_M, TCS_BYTES, h->stream>>>((const unsigned short *)params_bf16, x, rows,
+                                                                  nullptr, out, nullptr, nullptr, nullptr, nullptr,
+                                                                  h->counters + C_TC_FAIL);
+    h->stats.kernel_launches++;
+    CK(cudaGetLastError());
+    return KDT_OK;
+}
+
+// per-block partial gradients for `blocks` blocks (kept between calls)
+static int ensure_mlp_part(kdt *h, int blocks)
+{
     if (blocks > h->mlp_part_blocks) {
         if (h->mlp_part) cudaFree(h->mlp_part);
         h->mlp_part = nullptr;
@@ -1866,11 +1904,46 @@ int kdt_mlp_loss_grad(kdt *h, const uint16_t *params_bf16, const float *x, const
             return KDT_ERR_CUDA;
         h->mlp_part_blocks = blocks;
     }
+    return KDT_OK;
+}
+
+int kdt_mlp_loss_grad(kdt *h, const uint16_t *params_bf16, const float *x, const int32_t *labels,
+                      const int64_t *index, int64_t rows, float lam, float *grad, float *loss)
+{
+    if (!h || rows <= 0 || !params_bf16 || !x || !labels || !grad) return KDT_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    if (!on_device(h, params_bf16) || !on_device(h, x) || !on_device(h, labels) || !on_device(h, grad) ||
+        (loss && !on_device(h, loss)) || (index && !on_device(h, index)))
+        return KDT_ERR_ARG;
+    long long tiles = (rows + GT - 1) / GT;
+    int blocks = (int)std::min<long long>(tiles, 2ll * sm_count(h->device));
+    if (int rc = ensure_mlp_part(h, blocks)) return rc;
     const size_t smem = sizeof(MlpSmem);
     CK(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     float *part_loss = h->mlp_part + (size_t)h->mlp_part_blocks * MLP_PARAMS;
     k_mlp_grad<<<blocks, GTHREADS, smem, h->stream>>>((const unsigned short *)params_bf16, x, (const int *)labels,
                                                      (const long long *)index, rows, lam, h->mlp_part, part_loss);
+    k_mlp_reduce<<<(MLP_PARAMS + 255) / 256, 256, 0, h->stream>>>(h->mlp_part, part_loss, blocks, rows, grad, loss);
+    h->stats.kernel_launches += 2;
+    CK(cudaGetLastError());
+    return KDT_OK;
+}
+
+int kdt_mlp_loss_grad_tc(kdt *h, const uint16_t *params_bf16, const float *x, const int32_t *labels,
+                         const int64_t *index, int64_t rows, float lam, float *grad, float *loss)
+{
+    if (!h || rows <= 0 || !params_bf16 || !x || !labels || !grad) return KDT_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    if (!on_device(h, params_bf16) || !on_device(h, x) || !on_device(h, labels) || !on_device(h, grad) ||
+        (loss && !on_device(h, loss)) || (index && !on_device(h, index)))
+        return KDT_ERR_ARG;
+    if (((uintptr_t)params_bf16 & 3) != 0) return KDT_ERR_ARG;  // weight rows read as BF16 pairs
+    const int blocks = (int)std::min<long long>((rows + TC_M - 1) / TC_M, sm_count(h->device));
+    if (int rc = ensure_mlp_part(h, blocks)) return rc;
+    float *part_loss = h->mlp_part + (size_t)h->mlp_part_blocks * MLP_PARAMS;
+    k_mlp_grad_tc<<<blocks, TC_M, TG_BYTES, h->stream>>>((const unsigned short *)params_bf16, x, (const int *)labels,
+                                                        (const long long *)index, rows, lam, h->mlp_part, part_loss,
+                                                        h->counters + C_TC_FAIL);
     k_mlp_reduce<<<(MLP_PARAMS + 255) / 256, 256, 0, h->stream>>>(h->mlp_part, part_loss, blocks, rows, grad, loss);
     h->stats.kernel_launches += 2;
     CK(cudaGetLastError());

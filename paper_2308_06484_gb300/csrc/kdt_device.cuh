@@ -79,6 +79,8 @@ enum Counter : int {
     // warp's partitions and of its drain; summed spans from the start
     C_T0, C_TT, C_TD, C_SPAN_TICKETS, C_SPAN_DRAIN, C_SPAN_ALL,
     C_TH, C_TDM, C_SPAN_HUGE, C_SPAN_DRAINED, C_DRAINED_MAX, C_REDEFER,
+    // CTAs of the tensor-core network kernels that gave up waiting for their products
+    C_TC_FAIL,
     C_SLOTS
 };
 

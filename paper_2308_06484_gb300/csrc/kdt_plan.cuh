@@ -15,6 +15,8 @@
 //               star has not changed meanwhile); the move's estimated cost (k + 8, plus
 //               the predicted cavity size 2^out17 with the network) is added to its
 //               partition's total.
+//               With the network on the tensor cores the features go to a buffer
+//               instead and k_mlp_tc<1> evaluates all moves' rows as dense products.
 //   k_order     counting sort of the partitions by their estimated cost, largest
 //               first (64 logarithmic classes; the order inside a class is the order in
 //               which the atomics arrive, which only affects scheduling).
@@ -24,6 +26,7 @@ namespace kd {
 
 constexpr int PLAN_ORDER = 1;    // kdt_config.plan bit: hand out partitions by estimated work
 constexpr int PLAN_NETWORK = 2;  // ... bit: evaluate the proposal for all moves in the planner
+constexpr int PLAN_TENSOR = 4;   // ... bit: with PLAN_NETWORK, evaluate it on the tensor cores
 constexpr int PLAN_THREADS = 256;
 constexpr int PLAN_CLASSES = 64;
 
@@ -151,10 +154,13 @@ __device__ __forceinline__ bool plan_features(const Dev &d, const int *L, int k,
 
 // One thread per move i < m (m from the step's control words in a graph launch):
 // pguess[p] = the network's guess (0 .. 16, -1 = none) when mlp is set; pcost[cell of
-// the move's partition] += its estimated cost when pcost is set.
+// the move's partition] += its estimated cost when pcost is set.  With feat set (the
+// network evaluated on the tensor cores afterwards, k_mlp_tc<1>) the move's features go
+// to feat[i][0..31] and its partition to part[i] (-1: no features, no guess), pguess[p]
+// is set to -1 and the cost here leaves out the network's part.
 __global__ void __launch_bounds__(PLAN_THREADS) k_plan(Dev d, const int3 *gmoves, const int2 *old_xy, int m, Inst I,
                                                        int bits, const unsigned short *mlp, signed char *pguess,
-                                                       float *pcost)
+                                                       float *pcost, float *feat, int *part)
 {
     __shared__ float W[MLP_PARAMS];
     if (d.ctl) m = __ldcg(d.ctl);
@@ -172,18 +178,28 @@ __global__ void __launch_bounds__(PLAN_THREADS) k_plan(Dev d, const int3 *gmoves
         const int k = plan_star(d, p, L);
         float cost = 8.f + (k > 0 ? (float)k : (k == -2 ? 4.f * KMAX : 8.f));
         int guess = -1;
-        if (mlp && k > 0) {
-            float x[MLP_IN];
-            if (plan_features(d, L, k, po, q, x)) {
-                float o17 = 0.f;
-                guess = plan_network(W, x, o17);
-                cost += exp2f(fminf(fmaxf(o17, 0.f), 10.f));
-            }
+        bool featured = false;
+        float x[MLP_IN];
+        if ((mlp || feat) && k > 0) featured = plan_features(d, L, k, po, q, x);
+        if (featured && mlp) {
+            float o17 = 0.f;
+            guess = plan_network(W, x, o17);
+            cost += exp2f(fminf(fmaxf(o17, 0.f), 10.f));
         }
         if (pguess) pguess[p] = (signed char)guess;
-        if (pcost) {
+        int cell = -1;
+        if (pcost || feat) {
             const int inst = I.ninst > 1 ? csr_find(I.moff, I.ninst + 1, i) : 0;
-            atomicAdd(pcost + partition_of(I, inst, bits, po), cost);
+            cell = partition_of(I, inst, bits, po);
+        }
+        if (pcost) atomicAdd(pcost + cell, cost);
+        if (feat) {
+            if (featured) {
+                float4 *f4 = reinterpret_cast<float4 *>(feat + (long long)i * MLP_IN);
+#pragma unroll
+                for (int c = 0; c < MLP_IN / 4; ++c) f4[c] = make_float4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
+            }
+            part[i] = featured ? cell : -1;
         }
     }
 }

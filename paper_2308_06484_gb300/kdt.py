@@ -61,7 +61,7 @@ _STAT_FIELDS3 = ["cycles_ear", "cycles_lawson", "cycles_certify", "proposal_move
                  "span_tickets_ns", "span_drain_ns", "span_kernel_ns", "span_huge_ns", "span_drained_ns",
                  "cycles_drained_max", "redeferred", "far_rebuilds", "big_in_place", "cycles_big_in_place",
                  "cycles_big_delete", "cycles_big_insert", "cycles_unyielding_max", "cycles_global_insert",
-                 "cycles_global_insert_max"]
+                 "cycles_global_insert_max", "tensor_timeouts"]
 
 
 class Stats(ctypes.Structure):
@@ -89,7 +89,8 @@ SYMBOLS = ["kdt_default_config", "kdt_create", "kdt_destroy", "kdt_build", "kdt_
            "kdt_version", "kdt_stats_size", "kdt_config_size", "kdt_eval_predicates", "kdt_export_store",
            "kdt_export_triangles_noalloc", "kdt_build_batch", "kdt_step_batch",
            "kdt_export_triangles_inst", "kdt_num_instances", "kdt_set_trace", "kdt_trace_count",
-           "kdt_set_proposal", "kdt_mlp_forward", "kdt_mlp_loss_grad", "kdt_mlp_adam", "kdt_d_values",
+           "kdt_set_proposal", "kdt_mlp_forward", "kdt_mlp_forward_tc", "kdt_mlp_loss_grad",
+           "kdt_mlp_loss_grad_tc", "kdt_mlp_adam", "kdt_d_values",
            "kdt_num_cells"]
 
 MLP_IN, MLP_OUT, MLP_SLOTS, MLP_PARAMS = 32, 18, 17, 7442
@@ -141,7 +142,9 @@ def load(build_if_stale: bool = True):
     L.kdt_trace_count.argtypes = [vp, ctypes.POINTER(i64)]
     L.kdt_set_proposal.argtypes = [vp, vp]
     L.kdt_mlp_forward.argtypes = [vp, vp, vp, i64, vp]
+    L.kdt_mlp_forward_tc.argtypes = [vp, vp, vp, i64, vp]
     L.kdt_mlp_loss_grad.argtypes = [vp, vp, vp, vp, vp, i64, f32, vp, vp]
+    L.kdt_mlp_loss_grad_tc.argtypes = [vp, vp, vp, vp, vp, i64, f32, vp, vp]
     L.kdt_mlp_adam.argtypes = [vp, vp, vp, vp, vp, i64, f32, f32, f32, f32, vp]
     L.kdt_d_values.argtypes = [vp, ctypes.c_int32, vp, vp, ctypes.POINTER(DInfo)]
     L.kdt_num_cells.argtypes = [vp]
@@ -411,11 +414,18 @@ class Triangulation:
         _check(self.L.kdt_mlp_forward(self.h, _dptr(params_bf16, "int16"), _dptr(x, "float32", MLP_IN),
                                       x.shape[0], _dptr(out, "float32", MLP_OUT)), "kdt_mlp_forward")
 
-    def mlp_loss_grad(self, params_bf16, x, labels, grad, loss=None, index=None, rows=None, lam=0.25):
+    def mlp_forward_tc(self, params_bf16, x, out):
+        _check(self.L.kdt_mlp_forward_tc(self.h, _dptr(params_bf16, "int16"), _dptr(x, "float32", MLP_IN),
+                                         x.shape[0], _dptr(out, "float32", MLP_OUT)), "kdt_mlp_forward_tc")
+
+    def mlp_loss_grad(self, params_bf16, x, labels, grad, loss=None, index=None, rows=None, lam=0.25,
+                      tensor_cores=False):
+        """kdt_mlp_loss_grad, or kdt_mlp_loss_grad_tc with tensor_cores."""
         rows = (index.shape[0] if index is not None else x.shape[0]) if rows is None else rows
-        _check(self.L.kdt_mlp_loss_grad(self.h, _dptr(params_bf16, "int16"), _dptr(x, "float32", MLP_IN),
-                                        _dptr(labels, "int32", 2), _dptr(index, "int64"), rows, lam,
-                                        _dptr(grad, "float32"), _dptr(loss, "float32")), "kdt_mlp_loss_grad")
+        fn, name = ((self.L.kdt_mlp_loss_grad_tc, "kdt_mlp_loss_grad_tc") if tensor_cores
+                    else (self.L.kdt_mlp_loss_grad, "kdt_mlp_loss_grad"))
+        _check(fn(self.h, _dptr(params_bf16, "int16"), _dptr(x, "float32", MLP_IN), _dptr(labels, "int32", 2),
+                  _dptr(index, "int64"), rows, lam, _dptr(grad, "float32"), _dptr(loss, "float32")), name)
 
     def mlp_adam(self, master, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, params_bf16=None):
         _check(self.L.kdt_mlp_adam(self.h, _dptr(master, "float32"), _dptr(grad, "float32"), _dptr(m, "float32"),

@@ -59,9 +59,9 @@ class Trainer:
     """Adam on FP32 master parameters; the network always runs on their BF16 rounding."""
 
     def __init__(self, tri, seed: int = 0, lr: float = 2e-3, lam: float = 0.25, beta1: float = 0.9,
-                 beta2: float = 0.999, eps: float = 1e-8):
+                 beta2: float = 0.999, eps: float = 1e-8, tensor_cores: bool = False):
         import torch
-        self.tri, self.lr, self.lam = tri, lr, lam
+        self.tri, self.lr, self.lam, self.tensor_cores = tri, lr, lam, tensor_cores
         self.beta1, self.beta2, self.eps = beta1, beta2, eps
         dev = "cuda"
         self.master = torch.from_numpy(init_master(seed)).to(dev)
@@ -77,7 +77,8 @@ class Trainer:
     def step(self, x, y, index=None):
         """One Adam step on the batch (rows of x / y, or those listed in index)."""
         self.t += 1
-        self.tri.mlp_loss_grad(self.params, x, y, self.grad, self.loss, index=index, lam=self.lam)
+        self.tri.mlp_loss_grad(self.params, x, y, self.grad, self.loss, index=index, lam=self.lam,
+                               tensor_cores=self.tensor_cores)
         self.tri.mlp_adam(self.master, self.grad, self.m, self.v, self.t, self.lr, self.beta1, self.beta2,
                           self.eps, self.params)
 

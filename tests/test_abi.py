@@ -32,7 +32,7 @@ def test_library_exports_every_declared_symbol():
     for name in declared_functions():
         assert hasattr(L, name), name
     assert set(declared_functions()) <= set(kdt.SYMBOLS)
-    assert L.kdt_version() == 6
+    assert L.kdt_version() == 7
     assert L.kdt_stats_size() == ctypes.sizeof(kdt.Stats)
     assert L.kdt_config_size() == ctypes.sizeof(kdt.Config)
     assert L.kdt_num_cells(None) == 0 and L.kdt_num_points(None) == 0
