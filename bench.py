@@ -73,10 +73,10 @@ BYTES_K6 = bytes_per_update(6, 6)
 # sources it was taken on (their SHA-256 prefix) and the workload it was taken on; the
 # bench line reports it scaled to the launch's moves, null otherwise.
 KINETIC_TRAFFIC = {
-    # 16e6-point workload, 3 launches of 165,068 moves: 651.1, 650.3, 649.1 MB
-    "c3": {"sources": "5f448995558a0526", "bytes_per_move": 3939.0},
-    # 1e6-point workload, 2 launches of 4,096 moves: 15.62, 15.69 MB
-    "c2": {"sources": "5f448995558a0526", "bytes_per_move": 3823.0},
+    # 16e6-point workload, 3 launches of 165,068 moves: 649.9, 653.5, 648.7 MB
+    "c3": {"sources": "0a5e0b49bcda6ab7", "bytes_per_move": 3942.0},
+    # 1e6-point workload, 2 launches of 4,096 moves: 15.64, 15.69 MB
+    "c2": {"sources": "0a5e0b49bcda6ab7", "bytes_per_move": 3824.0},
 }
 
 
