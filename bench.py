@@ -73,9 +73,12 @@ BYTES_K6 = bytes_per_update(6, 6)
 # sources it was taken on (their SHA-256 prefix) and the workload it was taken on; the
 # bench line reports it scaled to the launch's moves, null otherwise.
 KINETIC_TRAFFIC = {
-    # 16e6-point workload, 3 launches of 165,068 moves: 649.9, 653.5, 648.7 MB
-    "c3": {"sources": "0a5e0b49bcda6ab7", "bytes_per_move": 3942.0},
-    # 1e6-point workload, 2 launches of 4,096 moves: 15.64, 15.69 MB
+    # 16e6-point workload, 3 launches of 165,068 moves: 441.5, 440.9, 438.7 MB (the
+    # triangle store as 32-byte records)
+    "c3": {"sources": "505f12924c6ce36f", "bytes_per_move": 2668.0},
+    # 1e6-point workload, 2 launches of 4,096 moves: 15.64, 15.69 MB, taken with the
+    # two halves of a triangle in separate arrays (no capture of the current sources:
+    # the traffic is reported as null)
     "c2": {"sources": "0a5e0b49bcda6ab7", "bytes_per_move": 3824.0},
 }
 

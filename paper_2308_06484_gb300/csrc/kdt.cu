@@ -67,8 +67,7 @@ struct kdt {
     int2 *xy = nullptr;
     int *pt_tri = nullptr;
     int *pt_stamp = nullptr;
-    int4 *tv = nullptr;
-    int4 *tn = nullptr;
+    int4 *tri = nullptr;  // 2 x cap int4: the 32-byte triangle records (TriHalf)
     int *scal = nullptr;                     // S_NUM device scalars
     unsigned long long *counters = nullptr;  // C_SLOTS
     int *dirty = nullptr;
@@ -231,8 +230,8 @@ Dev make_dev(kdt *h)
     Dev d;
     d.xy = h->xy;
     d.pt_tri = h->pt_tri;
-    d.tv = h->tv;
-    d.tn = h->tn;
+    d.tv = TriHalf{h->tri};
+    d.tn = TriHalf{h->tri + 1};
     d.n = (int)h->n;
     d.cap = h->cap;
     d.status = h->scal + S_STATUS;
@@ -409,8 +408,7 @@ int rebuild_instance(kdt *h, int i)
     CK(cudaMemcpyAsync(h->scal + S_MINX, init_bbox, sizeof init_bbox, cudaMemcpyHostToDevice, st));
     int third0 = INT_MAX;
     CK(cudaMemcpyAsync(h->scal + S_THIRD, &third0, sizeof(int), cudaMemcpyHostToDevice, st));
-    CK(cudaMemsetAsync(h->tv + s0, 0, (size_t)capi * sizeof(int4), st));
-    CK(cudaMemsetAsync(h->tn + s0, 0, (size_t)capi * sizeof(int4), st));
+    CK(cudaMemsetAsync(h->tri + 2 * (size_t)s0, 0, 2 * (size_t)capi * sizeof(int4), st));
     k_fill_int<<<thread_grid(h, n, 256), 256, 0, st>>>(h->pt_tri + p0, n, -1);
     k_range<<<thread_grid(h, n, 256), 256, 0, st>>>(h->xy + p0, n, h->cfg.domain_bits, h->scal + S_STATUS,
                                                     h->scal + S_MINX);
@@ -498,8 +496,7 @@ int rebuild_batch(kdt *h)
     }
     CK(cudaMemsetAsync(h->scal, 0, S_NUM * sizeof(int), st));
     CK(cudaMemcpyAsync(bbox, hb.data(), hb.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-    CK(cudaMemsetAsync(h->tv, 0, (size_t)h->cap * sizeof(int4), st));
-    CK(cudaMemsetAsync(h->tn, 0, (size_t)h->cap * sizeof(int4), st));
+    CK(cudaMemsetAsync(h->tri, 0, 2 * (size_t)h->cap * sizeof(int4), st));
     k_fill_int<<<thread_grid(h, n, 256), 256, 0, st>>>(h->pt_tri, n, -1);
     k_range_batch<<<thread_grid(h, n, 256), 256, 0, st>>>(h->xy, n, h->d_pofs, ni, h->cfg.domain_bits,
                                                           h->scal + S_STATUS, bbox);
@@ -688,7 +685,7 @@ void free_state(kdt *h)
 {
     drop_graph(h);
     h->gen++;
-    void *ps[] = {h->xy, h->pt_tri, h->pt_stamp, h->tv, h->tn, h->viol, h->moves, h->gmoves, h->old_xy,
+    void *ps[] = {h->xy, h->pt_tri, h->pt_stamp, h->tri, h->viol, h->moves, h->gmoves, h->old_xy,
                   h->next, h->head, h->deferred, h->dirty, h->scan_tmp, h->d_pofs, h->d_cofs, h->d_grid,
                   h->ctl, h->d_tofs, h->qmap, h->dloc2, h->pcost, h->order, h->ohist, h->pguess,
                   h->qhist, h->qpyr, h->qflag, h->qpre, h->qlev, h->pfeat, h->ppart};
@@ -697,7 +694,7 @@ void free_state(kdt *h)
     if (h->hctl) cudaFreeHost(h->hctl);
     h->ctl = nullptr;
     h->hctl = nullptr;
-    h->xy = nullptr; h->pt_tri = nullptr; h->pt_stamp = nullptr; h->tv = nullptr; h->tn = nullptr;
+    h->xy = nullptr; h->pt_tri = nullptr; h->pt_stamp = nullptr; h->tri = nullptr;
     h->viol = nullptr; h->moves = nullptr; h->gmoves = nullptr; h->old_xy = nullptr; h->next = nullptr;
     h->head = nullptr; h->deferred = nullptr; h->dirty = nullptr; h->scan_tmp = nullptr;
     h->d_pofs = nullptr; h->d_cofs = nullptr; h->d_grid = nullptr; h->d_moff = nullptr; h->h_moff = nullptr;
@@ -743,8 +740,7 @@ int alloc_state(kdt *h, const int64_t *offs, int n_inst)
     h->n = offs[n_inst];
     h->cap = h->tofs[n_inst];
     h->built = false;
-    if (dalloc(&h->xy, h->n) || dalloc(&h->pt_tri, h->n) || dalloc(&h->pt_stamp, h->n) || dalloc(&h->tv, h->cap) ||
-        dalloc(&h->tn, h->cap) || dalloc(&h->d_pofs, n_inst + 1) || dalloc(&h->ctl, 4 + n_inst + 1) ||
+    if (dalloc(&h->xy, h->n) || dalloc(&h->pt_tri, h->n) || dalloc(&h->pt_stamp, h->n) || dalloc(&h->tri, 2 * (size_t)h->cap) || dalloc(&h->d_pofs, n_inst + 1) || dalloc(&h->ctl, 4 + n_inst + 1) ||
         dalloc(&h->d_tofs, n_inst + 1) || dalloc(&h->pguess, h->n) || dalloc(&h->ohist, 2 * PLAN_CLASSES))
         return KDT_ERR_CUDA;
     if (cudaMallocHost(&h->hctl, (4 + n_inst + 1) * sizeof(int)) != cudaSuccess) return KDT_ERR_CUDA;
@@ -1238,7 +1234,7 @@ int export_range(kdt *h, int s0, int nslots, int idbase, int np, int32_t *out, i
         return KDT_ERR_CUDA;
     int *cnt = (int *)h->exp_cnt.p, *off = (int *)h->exp_off.p, *fill = (int *)h->exp_fill.p;
     CK(cudaMemsetAsync(cnt, 0, (size_t)np * 4, st));
-    k_exp_count<<<thread_grid(h, nslots, 256), 256, 0, st>>>(h->tv + s0, nslots, cnt, idbase);
+    k_exp_count<<<thread_grid(h, nslots, 256), 256, 0, st>>>(TriHalf{h->tri + 2 * (size_t)s0}, nslots, cnt, idbase);
     h->stats.kernel_launches++;
     if (scan(h, cnt, off, np, h->scal + S_TOTAL, st)) return KDT_ERR_CUDA;
     if (sync_scalars(h)) return KDT_ERR_CUDA;
@@ -1254,7 +1250,7 @@ int export_range(kdt *h, int s0, int nslots, int idbase, int np, int32_t *out, i
         dst = (int3 *)h->exp_out.p;
     }
     CK(cudaMemsetAsync(fill, 0, (size_t)np * 4, st));
-    k_exp_place<<<thread_grid(h, nslots, 256), 256, 0, st>>>(h->tv + s0, nslots, off, fill, dst, idbase);
+    k_exp_place<<<thread_grid(h, nslots, 256), 256, 0, st>>>(TriHalf{h->tri + 2 * (size_t)s0}, nslots, off, fill, dst, idbase);
     k_exp_sortseg<<<thread_grid(h, np, 256), 256, 0, st>>>(np, off, cnt, dst);
     h->stats.kernel_launches += 2;
     CK(cudaGetLastError());
@@ -1608,14 +1604,14 @@ int d_values_impl(kdt *h, int N, int64_t *dist2, int64_t *cell_min2, kdt_dinfo *
         return KDT_ERR_CUDA;
     int *deg = (int *)h->nb_deg.p, *off = (int *)h->nb_off.p;
     CK(cudaMemsetAsync(deg, 0, (size_t)n * sizeof(int), st));
-    k_nbr_count<<<thread_grid(h, h->cap, 256), 256, 0, st>>>(h->tv, h->cap, deg);
+    k_nbr_count<<<thread_grid(h, h->cap, 256), 256, 0, st>>>(TriHalf{h->tri}, h->cap, deg);
     if (scan(h, deg, off, n, off + n, st)) return KDT_ERR_CUDA;
     int total = 0;
     CK(cudaMemcpyAsync(&total, off + n, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (grow(h->nb_list, (size_t)std::max(total, 1) * sizeof(int))) return KDT_ERR_CUDA;
     CK(cudaMemsetAsync(deg, 0, (size_t)n * sizeof(int), st));  // now the fill positions
-    k_nbr_fill<<<thread_grid(h, h->cap, 256), 256, 0, st>>>(h->tv, h->cap, off, deg, (int *)h->nb_list.p);
+    k_nbr_fill<<<thread_grid(h, h->cap, 256), 256, 0, st>>>(TriHalf{h->tri}, h->cap, off, deg, (int *)h->nb_list.p);
     // the N-th nearest neighbours and their minima
     const bool dist_dev = dist2 && on_device(h, dist2);
     const bool cmin_dev = cell_min2 && on_device(h, cell_min2);
@@ -1716,8 +1712,11 @@ int kdt_export_store(kdt *h, int32_t *tv, int32_t *tn, int32_t *pt_tri, int64_t 
     if (cap_slots < h->cap) return KDT_ERR_CAPACITY;
     CK(cudaSetDevice(h->device));
     CK(cudaStreamSynchronize(h->stream));
-    if (tv) CK(cudaMemcpy(tv, h->tv, (size_t)h->cap * sizeof(int4), cudaMemcpyDeviceToHost));
-    if (tn) CK(cudaMemcpy(tn, h->tn, (size_t)h->cap * sizeof(int4), cudaMemcpyDeviceToHost));
+    // the two halves of the 32-byte records, each as a dense cap x 4 array
+    if (tv) CK(cudaMemcpy2D(tv, sizeof(int4), h->tri, 2 * sizeof(int4), sizeof(int4), (size_t)h->cap,
+                            cudaMemcpyDeviceToHost));
+    if (tn) CK(cudaMemcpy2D(tn, sizeof(int4), h->tri + 1, 2 * sizeof(int4), sizeof(int4), (size_t)h->cap,
+                            cudaMemcpyDeviceToHost));
     if (pt_tri) CK(cudaMemcpy(pt_tri, h->pt_tri, (size_t)h->n * sizeof(int), cudaMemcpyDeviceToHost));
     return KDT_OK;
 }
@@ -1791,7 +1790,7 @@ extern "C" int kdt_export_triangles_noalloc(kdt *h, int32_t *out, int64_t cap, i
     int *total = tiles + 1023;                            // grand total
     const int ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     CK(cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(int), st));
-    k_exp_count<<<thread_grid(h, h->cap, 256), 256, 0, st>>>(h->tv, h->cap, cnt, 0);
+    k_exp_count<<<thread_grid(h, h->cap, 256), 256, 0, st>>>(TriHalf{h->tri}, h->cap, cnt, 0);
     k_scan_tile<<<ntiles, SCAN_THREADS, 0, st>>>(cnt, off, n, tiles);
     k_scan_sums<<<1, 1024, 0, st>>>(tiles, ntiles, total);
     k_scan_add<<<ntiles, SCAN_THREADS, 0, st>>>(off, n, tiles);
@@ -1803,7 +1802,7 @@ extern "C" int kdt_export_triangles_noalloc(kdt *h, int32_t *out, int64_t cap, i
     *n_tri = tot;
     if (tot > cap) return KDT_ERR_CAPACITY;
     CK(cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(int), st));
-    k_exp_place<<<thread_grid(h, h->cap, 256), 256, 0, st>>>(h->tv, h->cap, off, cnt, (int3 *)out, 0);
+    k_exp_place<<<thread_grid(h, h->cap, 256), 256, 0, st>>>(TriHalf{h->tri}, h->cap, off, cnt, (int3 *)out, 0);
     k_exp_sortseg<<<thread_grid(h, n, 256), 256, 0, st>>>(n, off, cnt, (int3 *)out);
     h->stats.kernel_launches += 2;
     CK(cudaGetLastError());

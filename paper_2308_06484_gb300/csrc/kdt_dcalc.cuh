@@ -25,7 +25,7 @@ constexpr int DC_MAX_N = 16;  // largest N a call may ask for
 // counter-clockwise order gives u the neighbour v.  An interior edge is seen once from
 // each side and a hull edge once from its finite triangle and once from its ghost, so
 // every neighbour is counted exactly once.
-__global__ void k_nbr_count(const int4 *tv, int nslots, int *deg)
+__global__ void k_nbr_count(TriHalf tv, int nslots, int *deg)
 {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nslots; t += gridDim.x * blockDim.x) {
         int4 v = tv[t];
@@ -38,7 +38,7 @@ __global__ void k_nbr_count(const int4 *tv, int nslots, int *deg)
 
 // The same edges written into the lists (off: exclusive scan of the counts; cur:
 // zeroed fill positions).  The order inside a list does not matter.
-__global__ void k_nbr_fill(const int4 *tv, int nslots, const int *off, int *cur, int *nbr)
+__global__ void k_nbr_fill(TriHalf tv, int nslots, const int *off, int *cur, int *nbr)
 {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nslots; t += gridDim.x * blockDim.x) {
         int4 v = tv[t];

@@ -84,13 +84,24 @@ enum Counter : int {
     C_SLOTS
 };
 
+// One half of the triangle store.  A triangle is one 32-byte record: its vertex half
+// (tv: three point ids, the alive flag) at an even int4 slot and its neighbour half (tn:
+// three (slot << 2 | edge) references, the claim owner word) right after it, so both
+// halves of a triangle come from one DRAM sector.  tv[t] / tv + t reach record t's
+// vertex half, tn[t] / tn + t its neighbour half.
+struct TriHalf {
+    int4 *p;  // this half of record 0
+    __host__ __device__ __forceinline__ int4 &operator[](long long t) const { return p[2 * t]; }
+    __host__ __device__ __forceinline__ int4 *operator+(long long t) const { return p + 2 * t; }
+};
+
 struct Dev {
     // (pointers first, then 32-bit fields: no padding, the struct is copied into every
     // block's shared memory)
     int2 *xy;
     int *pt_tri;
-    int4 *tv;
-    int4 *tn;
+    TriHalf tv;
+    TriHalf tn;
     int *status;
     int *dirty;          // slots written in this step (for certification)
     int *dirty_count;

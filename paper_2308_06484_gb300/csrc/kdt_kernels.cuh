@@ -1180,7 +1180,7 @@ __device__ __forceinline__ bool finite_alive(const int4 &v)
     return (v.w & ALIVE) && v.x >= 0 && v.y >= 0 && v.z >= 0;
 }
 
-__global__ void k_exp_count(const int4 *tv, int nslots, int *cnt, int idbase)
+__global__ void k_exp_count(TriHalf tv, int nslots, int *cnt, int idbase)
 {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nslots; t += gridDim.x * blockDim.x) {
         int4 v = tv[t];
@@ -1190,7 +1190,7 @@ __global__ void k_exp_count(const int4 *tv, int nslots, int *cnt, int idbase)
 }
 
 // rotate so the smallest id comes first (keeps the counter-clockwise order)
-__global__ void k_exp_place(const int4 *tv, int nslots, const int *off, int *fill, int3 *out, int idbase)
+__global__ void k_exp_place(TriHalf tv, int nslots, const int *off, int *fill, int3 *out, int idbase)
 {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nslots; t += gridDim.x * blockDim.x) {
         int4 v = tv[t];
