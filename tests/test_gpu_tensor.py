@@ -58,8 +58,9 @@ def test_forward_tc_within_bound(rows, scale):
     err = np.abs(got - ref)
     assert np.all(np.isfinite(got))
     assert np.all(err <= bound), (err.max(), bound[err > bound][:4])
-    # the lo parts are used: BF16 activations alone would leave errors near 2^-9 of S3
-    assert np.max(err / S3) < 2.0 ** -13
+    # the lo parts are used: BF16 activations alone leave errors of about 2^-14.5 of S3
+    # (tests/test_split_precision.py); with them the kernel measured 2^-24 on a GB300
+    assert np.max(err / S3) < 2.0 ** -19
     # the guesses equal the FP32 CUDA-core evaluation's wherever the two largest slot
     # logits are farther apart than twice the bound
     o32 = torch.empty((rows, 18), dtype=torch.float32, device="cuda")
