@@ -284,7 +284,7 @@ int kdt_export_points(kdt *h, int32_t *xy, int64_t cap_points);
  * and whenever the point count grows, so it calls cudaMalloc.  Some callers cannot
  * allow that: an application that reserved the whole device memory budget for its
  * own pool before creating the handle, or a per-step output loop that must not take
- * the driver's allocation path.  This entry point produces the same canonical list
+ * the CUDA driver's allocation path.  This entry point produces the same canonical list
  * (same order, same rows) and allocates nothing: its scratch (per-vertex counts and
  * offsets, scan partial sums) is one file-scope device array of
  * KDT_NOALLOC_MAX_POINTS * 8 + 4 KiB bytes (about 8 MiB), which every GPU that
